@@ -1,0 +1,137 @@
+"""Whole-step pins for the oracle: the paper's verification problems (sec. 5)
+that have closed forms, and dense-vs-reduced brute force on tiny grids."""
+import zlib
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import angles
+
+
+def _slab_two_stream():
+    # one angle per octant seen from a slab: mu = +-1/sqrt(3), weights 1/2
+    mu = 1.0 / np.sqrt(3.0)
+    s = np.sqrt(1 - mu * mu)
+    return np.array([[mu, s, 0.0], [-mu, s, 0.0]]), np.array([0.5, 0.5])
+
+
+@pytest.mark.parametrize("eps,steps", [(0.1, 12000), (1e-2, 12000), (1e-3, 40000), (1e-4, 40000)])
+def test_non_lte_atmosphere(eps, steps):
+    # sec. 5.3: rho = 1e-3 exp(-z + 10) on z in (-10, 10), T = 1 held, v = 0,
+    # s_a = eps rho, s_s = (1 - eps) rho, one angle per octant, vacuum top,
+    # copy bottom.  The steady state follows
+    # E_r(tau) = 1 - exp(-sqrt(3 eps) tau) / (1 + sqrt(eps)), which is exact
+    # for the discrete two-stream problem; at the surface E = sqrt(eps)/(1+sqrt(eps)).
+    # The x, y directions are uniform, so the test runs on the vertical axis.
+    n, w = _slab_two_stream()
+    nz = 320
+    dz = 20.0 / nz
+    z = -10.0 + (np.arange(nz) + 0.5) * dz
+    rho = 1e-3 * np.exp(-z + 10.0)
+    p = oracle.Problem((1, 1, nz), dz, n, w, C=10.0, P=1.0, dim=1,
+                       bc=((oracle.COPY, oracle.VACUUM), (0, 0), (0, 0)), hold_T=True)
+    I = np.full((2, nz), 1.0 / (4 * np.pi))
+    T, v = np.ones(nz), np.zeros((3, nz))
+    dt = oracle.cfl_dt(p, 0.4)
+    for _ in range(steps):
+        out = oracle.step(p, dt, I, T, rho, v, eps * rho, (1 - eps) * rho)
+        I = out["I"]
+    tau = np.cumsum((rho * dz)[::-1])[::-1] - 0.5 * rho * dz
+    Ea = 1.0 - np.exp(-np.sqrt(3 * eps) * tau) / (1.0 + np.sqrt(eps))
+    surface = np.sqrt(eps) / (1.0 + np.sqrt(eps))
+    assert abs(out["E"][-1] / surface - 1.0) < 0.01
+    assert np.abs(out["E"] - Ea).max() < 3e-3
+
+
+def _diffusion(tau_cell, t_end, nx=128, C=10.0, v=1.0):
+    # sec. 5.5 setup: L = 2, periodic, rho = T = v = 1, pure scattering,
+    # one angle per octant (two rays in 1-D), initial E, F from the paper
+    L = 2.0
+    dx = L / nx
+    x = -1.0 + (np.arange(nx) + 0.5) * dx
+    ss = np.full(nx, tau_cell / dx)
+    n, w = _slab_two_stream()
+    mu = n[0, 0]
+    p = oracle.Problem((1, 1, nx), dx, n, w, C=C, P=1.0, dim=1, hold_T=True)
+    inside = np.abs(x) < 0.5
+    E0 = np.where(inside, np.exp(-40 * x * x), np.exp(-10.0))
+    F0 = np.where(inside, 80 * x / (3 * ss) * E0 + 4 * v / (3 * C) * E0, 4 * v * E0 / (3 * C))
+    # two rays: E = 2 pi (I+ + I-), F = 2 pi mu (I+ - I-)
+    I = np.stack([(E0 / (2 * np.pi) + F0 / (2 * np.pi * mu)) / 2, (E0 / (2 * np.pi) - F0 / (2 * np.pi * mu)) / 2])
+    vv = np.zeros((3, nx))
+    vv[0] = v
+    dt = oracle.cfl_dt(p, 0.4)
+    nsteps = int(round(t_end / dt))
+    for _ in range(nsteps):
+        out = oracle.step(p, dt, I, np.ones(nx), np.ones(nx), vv, np.zeros(nx), ss)
+        I = out["I"]
+    t = nsteps * dt
+    D = C / (3 * ss[0])
+    E = out["E"] - np.exp(-10.0)
+    centre = np.angle(np.sum(E * np.exp(1j * np.pi * x))) / np.pi
+    xc = (x - centre + 1) % 2 - 1
+    var = np.sum(E * xc ** 2) / np.sum(E)
+    xs = (x - v * t + 1) % 2 - 1
+    Ea = (160 * D * t + 1) ** -0.5 * np.exp(-40 * xs ** 2 / (160 * D * t + 1))
+    return dict(t=t, D=D, centre=centre, var=var, E=out["E"], Ea=Ea, mass=E.sum() * dx, mass0=(E0 - np.exp(-10)).sum() * dx)
+
+
+def test_dynamic_diffusion_optically_thick():
+    # sec. 5.5, tau_s = 625 per cell: the Gaussian moves with the gas and
+    # spreads at the physical rate D = C/(3 s_s) (eq. diffsolution).  The
+    # original Stone & Mihalas transport (alpha = 1) gives a numerical
+    # diffusion ~ C mu dx / 2, about 500 times D here: the variance growth
+    # must stay within a small factor of 2 D t.
+    r = _diffusion(625.0, 1.0)
+    expect_centre = (r["t"] + 1) % 2 - 1
+    assert abs(r["centre"] - expect_centre) < 0.02
+    growth = r["var"] - 1.0 / 80.0
+    assert 0.5 < growth / (2 * r["D"] * r["t"]) < 3.0
+    assert abs(r["mass"] / r["mass0"] - 1) < 1e-10
+
+
+def test_dynamic_diffusion_moderate_depth():
+    # sec. 5.5, tau_s = 6.25 per cell, t = 0.4: profile within a few per cent
+    r = _diffusion(6.25, 0.4)
+    assert abs(r["centre"] - r["t"]) < 0.01
+    growth = r["var"] - 1.0 / 80.0
+    assert abs(growth / (2 * r["D"] * r["t"]) - 1.0) < 0.05
+    assert np.abs(r["E"] - r["Ea"]).max() < 0.03
+
+
+def _random_problem(rng, shape, name, bc, estimate_v, hold_T, dense):
+    n, w = angles.by_name(name)
+    C = 15.0
+    inflow = {(0, 0): rng.uniform(0, 1, len(w))}
+    p = oracle.Problem(shape, (0.11, 0.13, 0.17), n, w, C=C, P=4.0, bc=bc, inflow=inflow,
+                       hold_T=hold_T, estimate_v=estimate_v, dense=dense)
+    return p
+
+
+@pytest.mark.parametrize("shape,name,bc", [
+    ((1, 1, 6), "gl8", ((oracle.COPY, oracle.VACUUM), (0, 0), (0, 0))),
+    ((1, 4, 5), "s4", ((oracle.INFLOW, oracle.COPY), (oracle.VACUUM, oracle.VACUUM), (0, 0))),
+    ((3, 4, 3), "s4", ((0, 0), (0, 0), (0, 0))),
+])
+@pytest.mark.parametrize("estimate_v,hold_T", [(False, True), (True, False)])
+def test_whole_step_dense_equals_reduced(shape, name, bc, estimate_v, hold_T):
+    # brute force on tiny grids: the full step with dense Gaussian-elimination
+    # solvers against the O(N) reduced solvers, random fields with velocity
+    rng = np.random.default_rng(zlib.crc32(repr((shape, name, estimate_v)).encode()))
+    pr = _random_problem(rng, shape, name, bc, estimate_v, hold_T, False)
+    pd = _random_problem(np.random.default_rng(0), shape, name, bc, estimate_v, hold_T, True)
+    pd._inflow[:] = pr._inflow
+    N, M = pr.N, pr.M
+    I = rng.uniform(0.05, 1.0, (M, N))
+    T = rng.uniform(0.5, 1.5, N)
+    rho = rng.uniform(0.5, 2.0, N)
+    v = rng.uniform(-0.1, 0.1, (3, N)) * pr.C
+    sa = 10 ** rng.uniform(-1, 2, N)
+    ss = 10 ** rng.uniform(-1, 2, N)
+    dt = oracle.cfl_dt(pr, 0.4)
+    a = oracle.run(pr, dt, 3, I, T, rho, v, sa, ss)
+    b = oracle.run(pd, dt, 3, I, T, rho, v, sa, ss)
+    for k in ("I", "T", "E", "F", "P", "dEgas", "dMom"):
+        scale = np.abs(b[k]).max()
+        np.testing.assert_allclose(a[k], b[k], rtol=1e-12, atol=1e-13 * scale, err_msg=k)

@@ -1,0 +1,118 @@
+"""Pins for the oracle's transport step (sec. 4.2) and boundary values."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import angles
+
+
+def _two_rays(mu=1.0):
+    s = np.sqrt(max(0.0, 1.0 - mu * mu))
+    n = np.array([[mu, s, 0.0], [-mu, s, 0.0]])
+    return n, np.array([0.5, 0.5])
+
+
+def _zeros(N):
+    return np.zeros(N)
+
+
+@pytest.mark.parametrize("with_v", [False, True])
+def test_flux_differencing_conserves_each_ray(with_v):
+    # Abstract / sec. 4.2: conservative differencing keeps sum_cells I_m fixed
+    # on a periodic grid with no sources (sigma = 0), for every angle.
+    rng = np.random.default_rng(11)
+    n, w = angles.level_symmetric(4)
+    p = oracle.Problem((5, 6, 7), (0.1, 0.12, 0.09), n, w, C=10.0, P=1.0)
+    N, M = p.N, p.M
+    I = rng.uniform(0.1, 2.0, (M, N))
+    v = rng.uniform(-0.5, 0.5, (3, N)) if with_v else np.zeros((3, N))
+    dt = oracle.cfl_dt(p, 0.4)
+    dF = oracle.transport(p, dt, I, v, _zeros(N), _zeros(N))
+    scale = np.abs(dF).max()
+    assert scale > 1e-3
+    np.testing.assert_allclose(dF.sum(axis=1), 0.0, atol=1e-13 * scale * N)
+    out = oracle.step(p, dt, I, np.ones(N), np.ones(N), v, _zeros(N), _zeros(N))
+    np.testing.assert_allclose(out["I"].sum(axis=1), I.sum(axis=1), rtol=1e-13)
+
+
+def test_unit_courant_number_shifts_one_cell():
+    # With alpha = 1 (sigma = 0), v = 0, mu = +-1 and C dt = dx (nu = 1) the
+    # van Leer face state is the upwind cell value, so each step moves every
+    # ray exactly one cell (sec. 4.2 with Stone & Mihalas eq. 4 at nu = 1).
+    n, w = _two_rays(1.0)
+    nx = 16
+    p = oracle.Problem((1, 1, nx), 1.0 / nx, n, w, C=10.0, P=1.0, dim=1)
+    rng = np.random.default_rng(3)
+    I = rng.uniform(0.0, 1.0, (2, nx))
+    dt = (1.0 / nx) / 10.0
+    out = oracle.step(p, dt, I, np.ones(nx), np.ones(nx), np.zeros((3, nx)), _zeros(nx), _zeros(nx))
+    np.testing.assert_allclose(out["I"][0], np.roll(I[0], 1), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(out["I"][1], np.roll(I[1], -1), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("kind", [oracle.VACUUM, oracle.INFLOW, oracle.COPY])
+def test_boundary_kinds_at_unit_courant(kind):
+    # Ghost values (sec. 5.3 / 5.8 setups): vacuum zeroes incoming rays,
+    # inflow sets them, copy repeats the last active cell.  At nu = 1 the first
+    # cell takes the ghost value of the incoming ray after one step.
+    n, w = _two_rays(1.0)
+    nx = 8
+    inflow = {(0, 0): np.array([7.0, 0.0])}
+    p = oracle.Problem((1, 1, nx), 1.0 / nx, n, w, C=10.0, P=1.0, dim=1,
+                       bc=((kind, oracle.VACUUM), (0, 0), (0, 0)), inflow=inflow)
+    I = np.arange(1.0, 1.0 + 2 * nx).reshape(2, nx)
+    dt = (1.0 / nx) / 10.0
+    out = oracle.step(p, dt, I, np.ones(nx), np.ones(nx), np.zeros((3, nx)), _zeros(nx), _zeros(nx))
+    expect_first = {oracle.VACUUM: 0.0, oracle.INFLOW: 7.0, oracle.COPY: I[0, 0]}[kind]
+    assert out["I"][0, 0] == expect_first
+    np.testing.assert_array_equal(out["I"][0, 1:], I[0, :-1])
+    # the mu < 0 ray leaves through x_lo and enters through the vacuum x_hi
+    np.testing.assert_array_equal(out["I"][1, :-1], I[1, 1:])
+    assert out["I"][1, -1] == 0.0
+
+
+def test_uniform_field_has_no_transport():
+    # a constant intensity with uniform J and v gives zero flux divergence
+    n, w = angles.level_symmetric(6)
+    p = oracle.Problem((4, 4, 4), 0.25, n, w, C=5.0, P=1.0)
+    N = p.N
+    I = np.full((p.M, N), 0.3)
+    v = np.tile(np.array([[0.2], [-0.1], [0.05]]), (1, N))
+    dF = oracle.transport(p, 0.01, I, v, np.full(N, 2.0), np.full(N, 1.0))
+    assert np.abs(dF).max() < 1e-15
+
+
+def _advect_error(nx, steps_per_unit=None):
+    # one ray along +x, sigma = 0, periodic, smooth profile; error after t = 1/C
+    n, w = _two_rays(1.0)
+    C = 1.0
+    p = oracle.Problem((1, 1, nx), 1.0 / nx, n, w, C=C, P=1.0, dim=1)
+    x = (np.arange(nx) + 0.5) / nx
+    prof = lambda s: 1.0 + 0.5 * np.sin(2 * np.pi * s)
+    I = np.stack([prof(x), prof(x)])
+    dt = oracle.cfl_dt(p, 0.4)
+    nsteps = int(round(0.5 / dt))
+    dt = 0.5 / nsteps
+    for _ in range(nsteps):
+        I = oracle.step(p, dt, I, np.ones(nx), np.ones(nx), np.zeros((3, nx)), _zeros(nx), _zeros(nx))["I"]
+    return np.mean(np.abs(I[0] - prof(x - 0.5)))
+
+
+def test_second_order_convergence_on_smooth_profile():
+    # van Leer reconstruction is second order away from extrema; in L1 over a
+    # sine wave the observed order must be well above first order.
+    e1, e2, e3 = (_advect_error(nx) for nx in (32, 64, 128))
+    order = np.log2(e2 / e3)
+    assert np.log2(e1 / e2) > 1.5 and order > 1.6, (e1, e2, e3)
+
+
+def test_alpha_limits():
+    # sec. 4.2: alpha -> 1 for an optically thin cell, alpha ~ 1/(10 dl sigma)
+    # when the optical depth per cell is large.
+    assert oracle.alpha(0.1, 0.0) == 1.0
+    assert abs(oracle.alpha(0.1, 1e-5) - 1.0) < 1e-9
+    for s in (10.0, 100.0, 1e4):
+        a = oracle.alpha(0.1, s)
+        assert abs(a * (10 * 0.1 * s) - 1.0) < 1e-12
+    # tau = 1 exactly: sqrt(1 - e^-1)
+    assert abs(oracle.alpha(0.1, 1.0) - np.sqrt(1 - np.exp(-1.0))) < 1e-15
