@@ -1,0 +1,378 @@
+"""Benchmark of the fused radiation-transfer step on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload box3d]
+                    [--impl reference] [--no-e2e] [--no-cpu-baseline]
+
+One step = one pass of the whole hot path (transport, velocity estimate,
+absorption with the T^4 solve, scattering, quadrature and gas sources) over
+the workload, which stays resident in HBM.  The default workload is the 3-D
+periodic radiation-dominated box, 128^3 cells x 80 angles (S8), float32
+intensities with the temperature solve finished in double.  Prints one JSON
+line.  Under torchrun (N > 1) every rank runs its own independent copy of
+the problem (replicas: the method needs no exchange between independent
+problems) and rank 0 reports the whole-job rate over the slowest rank.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores (rank 0 only).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PROFILE = os.path.join(ROOT, "profiles", "step_kernel_box3d.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_1403_6126_gb300", "csrc", "rt_step.cu")
+
+
+def algorithmic_bytes_per_cell(M, rs, velocity, live_T):
+    """Bytes one fused step must move per cell: read and write I (M values of
+    rs bytes); read rho, sigma_a, sigma_s, v and T; read E (for IV = 3 n.v J)
+    and F, P_xx..P_zz (for the velocity estimate) when velocity terms are on;
+    write T, E, F, P (10 moments), the gas energy source (double) and the
+    momentum source (3)."""
+    b = 2 * M * rs                 # I^n in, I^{n+1} out
+    b += 3 * rs + 3 * rs           # rho, sigma_a, sigma_s, v
+    b += 8 + (8 if live_T else 0)  # T in (double), T out when it evolves
+    if velocity:
+        b += 7 * rs                # E, F, P_dd of step n
+    b += 10 * rs + 8 + 3 * rs      # moments, dE_gas, dMom
+    return b
+
+
+def _sha(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _profile_traffic():
+    """Per-launch DRAM bytes from the committed ncu summary, or None when the
+    kernel source changed since that capture."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256_16") != _sha(KERNEL_SRC):
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed
+    region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu_index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.rows = []
+        if self.proc is None:
+            return
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 9:
+                self.rows.append(parts)
+
+    def summary(self):
+        rows = getattr(self, "rows", [])
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _angles(name):
+    import paper_1403_6126_gb300 as rt
+    if name.startswith("s"):
+        return rt.rt_angle_set(rt.RT_ANGLES_LEVEL_SYMMETRIC, int(name[1:]))
+    return rt.rt_angle_set(rt.RT_ANGLES_GAUSS_LEGENDRE, int(name[2:]))
+
+
+def _context(wl, n, w, stream=None, precision=None):
+    import paper_1403_6126_gb300 as rt
+    from paper_1403_6126_gb300 import workloads as wlmod
+    prec = {"fp64": rt.RT_FP64, "fp32": rt.RT_FP32}[precision or wl["precision"]]
+    ctx = rt.Context(wl["shape"], n, w, wl["C"], wl["P"], dim=wl["dim"], lo=wl["lo"], hi=wl["hi"], bc=wl["bc"],
+                     precision=prec, cfl=wl["cfl"], gamma=wl["gamma"], r_ideal=wl["R"], hold_T=wl["hold_T"],
+                     estimate_v=wl["estimate_v"], stream=stream)
+    for (axis, side), rule in wl["inflow"].items():
+        ctx.set_inflow(axis, side, wlmod.inflow_values(rule, n))
+    return ctx
+
+
+def cpu_baseline(wl_name, steps, warmup, sample_n=None):
+    """Times the FP64 oracle, as it stands, on a bounded sample of the
+    workload: the same recipe on a smaller grid, OpenMP over the host cores."""
+    import oracle
+    from paper_1403_6126_gb300 import workloads as wlmod
+    kw = {}
+    if wl_name == "box3d":
+        kw = dict(n=sample_n or 32)
+    wl = wlmod.by_name(wl_name, **kw)
+    n, w = oracle.angles.by_name(wl["angles"])
+    dx = tuple((wl["hi"][d] - wl["lo"][d]) / wl["shape"][2 - d] for d in range(3))
+    inflow = {face: wlmod.inflow_values(rule, n) for face, rule in wl["inflow"].items()}
+    p = oracle.Problem(wl["shape"], dx, n, w, C=wl["C"], P=wl["P"], dim=wl["dim"], bc=wl["bc"], inflow=inflow,
+                       gamma=wl["gamma"], R=wl["R"], hold_T=wl["hold_T"], estimate_v=wl["estimate_v"])
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    I = wlmod.initial_intensity(wl, len(w))
+    T = wl["T"].copy()
+    dt = oracle.cfl_dt(p, wl["cfl"])
+    for _ in range(warmup):
+        out = oracle.step(p, dt, I, T, wl["rho"], wl["v"], wl["sa"], wl["ss"])
+        I, T = out["I"], out["T"]
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        out = oracle.step(p, dt, I, T, wl["rho"], wl["v"], wl["sa"], wl["ss"])
+        I, T = out["I"], out["T"]
+    el = time.perf_counter() - t0
+    units = p.N * p.M * steps
+    return dict(value=units / el, unit="cell-angle updates/s", cores=oracle.max_threads(), kind="oracle",
+                sample="%s recipe at %s cells x %d angles, %d timed steps (+%d warm-up), FP64 C oracle, OpenMP"
+                       % (wl_name, "x".join(str(s) for s in wl["shape"][::-1]), p.M, steps, warmup),
+                seconds=el)
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    res = cpu_baseline(args.workload, args.steps, args.warmup, sample_n=args.cpu_sample_n)
+    line = {
+        "impl": "reference", "metric": "cell-angle updates/s", "value": res["value"], "unit": res["unit"],
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * res["seconds"] / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample": res["sample"]},
+        "cpu_baseline": {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "e2e": {"value": res["value"], "unit": res["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    import paper_1403_6126_gb300 as rt
+    from paper_1403_6126_gb300 import build as rtbuild
+    from paper_1403_6126_gb300 import workloads as wlmod
+
+    rtbuild.build()
+    kw = {}
+    if args.workload == "box3d" and args.n:
+        kw["n"] = args.n
+    wl = wlmod.by_name(args.workload, **kw)
+    n, w = _angles(wl["angles"])
+    M = len(w)
+    N = int(np.prod(wl["shape"]))
+    stream = torch.cuda.Stream()
+    ctx = _context(wl, n, w, stream=stream.cuda_stream)
+    ctx.set_intensity(wlmod.initial_intensity(wl, M))
+    ctx.set_material(wl["rho"], wl["T"], wl["v"], wl["sa"], wl["ss"])
+    dt = ctx.cfl_dt()
+    velocity = bool(np.any(wl["v"] != 0)) or wl["estimate_v"]
+    rs = 8 if wl["precision"] == "fp64" else 4
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # warm-up
+    for _ in range(args.warmup):
+        ctx.step(dt)
+    ctx.sync()
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local)
+    with sampler:
+        barrier()
+        torch.cuda.synchronize()
+        t_all0.record(stream)
+        for k in range(args.steps):
+            starts[k].record(stream)
+            ctx.step(dt)
+            ends[k].record(stream)
+        t_all1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ctx.sync()
+    total_ms = t_all0.elapsed_time(t_all1)
+    launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    units_per_step = N * M
+    value = units_per_step * args.steps * world / (total_ms / 1e3)
+
+    bytes_per_launch = algorithmic_bytes_per_cell(M, rs, velocity, not wl["hold_T"]) * N
+    avg_launch_s = statistics.mean(launch_ms) / 1e3
+    peak, peak_kind = _peaks()
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    traffic = _profile_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
+                "kernel": "step_kernel<float,3,true>"}
+
+    # end to end through the C ABI with host buffers: per step the gas
+    # fields go host->device, the moments and sources come back
+    e2e = None
+    if not args.no_e2e:
+        e2e = _e2e(ctx, wl, N, M, stream, args, world)
+    clocks = sampler.summary()
+    ctx.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload, 2, 1, sample_n=max(args.cpu_sample_n, 48))
+        cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        line = {
+            "metric": "cell-angle updates/s", "value": value, "unit": "cell-angle updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if rs == 4 else "f64", "data": "synthetic",
+            "config": {"workload": "%s: %s cells x %d angles (%s), %s intensities, T live=%s, velocity=%s"
+                                   % (wl["name"], "x".join(str(s) for s in wl["shape"][::-1]), M, wl["angles"],
+                                      wl["precision"], not wl["hold_T"], velocity),
+                       "cells": N, "angles": M, "dt": dt,
+                       "l2": "inputs larger than L2: %.2f GB of intensity read per step" % (N * M * rs / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def _e2e(ctx, wl, N, M, stream, args, world):
+    import torch
+    pin = lambda shape: torch.zeros(shape, dtype=torch.float64, pin_memory=True).numpy()
+    rho, T, v, sa, ss = pin(N), pin(N), pin((3, N)), pin(N), pin(N)
+    rho[:] = wl["rho"]; T[:] = wl["T"]; v[:] = wl["v"]; sa[:] = wl["sa"]; ss[:] = wl["ss"]
+    E, F, P = pin(N), pin((3, N)), pin((6, N))
+    dE, dM = pin(N), pin((3, N))
+    import paper_1403_6126_gb300 as rt
+
+    def one():
+        rt.rt_set_material(ctx.ctx, rho, T, v, sa, ss)
+        rt.rt_step(ctx.ctx, 0.0)
+        rt.rt_moments(ctx.ctx, E, F, P)
+        rt.rt_sources(ctx.ctx, dE, dM, T)
+
+    for _ in range(max(1, args.warmup)):
+        one()
+    torch.cuda.synchronize()
+    k = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(k):
+        one()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([el], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    h2d = 7 * N * 8
+    d2h = (10 + 1 + 3 + 1) * N * 8
+    return {"value": N * M * k * world / el, "unit": "cell-angle updates/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": k, "ms_per_step": 1e3 * el / k}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="box3d")
+    ap.add_argument("--n", type=int, default=0, help="box3d side (default 128)")
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-n", type=int, default=32)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gpu":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

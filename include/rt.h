@@ -1,0 +1,195 @@
+/*
+ * rt.h -- C ABI of the GB300 radiation-transfer step library.
+ *
+ * The library advances the frequency-integrated specific intensity
+ * I(x, n_m) of Jiang, Stone & Davis (2014, arXiv:1403.6126) by one time step
+ * on a Cartesian grid, on one GPU:
+ *   transport   (sec. 4.2, eqs. decomposeI and transporttwoterms, the alpha
+ *                factor, van Leer faces as eq. 4 of Stone & Mihalas 1992)
+ *   velocity    (sec. 4.5, the half-step estimate v~)
+ *   absorption  (sec. 4.3, eq. absorptionmatrix, implicit with the T^4 gas
+ *                energy exchange)
+ *   scattering  (sec. 4.4, the matrix M_s, implicit)
+ *   quadrature  (sec. 3: E_r = 4 pi sum W I, F_r = 4 pi sum W n I,
+ *                P_r = 4 pi sum W n n I) and the gas source terms
+ *                (eqs. momentumchange and kinetichange).
+ * All quantities are dimensionless as in sec. 2 (eq. RTequation): Crat is
+ * the speed of light, Prat the radiation-to-gas pressure ratio.  The MHD
+ * update (Steps 6-7 of sec. 4.1) is the caller's: density, temperature and
+ * velocity enter as given fields.
+ *
+ * Conventions for every call:
+ *  - Arrays are plain pointers.  Cell arrays have N = n[0]*n[1]*n[2] entries,
+ *    x fastest: cell (i, j, k) is at i + n[0]*(j + n[1]*k).  Vector fields
+ *    are component-major: v[d*N + c].  The pressure tensor is P[q*N + c]
+ *    with q = xx, yy, zz, xy, xz, yz.  Intensities are angle-major:
+ *    I[m*N + c], angles in the caller's order.
+ *  - Host pointers unless rt_options.device_ptrs is set, in which case every
+ *    array argument of rt_set_material / rt_set_intensity / rt_moments /
+ *    rt_sources / rt_get_intensity is a device pointer (doubles) valid on
+ *    the context's device; the call reads or writes it on the context's
+ *    stream and returns when the work is queued (stream-ordered).
+ *  - The caller owns every array it passes; the library copies what it keeps.
+ *    The library owns contexts, servers and all device state they hold.
+ *  - Every call returns an rt_status and never aborts the process.  On an
+ *    error the context is left as it was before the call (except RT_E_CUDA,
+ *    after which the context should be destroyed) and rt_last_error() gives
+ *    a message for the calling thread.
+ */
+#ifndef RT_GB300_H
+#define RT_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RT_OK = 0,
+  RT_PENDING = 1,       /* rt_poll: the solve has not finished yet           */
+  RT_E_INVALID = -1,    /* bad argument (size, NULL, non-unit n, sum W != 1) */
+  RT_E_NOMEM = -2,      /* device or host allocation failed                  */
+  RT_E_BUDGET = -3,     /* request larger than the server's HBM budget       */
+  RT_E_CUDA = -4,       /* a CUDA call failed                                */
+  RT_E_NONFINITE = -5,  /* non-finite input, or the T^4 Newton did not converge */
+  RT_E_TIMEOUT = -6,    /* rt_poll timed out                                 */
+  RT_E_STATE = -7       /* call out of order (e.g. rt_step before material)  */
+} rt_status;
+
+/* Boundary kinds (the setups of sec. 5): PERIODIC wraps; VACUUM copies
+ * outgoing rays and zeroes incoming ones (sec. 5.3 top); COPY copies all
+ * rays from the last active cell (sec. 5.3 bottom, sec. 5.8 right side);
+ * INFLOW copies outgoing rays and sets incoming ones to per-angle values
+ * given by rt_set_inflow (sec. 5.8 beams). */
+enum { RT_BC_PERIODIC = 0, RT_BC_VACUUM = 1, RT_BC_COPY = 2, RT_BC_INFLOW = 3 };
+
+/* Storage precision of the intensity.  RT_FP64: everything in double.
+ * RT_FP32: intensities, transport and angle sums in float (compensated
+ * sums), the T^4 solve finished in double, T and the gas energy source in
+ * double.  RT_BF16 is reserved and rejected with RT_E_INVALID. */
+enum { RT_FP64 = 0, RT_FP32 = 1, RT_BF16 = 2 };
+
+/* Angle-set generators for rt_angle_set. */
+enum { RT_ANGLES_LEVEL_SYMMETRIC = 0,  /* S_N, order N in {2,4,6,8}: N(N+2) angles */
+       RT_ANGLES_GAUSS_LEGENDRE = 1,   /* 1-D slab, order = number of angles (1..64) */
+       RT_ANGLES_PAPER_S4 = 2 };       /* 24 angles, mu_1 = 1/3 (sec. 5.2)   */
+
+typedef struct rt_ctx rt_ctx;
+
+/* Grid.  dim = 1, 2 or 3 active axes (x, then y, then z); n[d] cells on
+ * axis d (1 on inactive axes); the domain is [lo[d], hi[d]] so the cell
+ * size is (hi - lo) / n.  bc[d][0] / bc[d][1] are the lower / upper faces
+ * of active axes (ignored on inactive ones). */
+typedef struct {
+  int dim;
+  int n[3];
+  double lo[3], hi[3];
+  int bc[3][2];
+} rt_grid;
+
+/* Angle set (sec. 3): m unit vectors n[3*l + d] and weights w[l].  The
+ * weights must sum to 1 (J = sum W I is the mean intensity, E_r = 4 pi J)
+ * and each |n| must be 1, both to 1e-12; host memory, copied by rt_create. */
+typedef struct {
+  int m;
+  const double *n;
+  const double *w;
+} rt_angles;
+
+/* Options.  Defaults (rt_options_default): RT_FP32, cfl 0.4 (Step 1 of
+ * sec. 4.1), gamma 5/3, r_ideal 1, hold_T 0, estimate_v 1, device_ptrs 0,
+ * stream NULL (the legacy default stream). */
+typedef struct {
+  int precision;
+  double cfl;        /* dt = cfl * min dx / Crat when rt_step gets dt <= 0      */
+  double gamma;      /* adiabatic index: E_g = rho R_ideal T / (gamma - 1)      */
+  double r_ideal;
+  int hold_T;        /* 1: gas temperature held fixed (secs. 5.3, 5.8)        */
+  int estimate_v;    /* 1: use the sec. 4.5 half-step velocity in Steps 4-5   */
+  int device_ptrs;   /* 1: array arguments are device pointers               */
+  void *stream;      /* cudaStream_t the context launches on                  */
+} rt_options;
+
+/* Fills *o with the defaults above.  RT_E_INVALID if o is NULL. */
+rt_status rt_options_default(rt_options *o);
+
+/* Writes an angle set (sec. 3) into n_out[3*m] and w_out[m] (host memory,
+ * capacity `cap` angles) and its size into *m_out.  LEVEL_SYMMETRIC: the
+ * LQ_N construction (Carlson 1963) with mu_1 and the class weights fixed by
+ * normalisation and the even moments <mu^2k> = 1/(2k+1); the set satisfies
+ * sum W = 1, sum W n = 0, sum W n n = I/3.  GAUSS_LEGENDRE: mu at the
+ * Gauss-Legendre nodes, weights w_GL/2, n = (mu, sqrt(1-mu^2), 0).
+ * RT_E_INVALID for an unknown kind/order or too small a capacity. */
+rt_status rt_angle_set(int kind, int order, int cap, int *m_out, double *n_out, double *w_out);
+
+/* Creates a context on the current CUDA device: validates the grid and the
+ * angle set, allocates the device state (two intensity buffers of M*N
+ * values, the material, T, moments and sources; about (2*M*s + 200) bytes
+ * per cell, s = 8 for RT_FP64 and 4 for RT_FP32).  Crat, Prat > 0.
+ * On success *out owns the state until rt_destroy. */
+rt_status rt_create(const rt_grid *grid, const rt_angles *angles, double Crat, double Prat,
+                    const rt_options *opts, rt_ctx **out);
+
+/* Sets the gas fields for the following steps (sec. 2: rho, T, v; the
+ * attenuation coefficients sigma_a, sigma_s).  rho, T, sigma_a, sigma_s:
+ * N values; v: 3N (component-major).  Requires rho > 0, T > 0,
+ * sigma >= 0, all finite (RT_E_NONFINITE / RT_E_INVALID otherwise).  The
+ * first call also sets I to the isotropic equilibrium T^4/(4 pi) unless
+ * rt_set_intensity was called before. */
+rt_status rt_set_material(rt_ctx *ctx, const double *rho, const double *T, const double *v,
+                          const double *sigma_a, const double *sigma_s);
+
+/* Sets I (M*N values, angle-major).  NULL sets the isotropic equilibrium
+ * I = T^4/(4 pi) from the current temperature (needs rt_set_material).
+ * Recomputes E_r, F_r, P_r of the new field. */
+rt_status rt_set_intensity(rt_ctx *ctx, const double *I);
+
+/* Incoming intensities (M values) for a face with bc == RT_BC_INFLOW:
+ * axis 0..dim-1, side 0 (lower) or 1 (upper).  Only rays entering the
+ * domain through that face use them.  Host memory always. */
+rt_status rt_set_inflow(rt_ctx *ctx, int axis, int side, const double *I_ghost);
+
+/* Step 1 of sec. 4.1: the time step cfl * min_d dx_d / Crat. */
+double rt_cfl_dt(const rt_ctx *ctx);
+
+/* One radiation step of length dt (dt <= 0: rt_cfl_dt).  Steps 2-5 of
+ * sec. 4.1 plus the quadrature, fused on the device.  Updates I and T,
+ * stores E_r, F_r, P_r of the new intensity and the gas sources of the step.
+ * Stream-ordered: returns once the work is queued.  RT_E_STATE before
+ * rt_set_material. */
+rt_status rt_step(rt_ctx *ctx, double dt);
+
+/* nsteps calls of rt_step with the same dt, launched through one captured
+ * CUDA graph (no host work between steps). */
+rt_status rt_run(rt_ctx *ctx, double dt, int nsteps);
+
+/* Waits for the context's stream and reports the status of the steps run
+ * since the last check: RT_E_NONFINITE if a cell's T^4 Newton iteration did
+ * not converge, else RT_OK. */
+rt_status rt_sync(rt_ctx *ctx);
+
+/* E_r (N), F_r (3N), P_r (6N) of the current intensity (sec. 3 quadrature).
+ * Any pointer may be NULL to skip that field.  Host pointers: the call
+ * waits for the stream. */
+rt_status rt_moments(rt_ctx *ctx, double *E, double *F, double *P);
+
+/* Gas sources of the last step (eqs. momentumchange, kinetichange and the
+ * Delta E_T of sec. 4.3): dE_gas = Delta E_T + Delta E_K (N),
+ * dMom = Delta(rho v) (3N), T_new = T^{n+1} (N).  NULL skips a field. */
+rt_status rt_sources(rt_ctx *ctx, double *dE_gas, double *dMom, double *T_new);
+
+/* Copies the current intensity out (M*N values, angle-major). */
+rt_status rt_get_intensity(rt_ctx *ctx, double *I);
+
+/* Frees the context and its device state.  NULL is ignored. */
+void rt_destroy(rt_ctx *ctx);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *rt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RT_GB300_H */

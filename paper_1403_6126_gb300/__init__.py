@@ -1,0 +1,290 @@
+"""GB300 radiation-transfer step (Jiang, Stone & Davis 2014, arXiv:1403.6126).
+
+Thin Python binding over the C ABI declared in ``include/rt.h``: the
+functions below carry the C names and only marshal arguments (numpy arrays
+for host memory, torch CUDA tensors for device memory).  Every step of the
+method runs in the CUDA library ``librt_gb300.so`` built from ``csrc/``;
+there is no CPU fallback, and importing the binding fails loudly when the
+library has not been built.
+
+Array conventions (as in rt.h): cell fields (nz, ny, nx) or flat N, x
+fastest; vectors component-major (3, N); pressure (6, N) ordered xx, yy, zz,
+xy, xz, yz; intensities angle-major (M, N).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librt_gb300.so")
+
+RT_OK, RT_PENDING = 0, 1
+RT_E_INVALID, RT_E_NOMEM, RT_E_BUDGET, RT_E_CUDA, RT_E_NONFINITE, RT_E_TIMEOUT, RT_E_STATE = -1, -2, -3, -4, -5, -6, -7
+RT_BC_PERIODIC, RT_BC_VACUUM, RT_BC_COPY, RT_BC_INFLOW = 0, 1, 2, 3
+RT_FP64, RT_FP32, RT_BF16 = 0, 1, 2
+RT_ANGLES_LEVEL_SYMMETRIC, RT_ANGLES_GAUSS_LEGENDRE, RT_ANGLES_PAPER_S4 = 0, 1, 2
+
+_STATUS_NAMES = {0: "RT_OK", 1: "RT_PENDING", -1: "RT_E_INVALID", -2: "RT_E_NOMEM", -3: "RT_E_BUDGET",
+                 -4: "RT_E_CUDA", -5: "RT_E_NONFINITE", -6: "RT_E_TIMEOUT", -7: "RT_E_STATE"}
+
+
+class rt_grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3),
+                ("hi", ctypes.c_double * 3), ("bc", (ctypes.c_int * 2) * 3)]
+
+
+class rt_angles(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("n", ctypes.POINTER(ctypes.c_double)), ("w", ctypes.POINTER(ctypes.c_double))]
+
+
+class rt_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("cfl", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("r_ideal", ctypes.c_double), ("hold_T", ctypes.c_int), ("estimate_v", ctypes.c_int),
+                ("device_ptrs", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class RTError(RuntimeError):
+    def __init__(self, status, where, msg):
+        super().__init__("%s: %s (%s)" % (where, _STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+_DP = ctypes.POINTER(ctypes.c_double)
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("librt_gb300.so is missing: run paper_1403_6126_gb300/build.py "
+                              "(or __graft_entry__.build()) first; there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        V, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        sig = {
+            "rt_options_default": (I, [ctypes.POINTER(rt_options)]),
+            "rt_angle_set": (I, [I, I, I, ctypes.POINTER(I), _DP, _DP]),
+            "rt_create": (I, [ctypes.POINTER(rt_grid), ctypes.POINTER(rt_angles), D, D,
+                              ctypes.POINTER(rt_options), ctypes.POINTER(V)]),
+            "rt_set_material": (I, [V, V, V, V, V, V]),
+            "rt_set_intensity": (I, [V, V]),
+            "rt_set_inflow": (I, [V, I, I, _DP]),
+            "rt_cfl_dt": (D, [V]),
+            "rt_step": (I, [V, D]),
+            "rt_run": (I, [V, D, I]),
+            "rt_sync": (I, [V]),
+            "rt_moments": (I, [V, V, V, V]),
+            "rt_sources": (I, [V, V, V, V]),
+            "rt_get_intensity": (I, [V, V]),
+            "rt_destroy": (None, [V]),
+            "rt_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status, where):
+    if status != RT_OK:
+        raise RTError(status, where, lib().rt_last_error().decode(errors="replace"))
+    return status
+
+
+def _ptr(a):
+    """Address of a C-contiguous float64 numpy array or torch tensor (or None)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous() or str(a.dtype) != "torch.float64":
+            raise ValueError("device arrays must be contiguous float64 tensors")
+        return a.data_ptr()
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+        raise ValueError("host arrays must be C-contiguous float64 numpy arrays")
+    return a.ctypes.data
+
+
+# ---- the C ABI, one Python function per entry point ------------------------
+
+def rt_options_default():
+    o = rt_options()
+    _check(lib().rt_options_default(ctypes.byref(o)), "rt_options_default")
+    return o
+
+
+def rt_angle_set(kind, order):
+    """Returns (n [M,3], w [M]) from the library's generator."""
+    cap = 512
+    n = np.zeros((cap, 3))
+    w = np.zeros(cap)
+    m = ctypes.c_int(0)
+    _check(lib().rt_angle_set(kind, order, cap, ctypes.byref(m), n.ctypes.data_as(_DP), w.ctypes.data_as(_DP)),
+           "rt_angle_set")
+    return n[: m.value].copy(), w[: m.value].copy()
+
+
+def rt_create(grid, angles, Crat, Prat, opts):
+    out = ctypes.c_void_p()
+    _check(lib().rt_create(ctypes.byref(grid), ctypes.byref(angles), Crat, Prat, ctypes.byref(opts),
+                           ctypes.byref(out)), "rt_create")
+    return out
+
+
+def rt_set_material(ctx, rho, T, v, sigma_a, sigma_s):
+    _check(lib().rt_set_material(ctx, _ptr(rho), _ptr(T), _ptr(v), _ptr(sigma_a), _ptr(sigma_s)), "rt_set_material")
+
+
+def rt_set_intensity(ctx, I):
+    _check(lib().rt_set_intensity(ctx, _ptr(I)), "rt_set_intensity")
+
+
+def rt_set_inflow(ctx, axis, side, I_ghost):
+    I_ghost = np.ascontiguousarray(I_ghost, dtype=np.float64)
+    _check(lib().rt_set_inflow(ctx, axis, side, I_ghost.ctypes.data_as(_DP)), "rt_set_inflow")
+
+
+def rt_cfl_dt(ctx):
+    return lib().rt_cfl_dt(ctx)
+
+
+def rt_step(ctx, dt):
+    _check(lib().rt_step(ctx, dt), "rt_step")
+
+
+def rt_run(ctx, dt, nsteps):
+    _check(lib().rt_run(ctx, dt, nsteps), "rt_run")
+
+
+def rt_sync(ctx):
+    _check(lib().rt_sync(ctx), "rt_sync")
+
+
+def rt_moments(ctx, E, F, P):
+    _check(lib().rt_moments(ctx, _ptr(E), _ptr(F), _ptr(P)), "rt_moments")
+
+
+def rt_sources(ctx, dE_gas, dMom, T_new):
+    _check(lib().rt_sources(ctx, _ptr(dE_gas), _ptr(dMom), _ptr(T_new)), "rt_sources")
+
+
+def rt_get_intensity(ctx, I):
+    _check(lib().rt_get_intensity(ctx, _ptr(I)), "rt_get_intensity")
+
+
+def rt_destroy(ctx):
+    lib().rt_destroy(ctx)
+
+
+def rt_last_error():
+    return lib().rt_last_error().decode(errors="replace")
+
+
+# ---- convenience wrapper (argument marshalling only) ----------------------
+
+class Context:
+    """Owns one rt_ctx.  shape = (nz, ny, nx); lo/hi per axis (x, y, z);
+    bc = ((x_lo, x_hi), (y_lo, y_hi), (z_lo, z_hi)); n, w the angle set."""
+
+    def __init__(self, shape, n, w, Crat, Prat, dim=None, lo=(0, 0, 0), hi=(1, 1, 1), bc=None,
+                 precision=RT_FP32, cfl=0.4, gamma=5.0 / 3.0, r_ideal=1.0, hold_T=False, estimate_v=True,
+                 device_ptrs=False, stream=None):
+        nz, ny, nx = shape
+        self.shape = (nz, ny, nx)
+        self.dim = dim if dim is not None else (3 if nz > 1 else (2 if ny > 1 else 1))
+        g = rt_grid()
+        g.dim = self.dim
+        for d, nd in enumerate((nx, ny, nz)):
+            g.n[d] = nd
+            g.lo[d] = lo[d]
+            g.hi[d] = hi[d]
+        bc = bc or ((RT_BC_PERIODIC, RT_BC_PERIODIC),) * 3
+        for d in range(3):
+            g.bc[d][0], g.bc[d][1] = bc[d]
+        self._n = np.ascontiguousarray(n, dtype=np.float64).reshape(-1, 3)
+        self._w = np.ascontiguousarray(w, dtype=np.float64).reshape(-1)
+        self.M = len(self._w)
+        a = rt_angles()
+        a.m = self.M
+        a.n = self._n.ctypes.data_as(_DP)
+        a.w = self._w.ctypes.data_as(_DP)
+        o = rt_options_default()
+        o.precision, o.cfl, o.gamma, o.r_ideal = precision, cfl, gamma, r_ideal
+        o.hold_T, o.estimate_v, o.device_ptrs = int(hold_T), int(estimate_v), int(device_ptrs)
+        o.stream = stream
+        self.device_ptrs = bool(device_ptrs)
+        self.ctx = rt_create(g, a, float(Crat), float(Prat), o)
+
+    @property
+    def N(self):
+        nz, ny, nx = self.shape
+        return nz * ny * nx
+
+    def _host(self, a, count):
+        if self.device_ptrs:
+            return a
+        a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+        if a.size != count:
+            raise ValueError("expected %d values, got %d" % (count, a.size))
+        return a
+
+    def set_material(self, rho, T, v, sigma_a, sigma_s):
+        N = self.N
+        self._keep = [self._host(rho, N), self._host(T, N), self._host(v, 3 * N), self._host(sigma_a, N),
+                      self._host(sigma_s, N)]
+        rt_set_material(self.ctx, *self._keep)
+
+    def set_intensity(self, I=None):
+        rt_set_intensity(self.ctx, None if I is None else self._host(I, self.M * self.N))
+
+    def set_inflow(self, axis, side, I_ghost):
+        rt_set_inflow(self.ctx, axis, side, I_ghost)
+
+    def cfl_dt(self):
+        return rt_cfl_dt(self.ctx)
+
+    def step(self, dt=0.0):
+        rt_step(self.ctx, dt)
+
+    def run(self, dt, nsteps):
+        rt_run(self.ctx, dt, nsteps)
+
+    def sync(self):
+        rt_sync(self.ctx)
+
+    def moments(self):
+        N = self.N
+        E, F, P = np.zeros(N), np.zeros((3, N)), np.zeros((6, N))
+        rt_moments(self.ctx, E, F, P)
+        return E, F, P
+
+    def sources(self):
+        N = self.N
+        dE, dM, T = np.zeros(N), np.zeros((3, N)), np.zeros(N)
+        rt_sources(self.ctx, dE, dM, T)
+        return dE, dM, T
+
+    def intensity(self):
+        I = np.zeros((self.M, self.N))
+        rt_get_intensity(self.ctx, I)
+        return I
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            rt_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

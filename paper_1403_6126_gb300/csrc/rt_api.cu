@@ -1,0 +1,510 @@
+// C ABI runtime: contexts, device state, validation, launches and graphs.
+// The declarations and their documentation are in include/rt.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "rt.h"
+#include "rt_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+rt_status fail(rt_status s, const std::string &msg) {
+  g_last_error = msg;
+  return s;
+}
+
+rt_status cuda_fail(cudaError_t e, const char *what) {
+  return fail(RT_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define RT_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t _e = (call);                            \
+    if (_e != cudaSuccess) return cuda_fail(_e, #call); \
+  } while (0)
+
+}  // namespace
+
+struct rt_ctx {
+  int dim = 0, n[3] = {1, 1, 1}, M = 0;
+  long long N = 0;
+  double dx[3] = {1, 1, 1};
+  int bc[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  double C = 1, P = 1;
+  rt_options opt{};
+  cudaStream_t stream = nullptr;
+  bool fp64 = false;
+  size_t rs = 4;  // bytes per stored real
+  bool has_v = false, material_set = false, intensity_set = false;
+  rtg::TileShape tile{0, 0, 0};
+  // device state (Real = double or float)
+  void *I[2] = {nullptr, nullptr};
+  void *mom[2] = {nullptr, nullptr};
+  int cur = 0;
+  void *rho = nullptr, *sa = nullptr, *ss = nullptr, *v = nullptr;
+  double *T = nullptr, *dEgas = nullptr;
+  void *dMom = nullptr, *ang = nullptr, *inflow = nullptr;
+  int *flags = nullptr;  // [0] Newton failures, [1] input scan
+  double *stage = nullptr;
+  long long stage_len = 0;
+  std::vector<double> host_n, host_w, host_inflow;
+  // captured multi-step graph
+  cudaGraphExec_t graph = nullptr;
+  double graph_dt = 0;
+  int graph_steps = 0, graph_cur = -1;
+  bool graph_vel = false;
+};
+
+namespace {
+
+void free_all(rt_ctx *c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  void *ptrs[] = {c->I[0], c->I[1], c->mom[0], c->mom[1], c->rho, c->sa, c->ss, c->v,
+                  c->T, c->dEgas, c->dMom, c->ang, c->inflow, c->flags, c->stage};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+}
+
+template <typename Real>
+rtg::StepArgs<Real> make_args(rt_ctx *c, double dt) {
+  rtg::StepArgs<Real> a;
+  for (int d = 0; d < 3; ++d) {
+    a.n[d] = c->n[d];
+    a.bc[d][0] = c->bc[d][0];
+    a.bc[d][1] = c->bc[d][1];
+    a.dx[d] = (Real)c->dx[d];
+    a.dtdx[d] = (Real)(dt / c->dx[d]);
+  }
+  a.M = c->M;
+  a.N = c->N;
+  a.C = (Real)c->C;
+  a.invC = (Real)(1.0 / c->C);
+  a.P = (Real)c->P;
+  a.dt = (Real)dt;
+  a.dt_d = dt;
+  a.kv_per_rho = c->opt.r_ideal / (c->opt.gamma - 1.0);
+  a.hold_T = c->opt.hold_T;
+  a.estimate_v = c->opt.estimate_v;
+  a.ang = (const Real *)c->ang;
+  a.inflow = (const Real *)c->inflow;
+  a.I_in = (const Real *)c->I[c->cur];
+  a.I_out = (Real *)c->I[1 - c->cur];
+  a.rho = (const Real *)c->rho;
+  a.sa = (const Real *)c->sa;
+  a.ss = (const Real *)c->ss;
+  a.v = (const Real *)c->v;
+  a.T_in = c->T;
+  a.T_out = c->T;
+  a.mom_in = (const Real *)c->mom[c->cur];
+  a.mom_out = (Real *)c->mom[1 - c->cur];
+  a.dEgas = c->dEgas;
+  a.dMom = (Real *)c->dMom;
+  a.status = c->flags;
+  return a;
+}
+
+bool velocity_on(const rt_ctx *c) { return c->has_v || c->opt.estimate_v; }
+
+rt_status launch_step(rt_ctx *c, double dt) {
+  cudaError_t e;
+  bool vel = velocity_on(c);
+  if (c->fp64)
+    e = rtg::launch_step<double>(make_args<double>(c, dt), c->dim, vel, c->tile, c->stream);
+  else
+    e = rtg::launch_step<float>(make_args<float>(c, dt), c->dim, vel, c->tile, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+  c->cur = 1 - c->cur;
+  return RT_OK;
+}
+
+rt_status convert_in(rt_ctx *c, const double *src, void *dst, long long n) {
+  cudaError_t e = c->fp64 ? rtg::launch_convert_in<double>(src, (double *)dst, n, c->stream)
+                          : rtg::launch_convert_in<float>(src, (float *)dst, n, c->stream);
+  return e == cudaSuccess ? RT_OK : cuda_fail(e, "convert");
+}
+
+rt_status convert_out(rt_ctx *c, const void *src, double *dst, long long n) {
+  cudaError_t e = c->fp64 ? rtg::launch_convert_out<double>((const double *)src, dst, n, c->stream)
+                          : rtg::launch_convert_out<float>((const float *)src, dst, n, c->stream);
+  return e == cudaSuccess ? RT_OK : cuda_fail(e, "convert");
+}
+
+rt_status recompute_moments(rt_ctx *c) {
+  cudaError_t e = c->fp64 ? rtg::launch_moments<double>((const double *)c->I[c->cur], (const double *)c->ang, c->M,
+                                                        c->N, (double *)c->mom[c->cur], c->stream)
+                          : rtg::launch_moments<float>((const float *)c->I[c->cur], (const float *)c->ang, c->M,
+                                                       c->N, (float *)c->mom[c->cur], c->stream);
+  return e == cudaSuccess ? RT_OK : cuda_fail(e, "moments");
+}
+
+// Copies n doubles from the caller (host or device) into dst (device).
+rt_status fetch(rt_ctx *c, const double *src, double *dst, long long n) {
+  if (c->opt.device_ptrs) {
+    RT_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    RT_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  }
+  return RT_OK;
+}
+
+// Copies n doubles from the device buffer src to the caller.
+rt_status deliver(rt_ctx *c, const double *src, double *dst, long long n) {
+  if (c->opt.device_ptrs) {
+    RT_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    RT_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    RT_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  return RT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *rt_last_error(void) { return g_last_error.c_str(); }
+
+rt_status rt_options_default(rt_options *o) {
+  if (!o) return fail(RT_E_INVALID, "rt_options_default: NULL");
+  std::memset(o, 0, sizeof(*o));
+  o->precision = RT_FP32;
+  o->cfl = 0.4;
+  o->gamma = 5.0 / 3.0;
+  o->r_ideal = 1.0;
+  o->hold_T = 0;
+  o->estimate_v = 1;
+  o->device_ptrs = 0;
+  o->stream = nullptr;
+  return RT_OK;
+}
+
+rt_status rt_create(const rt_grid *g, const rt_angles *ang, double Crat, double Prat, const rt_options *opts,
+                    rt_ctx **out) {
+  if (!out) return fail(RT_E_INVALID, "rt_create: out is NULL");
+  *out = nullptr;
+  if (!g || !ang || !ang->n || !ang->w) return fail(RT_E_INVALID, "rt_create: NULL grid or angles");
+  if (g->dim < 1 || g->dim > 3) return fail(RT_E_INVALID, "rt_create: dim must be 1, 2 or 3");
+  long long N = 1;
+  for (int d = 0; d < 3; ++d) {
+    int nd = d < g->dim ? g->n[d] : 1;
+    if (d < g->dim) {
+      if (nd < 1) return fail(RT_E_INVALID, "rt_create: n[d] < 1 on an active axis");
+      if (!(g->hi[d] > g->lo[d]) || !std::isfinite(g->hi[d] - g->lo[d]))
+        return fail(RT_E_INVALID, "rt_create: hi <= lo on an active axis");
+      for (int s = 0; s < 2; ++s)
+        if (g->bc[d][s] < RT_BC_PERIODIC || g->bc[d][s] > RT_BC_INFLOW)
+          return fail(RT_E_INVALID, "rt_create: unknown boundary kind");
+      if ((g->bc[d][0] == RT_BC_PERIODIC) != (g->bc[d][1] == RT_BC_PERIODIC))
+        return fail(RT_E_INVALID, "rt_create: periodic must be set on both faces of an axis");
+    }
+    N *= nd;
+  }
+  if (N >= (1LL << 28)) return fail(RT_E_INVALID, "rt_create: more than 2^28 cells");
+  int M = ang->m;
+  if (M < 1 || M > rtg::kMaxAngles) return fail(RT_E_INVALID, "rt_create: angle count out of range (1..256)");
+  double wsum = 0;
+  for (int m = 0; m < M; ++m) {
+    const double *nm = ang->n + 3 * m;
+    double nn = nm[0] * nm[0] + nm[1] * nm[1] + nm[2] * nm[2];
+    if (!(std::fabs(std::sqrt(nn) - 1.0) <= 1e-12)) return fail(RT_E_INVALID, "rt_create: |n| != 1");
+    if (!(ang->w[m] > 0) || !std::isfinite(ang->w[m])) return fail(RT_E_INVALID, "rt_create: weight <= 0");
+    wsum += ang->w[m];
+  }
+  if (!(std::fabs(wsum - 1.0) <= 1e-12)) return fail(RT_E_INVALID, "rt_create: weights must sum to 1");
+  if (!(Crat > 0) || !(Prat > 0) || !std::isfinite(Crat) || !std::isfinite(Prat))
+    return fail(RT_E_INVALID, "rt_create: Crat and Prat must be positive");
+  rt_options o;
+  rt_options_default(&o);
+  if (opts) o = *opts;
+  if (o.precision != RT_FP64 && o.precision != RT_FP32)
+    return fail(RT_E_INVALID, "rt_create: precision must be RT_FP64 or RT_FP32");
+  if (!(o.cfl > 0) || !(o.gamma > 1.0) || !(o.r_ideal > 0))
+    return fail(RT_E_INVALID, "rt_create: need cfl > 0, gamma > 1, r_ideal > 0");
+
+  rt_ctx *c = new (std::nothrow) rt_ctx;
+  if (!c) return fail(RT_E_NOMEM, "rt_create: host allocation");
+  c->dim = g->dim;
+  for (int d = 0; d < 3; ++d) {
+    c->n[d] = d < g->dim ? g->n[d] : 1;
+    c->dx[d] = d < g->dim ? (g->hi[d] - g->lo[d]) / g->n[d] : 1.0;
+    c->bc[d][0] = d < g->dim ? g->bc[d][0] : RT_BC_PERIODIC;
+    c->bc[d][1] = d < g->dim ? g->bc[d][1] : RT_BC_PERIODIC;
+  }
+  c->N = N;
+  c->M = M;
+  c->C = Crat;
+  c->P = Prat;
+  c->opt = o;
+  c->stream = (cudaStream_t)o.stream;
+  c->fp64 = o.precision == RT_FP64;
+  c->rs = c->fp64 ? 8 : 4;
+  c->host_n.assign(ang->n, ang->n + 3 * M);
+  c->host_w.assign(ang->w, ang->w + M);
+  c->host_inflow.assign(6 * (size_t)M, 0.0);
+  bool ok = c->fp64 ? rtg::choose_tile<double>(c->dim, M, true, &c->tile)
+                    : rtg::choose_tile<float>(c->dim, M, true, &c->tile);
+  if (!ok) {
+    delete c;
+    return fail(RT_E_INVALID, "rt_create: too many angles for one CTA's shared memory");
+  }
+  size_t rs = c->rs;
+  c->stage_len = std::max<long long>(10 * N, (long long)8 * M);
+  const size_t Nz = (size_t)N, Mz = (size_t)M;
+  struct {
+    void **p;
+    size_t bytes;
+  } allocs[] = {
+      {&c->I[0], rs * Mz * Nz},  {&c->I[1], rs * Mz * Nz},         {&c->mom[0], rs * 10 * Nz},
+      {&c->mom[1], rs * 10 * Nz}, {&c->rho, rs * Nz},               {&c->sa, rs * Nz},
+      {&c->ss, rs * Nz},         {&c->v, rs * 3 * Nz},             {(void **)&c->T, 8 * Nz},
+      {(void **)&c->dEgas, 8 * Nz}, {&c->dMom, rs * 3 * Nz},       {&c->ang, rs * 4 * Mz},
+      {&c->inflow, rs * 6 * Mz}, {(void **)&c->flags, 2 * sizeof(int)},
+      {(void **)&c->stage, sizeof(double) * (size_t)c->stage_len},
+  };
+  for (auto &a : allocs) {
+    if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
+      cudaGetLastError();
+      free_all(c);
+      delete c;
+      return fail(RT_E_NOMEM, "rt_create: device allocation failed");
+    }
+  }
+  // angle table [M][4] = (n_x, n_y, n_z, W) and zero inflow, via the stage
+  std::vector<double> tab(4 * (size_t)M);
+  for (int m = 0; m < M; ++m) {
+    for (int d = 0; d < 3; ++d) tab[4 * m + d] = ang->n[3 * m + d];
+    tab[4 * m + 3] = ang->w[m];
+  }
+  rt_status st = RT_OK;
+  cudaError_t e = cudaMemcpyAsync(c->stage, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) st = convert_in(c, c->stage, c->ang, 4 * M);
+  if (e == cudaSuccess && st == RT_OK) e = cudaMemsetAsync(c->inflow, 0, rs * 6 * M, c->stream);
+  if (e == cudaSuccess && st == RT_OK) e = cudaMemsetAsync(c->flags, 0, 2 * sizeof(int), c->stream);
+  if (e == cudaSuccess && st == RT_OK) e = cudaMemsetAsync(c->dEgas, 0, 8 * N, c->stream);
+  if (e == cudaSuccess && st == RT_OK) e = cudaMemsetAsync(c->dMom, 0, rs * 3 * N, c->stream);
+  if (e == cudaSuccess && st == RT_OK) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess || st != RT_OK) {
+    free_all(c);
+    delete c;
+    return e != cudaSuccess ? cuda_fail(e, "rt_create") : st;
+  }
+  *out = c;
+  return RT_OK;
+}
+
+rt_status rt_set_material(rt_ctx *c, const double *rho, const double *T, const double *v, const double *sa,
+                          const double *ss) {
+  if (!c || !rho || !T || !v || !sa || !ss) return fail(RT_E_INVALID, "rt_set_material: NULL argument");
+  const long long N = c->N;
+  if (c->stage_len < 7 * N) return fail(RT_E_STATE, "rt_set_material: staging buffer too small");
+  double *s_rho = c->stage, *s_T = c->stage + N, *s_v = c->stage + 2 * N, *s_sa = c->stage + 5 * N,
+         *s_ss = c->stage + 6 * N;
+  rt_status st;
+  if ((st = fetch(c, rho, s_rho, N)) != RT_OK) return st;
+  if ((st = fetch(c, T, s_T, N)) != RT_OK) return st;
+  if ((st = fetch(c, v, s_v, 3 * N)) != RT_OK) return st;
+  if ((st = fetch(c, sa, s_sa, N)) != RT_OK) return st;
+  if ((st = fetch(c, ss, s_ss, N)) != RT_OK) return st;
+  // scan: bit 0 = a value out of range or non-finite, bit 1 = some v != 0
+  RT_CUDA(cudaMemsetAsync(c->flags + 1, 0, sizeof(int), c->stream));
+  RT_CUDA(rtg::launch_check(s_rho, N, 0.0, 1, 0, c->flags + 1, c->stream));
+  RT_CUDA(rtg::launch_check(s_T, N, 0.0, 1, 0, c->flags + 1, c->stream));
+  RT_CUDA(rtg::launch_check(s_sa, N, 0.0, 0, 0, c->flags + 1, c->stream));
+  RT_CUDA(rtg::launch_check(s_ss, N, 0.0, 0, 0, c->flags + 1, c->stream));
+  RT_CUDA(rtg::launch_check(s_v, 3 * N, -INFINITY, 0, 2, c->flags + 1, c->stream));
+  int flag = 0;
+  RT_CUDA(cudaMemcpyAsync(&flag, c->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  RT_CUDA(cudaStreamSynchronize(c->stream));
+  if (flag & 1) return fail(RT_E_NONFINITE, "rt_set_material: need finite rho > 0, T > 0, sigma >= 0, v");
+  if ((st = convert_in(c, s_rho, c->rho, N)) != RT_OK) return st;
+  if ((st = convert_in(c, s_sa, c->sa, N)) != RT_OK) return st;
+  if ((st = convert_in(c, s_ss, c->ss, N)) != RT_OK) return st;
+  if ((st = convert_in(c, s_v, c->v, 3 * N)) != RT_OK) return st;
+  RT_CUDA(cudaMemcpyAsync(c->T, s_T, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  c->has_v = (flag & 2) != 0;
+  c->material_set = true;
+  if (!c->intensity_set) return rt_set_intensity(c, nullptr);
+  return RT_OK;
+}
+
+rt_status rt_set_intensity(rt_ctx *c, const double *I) {
+  if (!c) return fail(RT_E_INVALID, "rt_set_intensity: NULL context");
+  const long long N = c->N;
+  if (!I) {
+    if (!c->material_set) return fail(RT_E_STATE, "rt_set_intensity(NULL) needs rt_set_material first");
+    cudaError_t e = c->fp64 ? rtg::launch_isotropic<double>(c->T, (double *)c->I[c->cur], c->M, N, c->stream)
+                            : rtg::launch_isotropic<float>(c->T, (float *)c->I[c->cur], c->M, N, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "isotropic");
+  } else {
+    // check everything first (finite, >= 0), then convert chunk by chunk
+    long long chunk = c->stage_len;
+    RT_CUDA(cudaMemsetAsync(c->flags + 1, 0, sizeof(int), c->stream));
+    for (long long off = 0; off < (long long)c->M * N; off += chunk) {
+      long long n = std::min(chunk, (long long)c->M * N - off);
+      rt_status st = fetch(c, I + off, c->stage, n);
+      if (st != RT_OK) return st;
+      RT_CUDA(rtg::launch_check(c->stage, n, 0.0, 0, 0, c->flags + 1, c->stream));
+    }
+    int flag = 0;
+    RT_CUDA(cudaMemcpyAsync(&flag, c->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    RT_CUDA(cudaStreamSynchronize(c->stream));
+    if (flag & 1) return fail(RT_E_NONFINITE, "rt_set_intensity: need finite I >= 0");
+    for (long long off = 0; off < (long long)c->M * N; off += chunk) {
+      long long n = std::min(chunk, (long long)c->M * N - off);
+      rt_status st = fetch(c, I + off, c->stage, n);
+      if (st != RT_OK) return st;
+      st = convert_in(c, c->stage, (char *)c->I[c->cur] + off * c->rs, n);
+      if (st != RT_OK) return st;
+    }
+  }
+  rt_status st = recompute_moments(c);
+  if (st != RT_OK) return st;
+  c->intensity_set = true;
+  return RT_OK;
+}
+
+rt_status rt_set_inflow(rt_ctx *c, int axis, int side, const double *I_ghost) {
+  if (!c || !I_ghost) return fail(RT_E_INVALID, "rt_set_inflow: NULL argument");
+  if (axis < 0 || axis >= c->dim || side < 0 || side > 1) return fail(RT_E_INVALID, "rt_set_inflow: bad face");
+  for (int m = 0; m < c->M; ++m)
+    if (!std::isfinite(I_ghost[m]) || I_ghost[m] < 0) return fail(RT_E_NONFINITE, "rt_set_inflow: need finite I >= 0");
+  std::copy(I_ghost, I_ghost + c->M, c->host_inflow.begin() + (size_t)(axis * 2 + side) * c->M);
+  RT_CUDA(cudaMemcpyAsync(c->stage, c->host_inflow.data(), 6 * c->M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  rt_status st = convert_in(c, c->stage, c->inflow, 6 * c->M);
+  if (st != RT_OK) return st;
+  RT_CUDA(cudaStreamSynchronize(c->stream));
+  return RT_OK;
+}
+
+double rt_cfl_dt(const rt_ctx *c) {
+  if (!c) return 0.0;
+  double h = c->dx[0];
+  for (int d = 1; d < c->dim; ++d) h = std::min(h, c->dx[d]);
+  return c->opt.cfl * h / c->C;
+}
+
+rt_status rt_step(rt_ctx *c, double dt) {
+  if (!c) return fail(RT_E_INVALID, "rt_step: NULL context");
+  if (!c->material_set) return fail(RT_E_STATE, "rt_step: call rt_set_material first");
+  if (!(dt > 0)) dt = rt_cfl_dt(c);
+  if (!std::isfinite(dt)) return fail(RT_E_INVALID, "rt_step: dt not finite");
+  return launch_step(c, dt);
+}
+
+rt_status rt_run(rt_ctx *c, double dt, int nsteps) {
+  if (!c) return fail(RT_E_INVALID, "rt_run: NULL context");
+  if (!c->material_set) return fail(RT_E_STATE, "rt_run: call rt_set_material first");
+  if (nsteps < 0) return fail(RT_E_INVALID, "rt_run: nsteps < 0");
+  if (nsteps == 0) return RT_OK;
+  if (!(dt > 0)) dt = rt_cfl_dt(c);
+  if (c->stream == nullptr) {
+    // the legacy default stream cannot be captured: plain launches
+    for (int k = 0; k < nsteps; ++k) {
+      rt_status st = launch_step(c, dt);
+      if (st != RT_OK) return st;
+    }
+    return RT_OK;
+  }
+  bool vel = velocity_on(c);
+  if (!c->graph || c->graph_dt != dt || c->graph_steps != nsteps || c->graph_cur != c->cur || c->graph_vel != vel) {
+    if (c->graph) {
+      cudaGraphExecDestroy(c->graph);
+      c->graph = nullptr;
+    }
+    int start = c->cur;
+    cudaGraph_t graph;
+    RT_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    rt_status st = RT_OK;
+    for (int k = 0; k < nsteps && st == RT_OK; ++k) st = launch_step(c, dt);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    c->cur = start;
+    if (st != RT_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "rt_run: capture");
+    e = cudaGraphInstantiate(&c->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "rt_run: instantiate");
+    c->graph_dt = dt;
+    c->graph_steps = nsteps;
+    c->graph_cur = start;
+    c->graph_vel = vel;
+  }
+  RT_CUDA(cudaGraphLaunch(c->graph, c->stream));
+  if (nsteps % 2) c->cur = 1 - c->cur;
+  return RT_OK;
+}
+
+rt_status rt_sync(rt_ctx *c) {
+  if (!c) return fail(RT_E_INVALID, "rt_sync: NULL context");
+  int bad = 0;
+  RT_CUDA(cudaMemcpyAsync(&bad, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  RT_CUDA(cudaStreamSynchronize(c->stream));
+  if (bad) {
+    RT_CUDA(cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream));
+    RT_CUDA(cudaStreamSynchronize(c->stream));
+    char msg[96];
+    std::snprintf(msg, sizeof msg, "T^4 Newton iteration failed in %d cell-steps", bad);
+    return fail(RT_E_NONFINITE, msg);
+  }
+  return RT_OK;
+}
+
+rt_status rt_moments(rt_ctx *c, double *E, double *F, double *P) {
+  if (!c) return fail(RT_E_INVALID, "rt_moments: NULL context");
+  if (!c->intensity_set) return fail(RT_E_STATE, "rt_moments: no intensity yet");
+  const long long N = c->N;
+  const char *mom = (const char *)c->mom[c->cur];
+  rt_status st;
+  if ((st = convert_out(c, mom, c->stage, 10 * N)) != RT_OK) return st;
+  if (E && (st = deliver(c, c->stage, E, N)) != RT_OK) return st;
+  if (F && (st = deliver(c, c->stage + N, F, 3 * N)) != RT_OK) return st;
+  if (P && (st = deliver(c, c->stage + 4 * N, P, 6 * N)) != RT_OK) return st;
+  return RT_OK;
+}
+
+rt_status rt_sources(rt_ctx *c, double *dE_gas, double *dMom, double *T_new) {
+  if (!c) return fail(RT_E_INVALID, "rt_sources: NULL context");
+  const long long N = c->N;
+  rt_status st;
+  if (dE_gas) {
+    RT_CUDA(cudaMemcpyAsync(c->stage, c->dEgas, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    if ((st = deliver(c, c->stage, dE_gas, N)) != RT_OK) return st;
+  }
+  if (dMom) {
+    if ((st = convert_out(c, c->dMom, c->stage, 3 * N)) != RT_OK) return st;
+    if ((st = deliver(c, c->stage, dMom, 3 * N)) != RT_OK) return st;
+  }
+  if (T_new) {
+    RT_CUDA(cudaMemcpyAsync(c->stage, c->T, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    if ((st = deliver(c, c->stage, T_new, N)) != RT_OK) return st;
+  }
+  return RT_OK;
+}
+
+rt_status rt_get_intensity(rt_ctx *c, double *I) {
+  if (!c || !I) return fail(RT_E_INVALID, "rt_get_intensity: NULL argument");
+  if (!c->intensity_set) return fail(RT_E_STATE, "rt_get_intensity: no intensity yet");
+  long long total = (long long)c->M * c->N, chunk = c->stage_len;
+  for (long long off = 0; off < total; off += chunk) {
+    long long n = std::min(chunk, total - off);
+    rt_status st = convert_out(c, (const char *)c->I[c->cur] + off * c->rs, c->stage, n);
+    if (st != RT_OK) return st;
+    if ((st = deliver(c, c->stage, I + off, n)) != RT_OK) return st;
+  }
+  return RT_OK;
+}
+
+void rt_destroy(rt_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,69 @@
+// Internal declarations shared by the host runtime and the device kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rtg {
+
+constexpr int kMaxAngles = 256;
+constexpr int kMomComps = 10;  // E, Fx, Fy, Fz, Pxx, Pyy, Pzz, Pxy, Pxz, Pyz
+
+// Everything one fused step launch needs.  Real is the intensity and
+// transport type (double for the FP64 path, float for the mixed path);
+// temperature and the gas energy source are always double.
+template <typename Real>
+struct StepArgs {
+  int n[3];           // cells per axis (1 on inactive axes)
+  int M;              // angles
+  long long N;        // cells
+  int bc[3][2];       // boundary kinds per axis / side
+  Real C, invC, P;    // Crat, 1/Crat, Prat
+  Real dt;            // time step
+  Real dtdx[3];       // dt / dx_d
+  Real dx[3];         // cell sizes
+  double dt_d, kv_per_rho;  // dt and R/(gamma-1) in double
+  int hold_T, estimate_v;
+  const Real *ang;    // [M][4]: n_x, n_y, n_z, W
+  const Real *inflow; // [3][2][M]
+  const Real *I_in;   // [M][N]
+  Real *I_out;        // [M][N]
+  const Real *rho, *sa, *ss;  // [N]
+  const Real *v;      // [3][N]
+  const double *T_in; // [N]
+  double *T_out;      // [N]
+  const Real *mom_in; // [10][N] moments of I_in
+  Real *mom_out;      // [10][N] moments of I_out
+  double *dEgas;      // [N]
+  Real *dMom;         // [3][N]
+  int *status;        // [0]: cells whose T Newton failed
+};
+
+struct TileShape {
+  int tx, ty, tz;
+};
+
+// Launch the fused step; returns the CUDA error of the launch.
+template <typename Real>
+cudaError_t launch_step(const StepArgs<Real> &a, int dim, bool has_v, TileShape tile, cudaStream_t s);
+
+// Pick a tile shape that fits shared memory for (dim, M, has_v); false if
+// even the smallest tile does not fit.
+template <typename Real>
+bool choose_tile(int dim, int M, bool has_v, TileShape *out);
+
+// Elementwise helpers (all stream-ordered).
+template <typename Real>
+cudaError_t launch_convert_in(const double *src, Real *dst, long long n, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_convert_out(const Real *src, double *dst, long long n, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_isotropic(const double *T, Real *I, int M, long long N, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_moments(const Real *I, const Real *ang, int M, long long N, Real *mom, cudaStream_t s);
+
+// Scans n doubles: ORs bit 0 into *flag for a non-finite value or one below
+// `lo` (or equal to it when strict), and ORs `nzbit` for a nonzero value.
+cudaError_t launch_check(const double *x, long long n, double lo, int strict, int nzbit, int *flag, cudaStream_t s);
+
+}  // namespace rtg

@@ -1,0 +1,112 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle on
+identical seeded inputs.  FP64 path: 1e-12 norm-relative on every output.
+Mixed path (FP32 intensities): 1e-5 on E_r and |F_r|, the bar for the
+mixed-precision path; the other outputs are reported against looser
+bounds derived from float32 storage."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1403_6126_gb300 import workloads as wlmod
+
+from _helpers import field_err, flux_magnitude, rel_err, run_both
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+MIXED_TOL = 1e-5
+
+
+def _check_fp64(g, o):
+    for k in ("I", "E", "F", "P", "T", "dEgas", "dMom"):
+        err = field_err(g, o, k, o["wl"])
+        assert err <= FP64_TOL, (k, err)
+
+
+def _check_mixed(g, o):
+    errE = rel_err(g["E"], o["E"])
+    errF = field_err({"F": flux_magnitude(g["F"])}, {"F": flux_magnitude(o["F"]), "E": o["E"]}, "F", o["wl"])
+    assert errE <= MIXED_TOL, ("E", errE)
+    assert errF <= MIXED_TOL, ("|F|", errF)
+    assert rel_err(g["T"], o["T"]) <= MIXED_TOL
+    assert rel_err(g["I"], o["I"]) <= 1e-4
+    # derived from float storage: the sources are differences of float sums
+    assert field_err(g, o, "dMom", o["wl"]) <= 1e-4
+    assert field_err(g, o, "dEgas", o["wl"]) <= 1e-4
+
+
+SMALL = [
+    ("slab1d", dict(n=64, steps=0), 30),
+    ("slab1d", dict(n=37, M=16, steps=0), 20),            # ragged tile, 16 angles
+    ("shadow2d", dict(nx=40, ny=24, angles="s4", steps=0), 15),
+    ("shadow2d", dict(nx=33, ny=17, angles="s8", steps=0), 6),
+    ("box3d", dict(n=12, angles="s4", steps=0), 5),
+    ("box3d", dict(n=10, angles="s8", steps=0), 3),
+]
+
+
+@pytest.mark.parametrize("name,kw,nsteps", SMALL)
+def test_fp64_matches_oracle(name, kw, nsteps):
+    wl = wlmod.by_name(name, **kw)
+    g, o = run_both(wl, nsteps, "fp64")
+    _check_fp64(g, o)
+
+
+@pytest.mark.parametrize("name,kw,nsteps", SMALL)
+def test_mixed_matches_oracle(name, kw, nsteps):
+    wl = wlmod.by_name(name, **kw)
+    g, o = run_both(wl, nsteps, "fp32")
+    _check_mixed(g, o)
+
+
+def test_box3d_ragged_many_tiles_fp64():
+    # several tiles in every direction plus a ragged tail on each axis
+    wl = wlmod.box3d(n=20, angles="s2", steps=0)
+    g, o = run_both(wl, 4, "fp64")
+    _check_fp64(g, o)
+
+
+def test_box3d_ragged_many_tiles_mixed():
+    wl = wlmod.box3d(n=37, angles="s4", steps=0)
+    g, o = run_both(wl, 3, "fp32", threads=8)
+    _check_mixed(g, o)
+
+
+def test_single_cell_and_single_angle():
+    # degenerate sizes: one cell (periodic onto itself) and one angle (W = 1)
+    wl = wlmod.slab1d(n=1, M=2, steps=0)
+    wl["bc"] = ((0, 0), (0, 0), (0, 0))
+    g, o = run_both(wl, 5, "fp64")
+    _check_fp64(g, o)
+    wl = wlmod.slab1d(n=19, M=2, steps=0)
+    n = np.array([[1.0, 0.0, 0.0]])
+    w = np.array([1.0])
+    g, o = run_both(wl, 4, "fp64", n=n, w=w)
+    _check_fp64(g, o)
+
+
+def test_many_angles():
+    # 256 random directions with random positive weights (the largest set)
+    rng = np.random.default_rng(7)
+    n = rng.normal(size=(256, 3))
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    w = rng.uniform(0.5, 1.5, 256)
+    w /= w.sum()
+    wl = wlmod.slab1d(n=70, steps=0)
+    g, o = run_both(wl, 3, "fp64", n=n, w=w)
+    _check_fp64(g, o)
+    g, o = run_both(wl, 3, "fp32", n=n, w=w)
+    _check_mixed(g, o)
+
+
+def test_pure_transport_and_opaque_limits():
+    # sigma = 0 everywhere (pure transport) and sigma = 1e6 (stiff sources)
+    wl = wlmod.shadow2d(nx=24, ny=20, angles="s4", steps=0)
+    wl["sa"] = np.zeros_like(wl["sa"])
+    g, o = run_both(wl, 10, "fp64")
+    _check_fp64(g, o)
+    wl = wlmod.box3d(n=8, angles="s2", steps=0)
+    wl["sa"] = np.full_like(wl["sa"], 1e6)
+    wl["ss"] = np.full_like(wl["ss"], 3e5)
+    g, o = run_both(wl, 3, "fp64")
+    _check_fp64(g, o)
