@@ -474,15 +474,24 @@ static int scattering_dense(const orc_problem *p, const cellstate *cs, const dou
  * and against 1 gives a 2x2 linear system for (s1, s2). */
 static int scattering_reduced(const orc_problem *p, const cellstate *cs, const double *r, double *I) {
   int M = p->M;
-  double Br = 0, B1 = 0, Bc = 0, Ar = 0, A1 = 0, Ac = 0;
+  double Br = 0, B1p = 0, Bc = 0, Ar = 0, A1 = 0, Ac = 0;
   for (int m = 0; m < M; ++m) {
     double a, b, c;
     scat_coeffs(p, cs, m, &a, &b, &c);
-    Br += b * r[m] / a; B1 += b / a; Bc += b * c / a;
+    Br += b * r[m] / a; Bc += b * c / a;
     Ar += r[m] / a; A1 += 1.0 / a; Ac += c / a;
+    /* 1 + B1 = sum_m W_m (1 + b_m / (W_m a_m)) since sum W = 1; the
+     * numerator W a + b = 1 + dt s_s vn - dt s_s (v.v + vn^2)/C has the
+     * dt C s_s terms of a and b cancelled exactly, which keeps the (1,1)
+     * entry accurate when dt C s_s >> 1 */
+    const double *n = p->mu + 3 * m;
+    double vn = n[0] * cs->v[0] + n[1] * cs->v[1] + n[2] * cs->v[2];
+    double v2 = cs->v[0] * cs->v[0] + cs->v[1] * cs->v[1] + cs->v[2] * cs->v[2];
+    double num = 1.0 + cs->dt * cs->ss * vn - cs->dt * cs->ss * (v2 + vn * vn) / p->C;
+    B1p += num / a;
   }
   /* (1 + B1) s1 + Bc s2 = Br ;  A1 s1 + (1 + Ac) s2 = Ar */
-  double m11 = 1.0 + B1, m12 = Bc, m21 = A1, m22 = 1.0 + Ac;
+  double m11 = B1p, m12 = Bc, m21 = A1, m22 = 1.0 + Ac;
   double det = m11 * m22 - m12 * m21;
   if (det == 0.0) return 1;
   double s1 = (Br * m22 - m12 * Ar) / det;
