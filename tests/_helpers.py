@@ -78,9 +78,10 @@ def natural_scale(o, key, wl):
     the radiation energy scale for E, F, P (|F_r| <= E_r), (P/C) E for the
     momentum source, P E for the gas energy source, the field itself for
     I and T."""
+    if key in ("I", "T"):
+        return float(np.abs(o[key]).max())
     E0 = float(np.abs(o["E"]).max())
-    return {"E": E0, "F": E0, "P": E0, "dMom": wl["P"] / wl["C"] * E0, "dEgas": wl["P"] * E0,
-            "I": float(np.abs(o["I"]).max()), "T": float(np.abs(o["T"]).max())}[key]
+    return {"E": E0, "F": E0, "P": E0, "dMom": wl["P"] / wl["C"] * E0, "dEgas": wl["P"] * E0}[key]
 
 
 def field_err(g, o, key, wl, floor=1e-3):
