@@ -30,7 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PROFILE = os.path.join(ROOT, "profiles", "step_kernel_box3d.md")
-KERNEL_SRC = os.path.join(ROOT, "paper_1403_6126_gb300", "csrc", "rt_step.cu")
+KERNEL_SRC = os.path.join(ROOT, "paper_1403_6126_gb300", "csrc", "rt_step_kernel.cuh")
 
 
 def algorithmic_bytes_per_cell(M, rs, velocity, live_T):
@@ -235,6 +235,9 @@ def run_gpu(args):
     ctx.set_intensity(wlmod.initial_intensity(wl, M))
     ctx.set_material(wl["rho"], wl["T"], wl["v"], wl["sa"], wl["ss"])
     dt = ctx.cfl_dt()
+    if args.tile:
+        ctx.set_tile(*[int(x) for x in args.tile.split("x")])
+    tile = ctx.tile()
     velocity = bool(np.any(wl["v"] != 0)) or wl["estimate_v"]
     rs = 8 if wl["precision"] == "fp64" else 4
 
@@ -286,7 +289,7 @@ def run_gpu(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
-                "kernel": "step_kernel<float,3,true>"}
+                "kernel": "step_kernel<float,3,true,%d,%d,%d>" % tile}
 
     # end to end through the C ABI with host buffers: per step the gas
     # fields go host->device, the moments and sources come back
@@ -362,6 +365,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="box3d")
     ap.add_argument("--n", type=int, default=0, help="box3d side (default 128)")
+    ap.add_argument("--tile", default="", help="tile shape TXxTYxTZ (default: the library's choice)")
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -150,6 +150,16 @@ rt_status rt_set_intensity(rt_ctx *ctx, const double *I);
  * domain through that face use them.  Host memory always. */
 rt_status rt_set_inflow(rt_ctx *ctx, int axis, int side, const double *I_ghost);
 
+/* Tile of cells one CTA of the step kernel owns (tx x ty x tz, one thread
+ * per cell; ty = 1 for 1-D, tz = 1 below 3-D).  (0, 0, 0) restores the
+ * default choice.  RT_E_INVALID when the shape exceeds the kernel's thread
+ * bound (512 for RT_FP32, 256 for RT_FP64), the 227 KB of shared memory
+ * (which grows with the angle count) or the staging capacity of its halo.
+ * Results do not depend on the tile; only speed does.  This is the hook
+ * the tile autotuner uses. */
+rt_status rt_set_tile(rt_ctx *ctx, int tx, int ty, int tz);
+rt_status rt_get_tile(const rt_ctx *ctx, int *tx, int *ty, int *tz);
+
 /* Step 1 of sec. 4.1: the time step cfl * min_d dx_d / Crat. */
 double rt_cfl_dt(const rt_ctx *ctx);
 

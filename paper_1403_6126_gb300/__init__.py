@@ -72,6 +72,8 @@ def lib():
             "rt_set_intensity": (I, [V, V]),
             "rt_set_inflow": (I, [V, I, I, _DP]),
             "rt_cfl_dt": (D, [V]),
+            "rt_set_tile": (I, [V, I, I, I]),
+            "rt_get_tile": (I, [V, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
             "rt_step": (I, [V, D]),
             "rt_run": (I, [V, D, I]),
             "rt_sync": (I, [V]),
@@ -145,6 +147,16 @@ def rt_set_intensity(ctx, I):
 def rt_set_inflow(ctx, axis, side, I_ghost):
     I_ghost = np.ascontiguousarray(I_ghost, dtype=np.float64)
     _check(lib().rt_set_inflow(ctx, axis, side, I_ghost.ctypes.data_as(_DP)), "rt_set_inflow")
+
+
+def rt_set_tile(ctx, tx, ty, tz):
+    _check(lib().rt_set_tile(ctx, tx, ty, tz), "rt_set_tile")
+
+
+def rt_get_tile(ctx):
+    t = [ctypes.c_int(0) for _ in range(3)]
+    _check(lib().rt_get_tile(ctx, *[ctypes.byref(x) for x in t]), "rt_get_tile")
+    return tuple(x.value for x in t)
 
 
 def rt_cfl_dt(ctx):
@@ -245,6 +257,12 @@ class Context:
 
     def cfl_dt(self):
         return rt_cfl_dt(self.ctx)
+
+    def set_tile(self, tx, ty, tz):
+        rt_set_tile(self.ctx, tx, ty, tz)
+
+    def tile(self):
+        return rt_get_tile(self.ctx)
 
     def step(self, dt=0.0):
         rt_step(self.ctx, dt)

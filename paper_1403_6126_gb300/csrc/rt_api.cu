@@ -383,6 +383,32 @@ rt_status rt_set_inflow(rt_ctx *c, int axis, int side, const double *I_ghost) {
   return RT_OK;
 }
 
+rt_status rt_set_tile(rt_ctx *c, int tx, int ty, int tz) {
+  if (!c) return fail(RT_E_INVALID, "rt_set_tile: NULL context");
+  rtg::TileShape t{tx, ty, tz};
+  if (tx == 0 && ty == 0 && tz == 0) {
+    bool ok = c->fp64 ? rtg::choose_tile<double>(c->dim, c->M, true, &t) : rtg::choose_tile<float>(c->dim, c->M, true, &t);
+    if (!ok) return fail(RT_E_INVALID, "rt_set_tile: no default tile fits");
+  } else {
+    bool ok = c->fp64 ? rtg::tile_ok<double>(c->dim, c->M, true, t) : rtg::tile_ok<float>(c->dim, c->M, true, t);
+    if (!ok) return fail(RT_E_INVALID, "rt_set_tile: shape exceeds the thread, shared-memory or staging limits");
+  }
+  c->tile = t;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return RT_OK;
+}
+
+rt_status rt_get_tile(const rt_ctx *c, int *tx, int *ty, int *tz) {
+  if (!c || !tx || !ty || !tz) return fail(RT_E_INVALID, "rt_get_tile: NULL argument");
+  *tx = c->tile.tx;
+  *ty = c->tile.ty;
+  *tz = c->tile.tz;
+  return RT_OK;
+}
+
 double rt_cfl_dt(const rt_ctx *c) {
   if (!c) return 0.0;
   double h = c->dx[0];

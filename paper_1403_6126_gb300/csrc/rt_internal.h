@@ -52,6 +52,12 @@ cudaError_t launch_step(const StepArgs<Real> &a, int dim, bool has_v, TileShape 
 template <typename Real>
 bool choose_tile(int dim, int M, bool has_v, TileShape *out);
 
+// Whether a tile shape can be launched: thread count within the kernel's
+// launch bound, shared memory within the opt-in limit, and enough staging
+// slots for its halo.
+template <typename Real>
+bool tile_ok(int dim, int M, bool has_v, TileShape t);
+
 // Elementwise helpers (all stream-ordered).
 template <typename Real>
 cudaError_t launch_convert_in(const double *src, Real *dst, long long n, cudaStream_t s);

@@ -1,0 +1,25 @@
+// Instantiations of the fused step kernel: double, all dimensions.
+#include "rt_shapes.h"
+#include "rt_step_kernel.cuh"
+
+namespace rtg {
+
+cudaError_t launch_d(const StepArgs<double> &a, int dim, bool vel, TileShape t, cudaStream_t s) {
+#define RT_CASE(D, X, Y, Z)                                                       \
+  if (dim == D && t.tx == X && t.ty == Y && t.tz == Z)                            \
+    return vel ? stepk::launch_shape<double, D, true, X, Y, Z>(a, s)              \
+               : stepk::launch_shape<double, D, false, X, Y, Z>(a, s);
+#define RT_CASE1(X, Y, Z) RT_CASE(1, X, Y, Z)
+#define RT_CASE2(X, Y, Z) RT_CASE(2, X, Y, Z)
+#define RT_CASE3(X, Y, Z) RT_CASE(3, X, Y, Z)
+  RT_SHAPES_D1(RT_CASE1)
+  RT_SHAPES_D2(RT_CASE2)
+  RT_SHAPES_D3(RT_CASE3)
+#undef RT_CASE1
+#undef RT_CASE2
+#undef RT_CASE3
+#undef RT_CASE
+  return cudaErrorInvalidConfiguration;
+}
+
+}  // namespace rtg
