@@ -114,6 +114,7 @@ struct KSum<double> {
 struct Geo {
   int T[3] = {1, 1, 1}, B[3] = {1, 1, 1}, P[3] = {1, 1, 1};   // tile, padded box, cells per layer
   int ncell = 1, nbox = 1, ncross = 1, next = 0, nlow = 0;
+  int RX = 1, RXF = 1;          // row lengths of the x slope / flux arrays
   int sl_off[4] = {0, 0, 0, 0}, fx_off[4] = {0, 0, 0, 0};  // slope / flux array offsets per axis
   __host__ __device__ constexpr void init(int dim, int tx, int ty, int tz) {
     T[0] = tx; T[1] = ty; T[2] = tz;
@@ -122,20 +123,74 @@ struct Geo {
     ncross = ncell;
     next = 0;
     nlow = 0;
+    // Threads are ordered x, then z, then y, so a warp holds 32/tx rows of
+    // x at consecutive z.  Rows of the x arrays are padded to a length
+    // congruent to tx mod 32, which puts those rows on disjoint banks.
+    RX = tx >= 32 ? tx + 2 : tx + 32;
+    RXF = tx >= 32 ? tx + 1 : tx + 32;
     sl_off[0] = fx_off[0] = 0;
     for (int d = 0; d < 3; ++d) {
       bool act = d < dim;
       B[d] = act ? T[d] + 2 * kHalo : 1;
       nbox *= B[d];
       P[d] = ncell / T[d];
-      int nsl = act ? (T[d] + 2) * P[d] : 0, nfx = act ? (T[d] + 1) * P[d] : 0;
       ncross += act ? 2 * kHalo * P[d] : 0;
       next += act ? 2 * P[d] : 0;
       nlow += act ? P[d] : 0;
-      sl_off[d + 1] = sl_off[d] + nsl;
-      fx_off[d + 1] = fx_off[d] + nfx;
+      sl_off[d + 1] = sl_off[d] + (act ? sl_size(d) : 0);
+      fx_off[d + 1] = fx_off[d] + (act ? fx_size(d) : 0);
     }
   }
+  // Slope of the cell at local (lx, ly, lz) along axis d, l_d in [-1, T_d].
+  __host__ __device__ constexpr int sl_idx(int d, int lx, int ly, int lz) const {
+    return d == 0 ? (lx + 1) + RX * (lz + T[2] * ly)
+           : d == 1 ? lx + T[0] * (lz + T[2] * (ly + 1))
+                    : lx + T[0] * ((lz + 1) + (T[2] + 2) * ly);
+  }
+  __host__ __device__ constexpr int sl_size(int d) const {
+    return d == 0 ? RX * T[2] * T[1] : d == 1 ? T[0] * T[2] * (T[1] + 2) : T[0] * (T[2] + 2) * T[1];
+  }
+  __host__ __device__ constexpr int sl_step(int d) const { return d == 0 ? 1 : d == 1 ? T[0] * T[2] : T[0]; }
+  // Flux of face f along d (between local f-1 and f) in the row of (lx, ly, lz).
+  __host__ __device__ constexpr int fx_idx(int d, int f, int lx, int ly, int lz) const {
+    return d == 0 ? f + RXF * (lz + T[2] * ly) : d == 1 ? lx + T[0] * (lz + T[2] * f) : lx + T[0] * (f + (T[2] + 1) * ly);
+  }
+  __host__ __device__ constexpr int fx_size(int d) const {
+    return d == 0 ? RXF * T[2] * T[1] : d == 1 ? T[0] * T[2] * (T[1] + 1) : T[0] * (T[2] + 1) * T[1];
+  }
+  __host__ __device__ constexpr int fx_step(int d) const { return d == 0 ? 1 : d == 1 ? T[0] * T[2] : T[0]; }
+};
+
+// The same geometry for a compile-time shape, as constants, for device
+// code (runtime-indexed member arrays would put the struct in memory).
+template <int DIM, int TX, int TY, int TZ>
+struct GeoT {
+  __host__ __device__ static constexpr Geo g() {
+    Geo x;
+    x.init(DIM, TX, TY, TZ);
+    return x;
+  }
+  static constexpr int ncell = g().ncell, nbox = g().nbox, ncross = g().ncross, next = g().next, nlow = g().nlow;
+  static constexpr int B0 = g().B[0], B1 = g().B[1];
+  static constexpr int P0 = g().P[0], P1 = g().P[1], P2 = g().P[2];
+  static constexpr int SL0 = g().sl_off[0], SL1 = g().sl_off[1], SL2 = g().sl_off[2], SL3 = g().sl_off[3];
+  static constexpr int FX0 = g().fx_off[0], FX1 = g().fx_off[1], FX2 = g().fx_off[2], FX3 = g().fx_off[3];
+  static constexpr int RX = g().RX, RXF = g().RXF;
+  __host__ __device__ static constexpr int T(int d) { return d == 0 ? TX : d == 1 ? TY : TZ; }
+  __host__ __device__ static constexpr int P(int d) { return d == 0 ? P0 : d == 1 ? P1 : P2; }
+  __host__ __device__ static constexpr int bstride(int d) { return d == 0 ? 1 : d == 1 ? B0 : B0 * B1; }
+  __host__ __device__ static constexpr int sl_off(int d) { return d == 0 ? SL0 : d == 1 ? SL1 : SL2; }
+  __host__ __device__ static constexpr int fx_off(int d) { return d == 0 ? FX0 : d == 1 ? FX1 : FX2; }
+  __host__ __device__ static constexpr int sl_idx(int d, int lx, int ly, int lz) {
+    return d == 0 ? (lx + 1) + RX * (lz + TZ * ly)
+           : d == 1 ? lx + TX * (lz + TZ * (ly + 1))
+                    : lx + TX * ((lz + 1) + (TZ + 2) * ly);
+  }
+  __host__ __device__ static constexpr int sl_step(int d) { return d == 0 ? 1 : d == 1 ? TX * TZ : TX; }
+  __host__ __device__ static constexpr int fx_idx(int d, int f, int lx, int ly, int lz) {
+    return d == 0 ? f + RXF * (lz + TZ * ly) : d == 1 ? lx + TX * (lz + TZ * f) : lx + TX * (f + (TZ + 1) * ly);
+  }
+  __host__ __device__ static constexpr int fx_step(int d) { return d == 0 ? 1 : d == 1 ? TX * TZ : TX; }
 };
 
 // Per-angle table entries: n (0-2), W (3), C mu dt/2dx (4-6), C |mu| dt/2dx
@@ -158,12 +213,6 @@ __device__ __forceinline__ int map_in(int g, int n, int kind_lo, int kind_hi) {
   if (g < 0) return kind_lo == BC_PERIODIC ? ((g % n) + n) % n : 0;
   if (g >= n) return kind_hi == BC_PERIODIC ? g % n : n - 1;
   return g;
-}
-
-// Index of local coordinates (other than axis d) within a layer normal to d.
-__device__ __forceinline__ int layer_index(const Geo &G, int d, const int l[3]) {
-  int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;
-  return l[a1] + G.T[a1] * l[a2];
 }
 
 // Flux through one face, already multiplied by dt/dx: the alpha blend of
@@ -210,22 +259,22 @@ __global__ void __launch_bounds__(TX * TY * TZ) step_kernel(const StepArgs<Real>
   constexpr int kSlots = slots_for(DIM, TX, TY, TZ);
   static_assert(kSlots <= 4, "tile halo too large for the staging slots");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Geo G;
-  G.init(DIM, TX, TY, TZ);
+  using G = GeoT<DIM, TX, TY, TZ>;
   const int M = a.M;
   const long long N = a.N;
-  const int nthr = G.ncell;
-  const int tid = threadIdx.x + G.T[0] * (threadIdx.y + G.T[1] * threadIdx.z);
-  const int org[3] = {(int)blockIdx.x * G.T[0], (int)blockIdx.y * G.T[1], (int)blockIdx.z * G.T[2]};
-  const int bstride[3] = {1, G.B[0], G.B[0] * G.B[1]};
+  const int nthr = G::ncell;
+  // block = (TX, TZ, TY): threads ordered x, z, y (see Geo)
+  const int tid = threadIdx.x + TX * (threadIdx.y + TZ * threadIdx.z);
+  const int org[3] = {(int)blockIdx.x * TX, (int)blockIdx.y * TY, (int)blockIdx.z * TZ};
+  const int bstride[3] = {1, G::B0, G::B0 * G::B1};
 
   Real *s_tab = reinterpret_cast<Real *>(smem_raw);   // [M][kTab]
   Real *s_Q = s_tab + kTab * M;                        // [M][ncell]
-  Real *s_It = s_Q + (size_t)M * G.ncell;              // [nbox]
-  Real *s_IV = s_It + G.nbox;                          // [nbox]            (VEL)
-  Real *s_sI = s_IV + (VEL ? G.nbox : 0);              // slopes of I~
-  Real *s_sV = s_sI + G.sl_off[3];                     // slopes of IV      (VEL)
-  Real *s_fx = s_sV + (VEL ? G.sl_off[3] : 0);         // face fluxes
+  Real *s_It = s_Q + (size_t)M * G::ncell;             // [nbox]
+  Real *s_IV = s_It + G::nbox;                         // [nbox]            (VEL)
+  Real *s_sI = s_IV + (VEL ? G::nbox : 0);             // slopes of I~
+  Real *s_sV = s_sI + G::SL3;                          // slopes of IV      (VEL)
+  Real *s_fx = s_sV + (VEL ? G::SL3 : 0);              // face fluxes
 
   const Real C = a.C, invC = a.invC, dt = a.dt;
 
@@ -248,17 +297,17 @@ __global__ void __launch_bounds__(TX * TY * TZ) step_kernel(const StepArgs<Real>
   }
 
   // ---- own cell ---------------------------------------------------------------
-  const int loc[3] = {(int)threadIdx.x, (int)threadIdx.y, (int)threadIdx.z};
+  const int loc[3] = {(int)threadIdx.x, (int)threadIdx.z, (int)threadIdx.y};
   const int gx = org[0] + loc[0], gy = org[1] + loc[1], gz = org[2] + loc[2];
   const bool valid = gx < a.n[0] && gy < a.n[1] && gz < a.n[2];
   const long long c = valid ? gx + (long long)a.n[0] * (gy + (long long)a.n[1] * gz) : 0;
   int bo = 0;
   for (int d = 0; d < DIM; ++d) bo += (loc[d] + kHalo) * bstride[d];
   int own_sl[3], own_fx[3];
+#pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    int li = layer_index(G, d, loc);
-    own_sl[d] = G.sl_off[d] + (loc[d] + 1) + (G.T[d] + 2) * li;
-    own_fx[d] = G.fx_off[d] + loc[d] + (G.T[d] + 1) * li;   // face below the cell
+    own_sl[d] = G::sl_off(d) + G::sl_idx(d, loc[0], loc[1], loc[2]);
+    own_fx[d] = G::fx_off(d) + G::fx_idx(d, loc[d], loc[0], loc[1], loc[2]);   // face below the cell
   }
 
   // ---- staging slots: fixed cross cells of this thread ---------------------
@@ -273,24 +322,26 @@ __global__ void __launch_bounds__(TX * TY * TZ) step_kernel(const StepArgs<Real>
     const int k = tid + s * nthr;
     sl_box[s] = -1; sl_code[s] = 0; sl_g[s] = 0;
     sl_w[s][0] = sl_w[s][1] = sl_w[s][2] = Real(0);
-    if (k >= G.ncross) continue;
+    if (k >= G::ncross) continue;
     int b[3] = {0, 0, 0};
-    if (k < G.ncell) {
-      b[0] = k % G.T[0] + (DIM >= 1 ? kHalo : 0);
-      b[1] = (k / G.T[0]) % G.T[1] + (DIM >= 2 ? kHalo : 0);
-      b[2] = k / (G.T[0] * G.T[1]) + (DIM >= 3 ? kHalo : 0);
+    if (k < G::ncell) {
+      b[0] = k % TX + (DIM >= 1 ? kHalo : 0);
+      b[2] = (k / TX) % TZ + (DIM >= 3 ? kHalo : 0);
+      b[1] = k / (TX * TZ) + (DIM >= 2 ? kHalo : 0);
     } else {
-      int kk = k - G.ncell;
+      int kk = k - G::ncell;
       int d = 0;
-      while (kk >= 2 * kHalo * G.P[d]) { kk -= 2 * kHalo * G.P[d]; ++d; }
-      int layer = kk / G.P[d], o = kk % G.P[d];
+      while (kk >= 2 * kHalo * G::P(d)) { kk -= 2 * kHalo * G::P(d); ++d; }
+      int layer = kk / G::P(d), o = kk % G::P(d);
       int side = layer / kHalo, h = layer % kHalo;
       int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;
-      b[d] = side == 0 ? h : G.T[d] + kHalo + h;
-      b[a1] = o % G.T[a1] + (a1 < DIM ? kHalo : 0);
-      b[a2] = o / G.T[a1] + (a2 < DIM ? kHalo : 0);
+      const int bd = side == 0 ? h : G::T(d) + kHalo + h;
+      const int b1v = o % G::T(a1) + (a1 < DIM ? kHalo : 0), b2v = o / G::T(a1) + (a2 < DIM ? kHalo : 0);
+      b[0] = d == 0 ? bd : (a1 == 0 ? b1v : b2v);
+      b[1] = d == 1 ? bd : (a1 == 1 ? b1v : b2v);
+      b[2] = d == 2 ? bd : (a1 == 2 ? b1v : b2v);
     }
-    sl_box[s] = b[0] + G.B[0] * (b[1] + G.B[1] * b[2]);
+    sl_box[s] = b[0] + G::B0 * (b[1] + G::B1 * b[2]);
     int g[3], code = 0;
     for (int d = 0; d < 3; ++d) {
       g[d] = d < DIM ? org[d] + b[d] - kHalo : 0;
@@ -321,20 +372,20 @@ __global__ void __launch_bounds__(TX * TY * TZ) step_kernel(const StepArgs<Real>
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     const int e = tid + j * nthr;
-    if (e >= G.next) continue;
+    if (e >= G::next) continue;
     int ee = e, d = 0;
-    while (ee >= 2 * G.P[d]) { ee -= 2 * G.P[d]; ++d; }
-    const int side = ee / G.P[d], o = ee % G.P[d];
+    while (ee >= 2 * G::P(d)) { ee -= 2 * G::P(d); ++d; }
+    const int side = ee / G::P(d), o = ee % G::P(d);
     const int a1x = d == 0 ? 1 : 0, a2x = d == 2 ? 1 : 2;
-    int b[3];
-    b[d] = side == 0 ? kHalo - 1 : G.T[d] + kHalo;
-    b[a1x] = o % G.T[a1x] + (a1x < DIM ? kHalo : 0);
-    b[a2x] = o / G.T[a1x] + (a2x < DIM ? kHalo : 0);
-    ext_bb[j] = b[0] + G.B[0] * (b[1] + G.B[1] * b[2]);
-    ext_st[j] = d == 0 ? 1 : (d == 1 ? G.B[0] : G.B[0] * G.B[1]);
-    ext_si[j] = G.sl_off[d] + (side == 0 ? 0 : G.T[d] + 1) + (G.T[d] + 2) * o;
+    const int ld = side == 0 ? -1 : G::T(d), l1v = o % G::T(a1x), l2v = o / G::T(a1x);
+    const int l0 = d == 0 ? ld : (a1x == 0 ? l1v : l2v);
+    const int l1 = d == 1 ? ld : (a1x == 1 ? l1v : l2v);
+    const int l2 = d == 2 ? ld : (a1x == 2 ? l1v : l2v);
+    ext_bb[j] = (l0 + kHalo) + G::B0 * ((DIM >= 2 ? l1 + kHalo : 0) + G::B1 * (DIM >= 3 ? l2 + kHalo : 0));
+    ext_st[j] = G::bstride(d);
+    ext_si[j] = G::sl_off(d) + G::sl_idx(d, l0, l1, l2);
   }
-  const int ncell = G.ncell;
+  const int ncell = G::ncell;
 
   // ---- face constants.  alpha of a face is the mean of its two cells'; the
   // IV face blends the van Leer states by the sign of the face velocity
@@ -352,31 +403,32 @@ __global__ void __launch_bounds__(TX * TY * TZ) step_kernel(const StepArgs<Real>
   }
   // The lowest face of the tile along each axis: work items spread over the
   // threads (at most two each), so no warp diverges over them.
-  int lf_d[2] = {0, 0}, lf_bb[2] = {0, 0}, lf_si[2] = {0, 0}, lf_fx[2] = {-1, -1};
+  int lf_d[2] = {0, 0}, lf_bb[2] = {0, 0}, lf_si[2] = {0, 0}, lf_sstep[2] = {1, 1}, lf_fx[2] = {-1, -1};
   Real lf_al[2] = {1, 1}, lf_hv[2] = {1, 1}, lf_wl[2] = {0.5, 0.5};
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     int e = tid + j * nthr;
-    if (e >= G.nlow) continue;
+    if (e >= G::nlow) continue;
     int d = 0;
-    while (e >= G.P[d]) { e -= G.P[d]; ++d; }
-    const int a1x = d == 0 ? 1 : 0, a2x = d == 2 ? 1 : 2;
-    int l[3];
-    l[d] = 0;
-    l[a1x] = e % G.T[a1x];
-    l[a2x] = e / G.T[a1x];
-    int bb = 0;
-    for (int q = 0; q < DIM; ++q) bb += (l[q] + kHalo) * (q == 0 ? 1 : q == 1 ? G.B[0] : G.B[0] * G.B[1]);
-    const int st = d == 0 ? 1 : (d == 1 ? G.B[0] : G.B[0] * G.B[1]);
+    while (e >= G::P(d)) { e -= G::P(d); ++d; }
+    const int a1x = d == 0 ? 1 : 0;
+    const int l1v = e % G::T(a1x), l2v = e / G::T(a1x);
+    const int l[3] = {d == 0 ? 0 : (a1x == 0 ? l1v : l2v), d == 1 ? 0 : (a1x == 1 ? l1v : l2v),
+                      d == 2 ? 0 : (a1x == 2 ? l1v : l2v)};
+    const int bb = (l[0] + kHalo) + G::B0 * ((DIM >= 2 ? l[1] + kHalo : 0) + G::B1 * (DIM >= 3 ? l[2] + kHalo : 0));
+    const int st = G::bstride(d);
     lf_d[j] = d;
     lf_bb[j] = bb - st;                                    // cell below the face
-    lf_si[j] = G.sl_off[d] + (G.T[d] + 2) * e;             // its slope (extension layer)
-    lf_fx[j] = G.fx_off[d] + (G.T[d] + 1) * e;             // face 0 of this layer
+    lf_si[j] = G::sl_off(d) + G::sl_idx(d, d == 0 ? -1 : l[0], d == 1 ? -1 : l[1], d == 2 ? -1 : l[2]);   // slope below
+    lf_sstep[j] = G::sl_step(d);
+    lf_fx[j] = G::fx_off(d) + G::fx_idx(d, 0, l[0], l[1], l[2]);   // face 0 of this row
     int gu[3] = {min(org[0] + l[0], a.n[0] - 1), min(org[1] + (DIM >= 2 ? l[1] : 0), a.n[1] - 1),
                  min(org[2] + (DIM >= 3 ? l[2] : 0), a.n[2] - 1)};
     int gl[3] = {gu[0], gu[1], gu[2]};
-    gu[d] = min(org[d], a.n[d] - 1);
-    gl[d] = map_in(org[d] - 1, a.n[d], a.bc[d][0], a.bc[d][1]);
+    const int od = d == 0 ? org[0] : d == 1 ? org[1] : org[2], nd = d == 0 ? a.n[0] : d == 1 ? a.n[1] : a.n[2];
+    const int kl = d == 0 ? a.bc[0][0] : d == 1 ? a.bc[1][0] : a.bc[2][0], kh = d == 0 ? a.bc[0][1] : d == 1 ? a.bc[1][1] : a.bc[2][1];
+    const int gud = min(od, nd - 1), gld = map_in(od - 1, nd, kl, kh);
+    if (d == 0) { gu[0] = gud; gl[0] = gld; } else if (d == 1) { gu[1] = gud; gl[1] = gld; } else { gu[2] = gud; gl[2] = gld; }
     face_consts<Real, VEL>(a, d, gl, gu, &lf_al[j], &lf_hv[j], &lf_wl[j]);
   }
 
@@ -492,18 +544,20 @@ __global__ void __launch_bounds__(TX * TY * TZ) step_kernel(const StepArgs<Real>
       const int st = bstride[d];
       const Real hc = t[4 + d], hca = t[8 + d], mud = t[12 + d];
       // face above the own cell
-      fhi[d] = face_flux<Real, VEL>(q0, sI[d], s_It[bo + st], s_sI[own_sl[d] + 1], p0, VEL ? sV[d] : Real(0),
-                                    VEL ? s_IV[bo + st] : Real(0), VEL ? s_sV[own_sl[d] + 1] : Real(0),
+      const int sn = own_sl[d] + G::sl_step(d);
+      fhi[d] = face_flux<Real, VEL>(q0, sI[d], s_It[bo + st], s_sI[sn], p0, VEL ? sV[d] : Real(0),
+                                    VEL ? s_IV[bo + st] : Real(0), VEL ? s_sV[sn] : Real(0),
                                     fu_al[d], fu_hv[d], fu_wl[d], hc, hca, mud);
-      s_fx[own_fx[d] + 1] = fhi[d];
+      s_fx[own_fx[d] + G::fx_step(d)] = fhi[d];
     }
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       if (lf_fx[j] < 0) continue;
       const int d = lf_d[j], bb = lf_bb[j], st = d == 0 ? 1 : bstride[d == 1 ? 1 : 2];
-      s_fx[lf_fx[j]] = face_flux<Real, VEL>(s_It[bb], s_sI[lf_si[j]], s_It[bb + st], s_sI[lf_si[j] + 1],
-                                            VEL ? s_IV[bb] : Real(0), VEL ? s_sV[lf_si[j]] : Real(0),
-                                            VEL ? s_IV[bb + st] : Real(0), VEL ? s_sV[lf_si[j] + 1] : Real(0),
+      const int si = lf_si[j], si1 = lf_si[j] + lf_sstep[j];
+      s_fx[lf_fx[j]] = face_flux<Real, VEL>(s_It[bb], s_sI[si], s_It[bb + st], s_sI[si1],
+                                            VEL ? s_IV[bb] : Real(0), VEL ? s_sV[si] : Real(0),
+                                            VEL ? s_IV[bb + st] : Real(0), VEL ? s_sV[si1] : Real(0),
                                             lf_al[j], lf_hv[j], lf_wl[j], t[4 + d], t[8 + d], t[12 + d]);
     }
     __syncthreads();
@@ -696,7 +750,7 @@ cudaError_t launch_shape(const StepArgs<Real> &a, cudaStream_t s) {
   auto kern = step_kernel<Real, DIM, VEL, TX, TY, TZ>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  dim3 block(TX, TY, TZ);
+  dim3 block(TX, TZ, TY);   // threads ordered x, z, y
   dim3 grid((a.n[0] + TX - 1) / TX, (a.n[1] + TY - 1) / TY, (a.n[2] + TZ - 1) / TZ);
   kern<<<grid, block, sm, s>>>(a);
   return cudaGetLastError();
