@@ -192,8 +192,33 @@ rt_status rt_sources(rt_ctx *ctx, double *dE_gas, double *dMom, double *T_new);
 /* Copies the current intensity out (M*N values, angle-major). */
 rt_status rt_get_intensity(rt_ctx *ctx, double *I);
 
-/* Frees the context and its device state.  NULL is ignored. */
+/* Frees the context and its device state (removing it from its batch
+ * first).  NULL is ignored. */
 void rt_destroy(rt_ctx *ctx);
+
+/* ---- many problems in one launch ------------------------------------------
+ * A batch advances several independent contexts together: each step is one
+ * persistent kernel launch whose CTAs take (problem, tile) work items from a
+ * device list, each problem with its own CFL time step.  Every problem
+ * computes exactly what rt_step would give it alone.  Contexts must use
+ * RT_FP32, the batch's stream, and have their material set; while in a
+ * batch they are stepped only by rt_batch_step (rt_step returns
+ * RT_E_STATE), and are read with the usual rt_moments / rt_sources /
+ * rt_get_intensity / rt_sync calls.  The caller keeps ownership of them. */
+typedef struct rt_batch rt_batch;
+
+/* stream: the cudaStream_t of the member contexts (NULL: legacy default
+ * stream, steps launched one by one instead of through a graph). */
+rt_status rt_batch_create(void *stream, rt_batch **out);
+rt_status rt_batch_add(rt_batch *b, rt_ctx *ctx);
+rt_status rt_batch_remove(rt_batch *b, rt_ctx *ctx);
+int rt_batch_size(const rt_batch *b);
+/* nsteps steps of every member, captured in one CUDA graph (a counter reset
+ * and one persistent launch per step) when the stream is not NULL.
+ * Stream-ordered.  RT_E_INVALID if the largest angle set does not fit. */
+rt_status rt_batch_step(rt_batch *b, int nsteps);
+/* Frees the batch (not its contexts).  NULL is ignored. */
+void rt_batch_destroy(rt_batch *b);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *rt_last_error(void);

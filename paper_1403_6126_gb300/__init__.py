@@ -81,6 +81,12 @@ def lib():
             "rt_sources": (I, [V, V, V, V]),
             "rt_get_intensity": (I, [V, V]),
             "rt_destroy": (None, [V]),
+            "rt_batch_create": (I, [V, ctypes.POINTER(V)]),
+            "rt_batch_add": (I, [V, V]),
+            "rt_batch_remove": (I, [V, V]),
+            "rt_batch_size": (I, [V]),
+            "rt_batch_step": (I, [V, I]),
+            "rt_batch_destroy": (None, [V]),
             "rt_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -189,6 +195,32 @@ def rt_get_intensity(ctx, I):
 
 def rt_destroy(ctx):
     lib().rt_destroy(ctx)
+
+
+def rt_batch_create(stream=None):
+    out = ctypes.c_void_p()
+    _check(lib().rt_batch_create(stream, ctypes.byref(out)), "rt_batch_create")
+    return out
+
+
+def rt_batch_add(b, ctx):
+    _check(lib().rt_batch_add(b, ctx), "rt_batch_add")
+
+
+def rt_batch_remove(b, ctx):
+    _check(lib().rt_batch_remove(b, ctx), "rt_batch_remove")
+
+
+def rt_batch_size(b):
+    return lib().rt_batch_size(b)
+
+
+def rt_batch_step(b, nsteps):
+    _check(lib().rt_batch_step(b, nsteps), "rt_batch_step")
+
+
+def rt_batch_destroy(b):
+    lib().rt_batch_destroy(b)
 
 
 def rt_last_error():

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "rt.h"
+#include "rt_ctx.h"
 #include "rt_internal.h"
 
 namespace {
@@ -19,6 +20,12 @@ rt_status fail(rt_status s, const std::string &msg) {
   g_last_error = msg;
   return s;
 }
+
+}  // namespace
+
+rt_status rtg::set_error(rt_status s, const std::string &msg) { return fail(s, msg); }
+
+namespace {
 
 rt_status cuda_fail(cudaError_t e, const char *what) {
   return fail(RT_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -32,35 +39,6 @@ rt_status cuda_fail(cudaError_t e, const char *what) {
 
 }  // namespace
 
-struct rt_ctx {
-  int dim = 0, n[3] = {1, 1, 1}, M = 0;
-  long long N = 0;
-  double dx[3] = {1, 1, 1};
-  int bc[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-  double C = 1, P = 1;
-  rt_options opt{};
-  cudaStream_t stream = nullptr;
-  bool fp64 = false;
-  size_t rs = 4;  // bytes per stored real
-  bool has_v = false, material_set = false, intensity_set = false;
-  rtg::TileShape tile{0, 0, 0};
-  // device state (Real = double or float)
-  void *I[2] = {nullptr, nullptr};
-  void *mom[2] = {nullptr, nullptr};
-  int cur = 0;
-  void *rho = nullptr, *sa = nullptr, *ss = nullptr, *v = nullptr;
-  double *T = nullptr, *dEgas = nullptr;
-  void *dMom = nullptr, *ang = nullptr, *inflow = nullptr;
-  int *flags = nullptr;  // [0] Newton failures, [1] input scan
-  double *stage = nullptr;
-  long long stage_len = 0;
-  std::vector<double> host_n, host_w, host_inflow;
-  // captured multi-step graph
-  cudaGraphExec_t graph = nullptr;
-  double graph_dt = 0;
-  int graph_steps = 0, graph_cur = -1;
-  bool graph_vel = false;
-};
 
 namespace {
 
@@ -72,9 +50,12 @@ void free_all(rt_ctx *c) {
     if (p) cudaFree(p);
 }
 
+}  // namespace
+
 template <typename Real>
-rtg::StepArgs<Real> make_args(rt_ctx *c, double dt) {
+rtg::StepArgs<Real> rtg::make_args(rt_ctx *c, double dt) {
   rtg::StepArgs<Real> a;
+  a.dim = c->dim;
   for (int d = 0; d < 3; ++d) {
     a.n[d] = c->n[d];
     a.bc[d][0] = c->bc[d][0];
@@ -110,15 +91,20 @@ rtg::StepArgs<Real> make_args(rt_ctx *c, double dt) {
   return a;
 }
 
-bool velocity_on(const rt_ctx *c) { return c->has_v || c->opt.estimate_v; }
+template rtg::StepArgs<float> rtg::make_args<float>(rt_ctx *, double);
+template rtg::StepArgs<double> rtg::make_args<double>(rt_ctx *, double);
+
+bool rtg::velocity_on(const rt_ctx *c) { return c->has_v || c->opt.estimate_v; }
+
+namespace {
 
 rt_status launch_step(rt_ctx *c, double dt) {
   cudaError_t e;
-  bool vel = velocity_on(c);
+  bool vel = rtg::velocity_on(c);
   if (c->fp64)
-    e = rtg::launch_step<double>(make_args<double>(c, dt), c->dim, vel, c->tile, c->stream);
+    e = rtg::launch_step<double>(rtg::make_args<double>(c, dt), c->dim, vel, c->tile, c->stream);
   else
-    e = rtg::launch_step<float>(make_args<float>(c, dt), c->dim, vel, c->tile, c->stream);
+    e = rtg::launch_step<float>(rtg::make_args<float>(c, dt), c->dim, vel, c->tile, c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
   c->cur = 1 - c->cur;
   return RT_OK;
@@ -419,6 +405,7 @@ double rt_cfl_dt(const rt_ctx *c) {
 rt_status rt_step(rt_ctx *c, double dt) {
   if (!c) return fail(RT_E_INVALID, "rt_step: NULL context");
   if (!c->material_set) return fail(RT_E_STATE, "rt_step: call rt_set_material first");
+  if (c->batch) return fail(RT_E_STATE, "rt_step: the context belongs to a batch; step it with rt_batch_step");
   if (!(dt > 0)) dt = rt_cfl_dt(c);
   if (!std::isfinite(dt)) return fail(RT_E_INVALID, "rt_step: dt not finite");
   return launch_step(c, dt);
@@ -427,6 +414,7 @@ rt_status rt_step(rt_ctx *c, double dt) {
 rt_status rt_run(rt_ctx *c, double dt, int nsteps) {
   if (!c) return fail(RT_E_INVALID, "rt_run: NULL context");
   if (!c->material_set) return fail(RT_E_STATE, "rt_run: call rt_set_material first");
+  if (c->batch) return fail(RT_E_STATE, "rt_run: the context belongs to a batch; step it with rt_batch_step");
   if (nsteps < 0) return fail(RT_E_INVALID, "rt_run: nsteps < 0");
   if (nsteps == 0) return RT_OK;
   if (!(dt > 0)) dt = rt_cfl_dt(c);
@@ -438,7 +426,7 @@ rt_status rt_run(rt_ctx *c, double dt, int nsteps) {
     }
     return RT_OK;
   }
-  bool vel = velocity_on(c);
+  bool vel = rtg::velocity_on(c);
   if (!c->graph || c->graph_dt != dt || c->graph_steps != nsteps || c->graph_cur != c->cur || c->graph_vel != vel) {
     if (c->graph) {
       cudaGraphExecDestroy(c->graph);
@@ -528,6 +516,7 @@ rt_status rt_get_intensity(rt_ctx *c, double *I) {
 
 void rt_destroy(rt_ctx *c) {
   if (!c) return;
+  if (c->batch) rt_batch_remove((rt_batch *)c->batch, c);
   cudaStreamSynchronize(c->stream);
   free_all(c);
   delete c;

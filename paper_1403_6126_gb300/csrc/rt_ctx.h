@@ -1,0 +1,51 @@
+// Internal layout of a context (one problem), shared by the single-problem
+// runtime (rt_api.cu), the multi-problem runtime (rt_batch.cu) and the
+// serving loop (rt_server.cpp).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "rt.h"
+#include "rt_internal.h"
+
+struct rt_ctx {
+  int dim = 0, n[3] = {1, 1, 1}, M = 0;
+  long long N = 0;
+  double dx[3] = {1, 1, 1};
+  int bc[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  double C = 1, P = 1;
+  rt_options opt{};
+  cudaStream_t stream = nullptr;
+  bool fp64 = false;
+  size_t rs = 4;  // bytes per stored real
+  bool has_v = false, material_set = false, intensity_set = false;
+  rtg::TileShape tile{0, 0, 0};
+  // device state (Real = double or float)
+  void *I[2] = {nullptr, nullptr};
+  void *mom[2] = {nullptr, nullptr};
+  int cur = 0;
+  void *rho = nullptr, *sa = nullptr, *ss = nullptr, *v = nullptr;
+  double *T = nullptr, *dEgas = nullptr;
+  void *dMom = nullptr, *ang = nullptr, *inflow = nullptr;
+  int *flags = nullptr;  // [0] Newton failures, [1] input scan
+  double *stage = nullptr;
+  long long stage_len = 0;
+  std::vector<double> host_n, host_w, host_inflow;
+  // captured multi-step graph
+  cudaGraphExec_t graph = nullptr;
+  double graph_dt = 0;
+  int graph_steps = 0, graph_cur = -1;
+  bool graph_vel = false;
+  void *batch = nullptr;  // the rt_batch this context belongs to, if any
+};
+
+namespace rtg {
+// Step arguments of context c for its current buffer parity.
+template <typename Real>
+StepArgs<Real> make_args(rt_ctx *c, double dt);
+// Whether the velocity terms are on (v != 0 somewhere, or the estimate).
+bool velocity_on(const rt_ctx *c);
+// Records msg as this thread's last error and returns s.
+rt_status set_error(rt_status s, const std::string &msg);
+}  // namespace rtg

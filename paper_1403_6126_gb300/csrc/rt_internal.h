@@ -14,6 +14,7 @@ constexpr int kMomComps = 10;  // E, Fx, Fy, Fz, Pxx, Pyy, Pzz, Pxy, Pxz, Pyz
 // temperature and the gas energy source are always double.
 template <typename Real>
 struct StepArgs {
+  int dim;            // active axes
   int n[3];           // cells per axis (1 on inactive axes)
   int M;              // angles
   long long N;        // cells

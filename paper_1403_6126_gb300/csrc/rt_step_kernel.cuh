@@ -254,20 +254,23 @@ __host__ __device__ constexpr int slots_for(int dim, int tx, int ty, int tz) {
   return (g.ncross + g.ncell - 1) / g.ncell;
 }
 
+// One tile of one problem: tile coordinates (tbx, tby, tbz) in units of the
+// tile shape, thread tid of TX*TY*TZ (ordered x, then z, then y, see Geo),
+// shared memory smem_raw of smem_bytes().  Used by the single-problem
+// kernel and by the persistent multi-problem kernel.
 template <typename Real, int DIM, bool VEL, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(TX * TY * TZ) step_kernel(const StepArgs<Real> a) {
+__device__ __forceinline__ void process_tile(const StepArgs<Real> &a, int tid, int tbx, int tby, int tbz,
+                                             unsigned char *smem_raw) {
   constexpr int kSlots = slots_for(DIM, TX, TY, TZ);
   static_assert(kSlots <= 4, "tile halo too large for the staging slots");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   using G = GeoT<DIM, TX, TY, TZ>;
   const int M = a.M;
   const long long N = a.N;
   const int nthr = G::ncell;
-  // block = (TX, TZ, TY): threads ordered x, z, y (see Geo)
-  const int tid = threadIdx.x + TX * (threadIdx.y + TZ * threadIdx.z);
-  const int org[3] = {(int)blockIdx.x * TX, (int)blockIdx.y * TY, (int)blockIdx.z * TZ};
+  const int org[3] = {tbx * TX, tby * TY, tbz * TZ};
   const int bstride[3] = {1, G::B0, G::B0 * G::B1};
 
+  __syncthreads();   // the previous tile of a persistent CTA is done with shared memory
   Real *s_tab = reinterpret_cast<Real *>(smem_raw);   // [M][kTab]
   Real *s_Q = s_tab + kTab * M;                        // [M][ncell]
   Real *s_It = s_Q + (size_t)M * G::ncell;             // [nbox]
@@ -297,7 +300,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) step_kernel(const StepArgs<Real>
   }
 
   // ---- own cell ---------------------------------------------------------------
-  const int loc[3] = {(int)threadIdx.x, (int)threadIdx.z, (int)threadIdx.y};
+  const int loc[3] = {tid % TX, tid / (TX * TZ), (tid / TX) % TZ};
   const int gx = org[0] + loc[0], gy = org[1] + loc[1], gz = org[2] + loc[2];
   const bool valid = gx < a.n[0] && gy < a.n[1] && gz < a.n[2];
   const long long c = valid ? gx + (long long)a.n[0] * (gy + (long long)a.n[1] * gz) : 0;
@@ -745,12 +748,18 @@ __global__ void __launch_bounds__(TX * TY * TZ) step_kernel(const StepArgs<Real>
 }
 
 template <typename Real, int DIM, bool VEL, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(TX * TY * TZ) step_kernel(const StepArgs<Real> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  process_tile<Real, DIM, VEL, TX, TY, TZ>(a, threadIdx.x, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+}
+
+template <typename Real, int DIM, bool VEL, int TX, int TY, int TZ>
 cudaError_t launch_shape(const StepArgs<Real> &a, cudaStream_t s) {
   const size_t sm = smem_bytes(DIM, a.M, VEL, TX, TY, TZ, sizeof(Real));
   auto kern = step_kernel<Real, DIM, VEL, TX, TY, TZ>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  dim3 block(TX, TZ, TY);   // threads ordered x, z, y
+  dim3 block(TX * TY * TZ);
   dim3 grid((a.n[0] + TX - 1) / TX, (a.n[1] + TY - 1) / TY, (a.n[2] + TZ - 1) / TZ);
   kern<<<grid, block, sm, s>>>(a);
   return cudaGetLastError();
