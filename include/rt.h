@@ -220,6 +220,50 @@ rt_status rt_batch_step(rt_batch *b, int nsteps);
 /* Frees the batch (not its contexts).  NULL is ignored. */
 void rt_batch_destroy(rt_batch *b);
 
+/* ---- one step without device allocation ------------------------------------
+ * The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory -- code running inside another framework's memory
+ * pool or under a fixed memory budget, plugins allowed to touch only the
+ * buffers handed to them, and latency-critical paths where an allocation
+ * could block or fail.  The caller passes every field as a device pointer
+ * (float intensities and cell data, double temperature and energy source,
+ * the layouts of the conventions above); the function calls no cudaMalloc,
+ * cudaFree or other allocating routine.  The little scratch the persistent
+ * step kernel needs (tile counter, Newton-failure word, angle and inflow
+ * tables) is a fixed device array of 10496 bytes that every GPU loading the
+ * library holds until the process exits; it limits the angle set to 256
+ * angles (RT_E_INVALID above that).
+ *
+ * The first call on a device looks up that array's device address (once per
+ * device, with the device current); make that first call before any stream
+ * capture.  Every call rewrites the tables and clears the counters before its
+ * kernel runs, but all calls share the one array: calls that overlap on the
+ * GPU (unordered streams) race.
+ *
+ * The step is the same as rt_step with RT_FP32 and the velocity terms on
+ * (grid, angles, Crat, Prat, opts->hold_T / estimate_v / gamma / r_ideal /
+ * stream as for rt_create; opts->precision must be RT_FP32; dt > 0).
+ * I_out, mom_out, dE_gas, dMom receive the new state; T is updated in place.
+ * mom_in must hold E_r, F_r, P_r of I_in (10 components, as rt_moments).
+ * inflow: host array [3][2][M] of incoming intensities for RT_BC_INFLOW
+ * faces, or NULL.  If newton_failures is not NULL the call waits for the
+ * stream and stores the number of cells whose T^4 Newton did not converge;
+ * otherwise it returns once the work is queued. */
+typedef struct {
+  const float *I_in;
+  float *I_out;
+  const float *rho, *sigma_a, *sigma_s, *v;
+  double *T;
+  const float *mom_in;
+  float *mom_out;
+  double *dE_gas;
+  float *dMom;
+  const double *inflow;
+} rt_noalloc_fields;
+
+rt_status rt_step_noalloc(const rt_grid *grid, const rt_angles *angles, double Crat, double Prat,
+                          const rt_options *opts, double dt, const rt_noalloc_fields *fields, int *newton_failures);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *rt_last_error(void);
 

@@ -44,6 +44,11 @@ class rt_options(ctypes.Structure):
                 ("device_ptrs", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
+class rt_noalloc_fields(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("I_in", "I_out", "rho", "sigma_a", "sigma_s", "v", "T", "mom_in",
+                                               "mom_out", "dE_gas", "dMom", "inflow")]
+
+
 class RTError(RuntimeError):
     def __init__(self, status, where, msg):
         super().__init__("%s: %s (%s)" % (where, _STATUS_NAMES.get(status, status), msg))
@@ -87,6 +92,8 @@ def lib():
             "rt_batch_size": (I, [V]),
             "rt_batch_step": (I, [V, I]),
             "rt_batch_destroy": (None, [V]),
+            "rt_step_noalloc": (I, [ctypes.POINTER(rt_grid), ctypes.POINTER(rt_angles), D, D, ctypes.POINTER(rt_options),
+                                    D, ctypes.POINTER(rt_noalloc_fields), ctypes.POINTER(I)]),
             "rt_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -221,6 +228,15 @@ def rt_batch_step(b, nsteps):
 
 def rt_batch_destroy(b):
     lib().rt_batch_destroy(b)
+
+
+def rt_step_noalloc(grid, angles, Crat, Prat, opts, dt, fields, want_failures=True):
+    """fields: rt_noalloc_fields of device addresses.  Returns the Newton
+    failure count when want_failures (the call then waits for the stream)."""
+    nf = ctypes.c_int(0)
+    _check(lib().rt_step_noalloc(ctypes.byref(grid), ctypes.byref(angles), Crat, Prat, ctypes.byref(opts), dt,
+                                 ctypes.byref(fields), ctypes.byref(nf) if want_failures else None), "rt_step_noalloc")
+    return nf.value
 
 
 def rt_last_error():

@@ -1,0 +1,200 @@
+// One radiation step without any device allocation.
+//
+// Some callers cannot call cudaMalloc: code that runs inside another
+// framework's memory pool or under a strict memory budget, plugins that may
+// only touch buffers handed to them, and stream-capture or real-time paths
+// where an allocation could block or fail.  rt_step_noalloc serves them: the
+// caller passes every field as a device pointer, and the little scratch the
+// persistent step kernel needs (its tile counter, the Newton-failure word,
+// the angle table and the inflow table) lives in a fixed file-scope device
+// array, reserved once per GPU when the library is loaded and kept until the
+// process exits.  Its size, kNoallocScratchBytes below, bounds the angle
+// count to kNoallocMaxAngles.
+//
+// The array is shared by every call: each call rewrites the tables and
+// clears the two counters before its kernel runs, so nothing carries over
+// from the previous call, but two calls that overlap on the GPU (different
+// streams without ordering between them) race on it.
+#include <cmath>
+#include <mutex>
+#include <string>
+
+#include "rt.h"
+#include "rt_ctx.h"
+#include "rt_step_kernel.cuh"
+
+namespace rtg {
+
+namespace {
+
+constexpr int kNoallocMaxAngles = 256;
+constexpr int kNoallocThreads = 512;
+// counter (4 B) + failure word (4 B), padded to 256; angle table [M][4];
+// inflow table [6][M]
+constexpr size_t kNoallocTableOffset = 256;
+constexpr size_t kNoallocScratchBytes = kNoallocTableOffset + sizeof(float) * 10 * kNoallocMaxAngles;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+// Persistent tiles of one problem: CTAs take tile numbers from the counter
+// at the start of the scratch array.
+template <int DIM, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(TX * TY * TZ, 1) noalloc_kernel(const StepArgs<float> a, int *counter) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_item;
+  const int ntx = (a.n[0] + TX - 1) / TX, nty = (a.n[1] + TY - 1) / TY, ntz = (a.n[2] + TZ - 1) / TZ;
+  const int ntiles = ntx * nty * ntz;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= ntiles) break;
+    stepk::process_tile<float, DIM, true, TX, TY, TZ>(a, threadIdx.x, it % ntx, (it / ntx) % nty, it / (ntx * nty),
+                                                     smem);
+    __syncthreads();
+  }
+}
+
+// Device address of the scratch array, looked up once per device.
+struct ScratchAddress {
+  std::mutex mu;
+  void *ptr[64] = {};
+};
+ScratchAddress g_addr;
+
+rt_status scratch_for_current_device(unsigned char **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_error(RT_E_CUDA, std::string("rt_step_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= 64) return set_error(RT_E_INVALID, "rt_step_noalloc: device ordinal above 63");
+  std::lock_guard<std::mutex> lock(g_addr.mu);
+  if (!g_addr.ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return set_error(RT_E_CUDA, std::string("rt_step_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_addr.ptr[dev] = p;
+  }
+  *out = static_cast<unsigned char *>(g_addr.ptr[dev]);
+  return RT_OK;
+}
+
+template <int DIM, int TX, int TY, int TZ>
+cudaError_t launch_noalloc(const StepArgs<float> &a, int *counter, cudaStream_t s) {
+  const size_t sm = stepk::smem_bytes(DIM, a.M, true, TX, TY, TZ, sizeof(float));
+  auto kern = noalloc_kernel<DIM, TX, TY, TZ>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, dev = 0, sms = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY * TZ, sm)) != cudaSuccess) return e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const long long ntiles = (long long)((a.n[0] + TX - 1) / TX) * ((a.n[1] + TY - 1) / TY) * ((a.n[2] + TZ - 1) / TZ);
+  const int grid = (int)std::max(1LL, std::min(ntiles, (long long)sms * std::max(1, per_sm)));
+  kern<<<grid, TX * TY * TZ, sm, s>>>(a, counter);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+}  // namespace rtg
+
+extern "C" rt_status rt_step_noalloc(const rt_grid *g, const rt_angles *ang, double Crat, double Prat,
+                                     const rt_options *opts, double dt, const rt_noalloc_fields *f,
+                                     int *newton_failures) {
+  using rtg::set_error;
+  if (!g || !ang || !ang->n || !ang->w || !opts || !f) return set_error(RT_E_INVALID, "rt_step_noalloc: NULL argument");
+  if (!f->I_in || !f->I_out || !f->rho || !f->sigma_a || !f->sigma_s || !f->v || !f->T || !f->mom_in ||
+      !f->mom_out || !f->dE_gas || !f->dMom)
+    return set_error(RT_E_INVALID, "rt_step_noalloc: NULL field pointer");
+  if (g->dim < 1 || g->dim > 3) return set_error(RT_E_INVALID, "rt_step_noalloc: dim must be 1, 2 or 3");
+  const int M = ang->m;
+  if (M < 1 || M > rtg::kNoallocMaxAngles)
+    return set_error(RT_E_INVALID, "rt_step_noalloc: angle count outside 1..256 (the fixed scratch holds 256)");
+  long long N = 1;
+  rtg::StepArgs<float> a;
+  a.dim = g->dim;
+  for (int d = 0; d < 3; ++d) {
+    const bool act = d < g->dim;
+    a.n[d] = act ? g->n[d] : 1;
+    if (act && (g->n[d] < 1 || !(g->hi[d] > g->lo[d])))
+      return set_error(RT_E_INVALID, "rt_step_noalloc: empty grid axis");
+    if (act && (g->bc[d][0] < RT_BC_PERIODIC || g->bc[d][0] > RT_BC_INFLOW || g->bc[d][1] < RT_BC_PERIODIC ||
+                g->bc[d][1] > RT_BC_INFLOW || (g->bc[d][0] == RT_BC_PERIODIC) != (g->bc[d][1] == RT_BC_PERIODIC)))
+      return set_error(RT_E_INVALID, "rt_step_noalloc: bad boundary kinds");
+    a.bc[d][0] = act ? g->bc[d][0] : RT_BC_PERIODIC;
+    a.bc[d][1] = act ? g->bc[d][1] : RT_BC_PERIODIC;
+    const double dx = act ? (g->hi[d] - g->lo[d]) / g->n[d] : 1.0;
+    a.dx[d] = (float)dx;
+    a.dtdx[d] = (float)(dt / dx);
+    N *= a.n[d];
+  }
+  if (N >= (1LL << 28)) return set_error(RT_E_INVALID, "rt_step_noalloc: more than 2^28 cells");
+  if (!(dt > 0) || !std::isfinite(dt) || !(Crat > 0) || !(Prat > 0) || !(opts->gamma > 1) || !(opts->r_ideal > 0))
+    return set_error(RT_E_INVALID, "rt_step_noalloc: need dt, Crat, Prat, r_ideal > 0 and gamma > 1");
+  if (opts->precision != RT_FP32) return set_error(RT_E_INVALID, "rt_step_noalloc: float intensities only (RT_FP32)");
+  const size_t sm_need = g->dim == 1   ? rtg::stepk::smem_bytes(1, M, true, 512, 1, 1, 4)
+                         : g->dim == 2 ? rtg::stepk::smem_bytes(2, M, true, 32, 16, 1, 4)
+                                       : rtg::stepk::smem_bytes(3, M, true, 16, 8, 4, 4);
+  if (sm_need > 227 * 1024) return set_error(RT_E_INVALID, "rt_step_noalloc: too many angles for one tile's shared memory");
+  double wsum = 0;
+  for (int m = 0; m < M; ++m) {
+    const double *nm = ang->n + 3 * m;
+    if (!(std::fabs(std::sqrt(nm[0] * nm[0] + nm[1] * nm[1] + nm[2] * nm[2]) - 1.0) <= 1e-12) || !(ang->w[m] > 0))
+      return set_error(RT_E_INVALID, "rt_step_noalloc: angles need |n| = 1 and W > 0");
+    wsum += ang->w[m];
+  }
+  if (!(std::fabs(wsum - 1.0) <= 1e-12)) return set_error(RT_E_INVALID, "rt_step_noalloc: weights must sum to 1");
+
+  unsigned char *scratch = nullptr;
+  rt_status st = rtg::scratch_for_current_device(&scratch);
+  if (st != RT_OK) return st;
+  int *counter = reinterpret_cast<int *>(scratch);
+  float *tab = reinterpret_cast<float *>(scratch + rtg::kNoallocTableOffset);
+  float host_tab[10 * rtg::kNoallocMaxAngles];
+  for (int m = 0; m < M; ++m) {
+    for (int d = 0; d < 3; ++d) host_tab[4 * m + d] = (float)ang->n[3 * m + d];
+    host_tab[4 * m + 3] = (float)ang->w[m];
+  }
+  for (int i = 0; i < 6 * M; ++i) host_tab[4 * M + i] = f->inflow ? (float)f->inflow[i] : 0.0f;
+  cudaStream_t s = (cudaStream_t)opts->stream;
+  cudaError_t e = cudaMemcpyAsync(tab, host_tab, sizeof(float) * 10 * M, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, 2 * sizeof(int), s);   // tile counter, failure word
+  if (e != cudaSuccess) return set_error(RT_E_CUDA, std::string("rt_step_noalloc: scratch set-up: ") + cudaGetErrorString(e));
+
+  a.M = M;
+  a.N = N;
+  a.C = (float)Crat;
+  a.invC = (float)(1.0 / Crat);
+  a.P = (float)Prat;
+  a.dt = (float)dt;
+  a.dt_d = dt;
+  a.kv_per_rho = opts->r_ideal / (opts->gamma - 1.0);
+  a.hold_T = opts->hold_T;
+  a.estimate_v = opts->estimate_v;
+  a.ang = tab;
+  a.inflow = tab + 4 * M;
+  a.I_in = f->I_in;
+  a.I_out = f->I_out;
+  a.rho = f->rho;
+  a.sa = f->sigma_a;
+  a.ss = f->sigma_s;
+  a.v = f->v;
+  a.T_in = f->T;
+  a.T_out = f->T;
+  a.mom_in = f->mom_in;
+  a.mom_out = f->mom_out;
+  a.dEgas = f->dE_gas;
+  a.dMom = f->dMom;
+  a.status = counter + 1;
+  e = g->dim == 1   ? rtg::launch_noalloc<1, 512, 1, 1>(a, counter, s)
+      : g->dim == 2 ? rtg::launch_noalloc<2, 32, 16, 1>(a, counter, s)
+                    : rtg::launch_noalloc<3, 16, 8, 4>(a, counter, s);
+  if (e != cudaSuccess) return set_error(RT_E_CUDA, std::string("rt_step_noalloc: launch: ") + cudaGetErrorString(e));
+  if (newton_failures) {
+    e = cudaMemcpyAsync(newton_failures, counter + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return set_error(RT_E_CUDA, std::string("rt_step_noalloc: status read: ") + cudaGetErrorString(e));
+  }
+  return RT_OK;
+}
