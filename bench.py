@@ -299,6 +299,12 @@ def run_gpu(args):
     clocks = sampler.summary()
     ctx.close()
 
+    batched = serving = None
+    if world == 1 and not args.no_batch:
+        batched = bench_batched(args, stream)
+    if world == 1 and not args.no_serve:
+        serving = bench_serving(args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload, 2, 1, sample_n=max(args.cpu_sample_n, 48))
@@ -315,6 +321,7 @@ def run_gpu(args):
                        "l2": "inputs larger than L2: %.2f GB of intensity read per step" % (N * M * rs / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
+            "batched": batched, "serving": serving,
         }
         print(json.dumps(line))
     if world > 1:
@@ -358,6 +365,137 @@ def _e2e(ctx, wl, N, M, stream, args, world):
             "d2h_bytes_per_step": d2h, "steps": k, "ms_per_step": 1e3 * el / k}
 
 
+def bench_batched(args, stream):
+    """Config 3: many uneven problems in one persistent launch per step, CUDA
+    graph; against stepping the same contexts one launch each."""
+    import torch
+    import paper_1403_6126_gb300 as rt
+    from paper_1403_6126_gb300 import workloads as wlmod
+    wls = wlmod.batched(nprob=args.batch_n)
+    ctxs, units, nbytes = [], 0, 0
+    for wl in wls:
+        n, w = _angles(wl["angles"])
+        c = _context(wl, n, w, stream=stream.cuda_stream)
+        c.set_intensity(wlmod.initial_intensity(wl, len(w)))
+        c.set_material(wl["rho"], wl["T"], wl["v"], wl["sa"], wl["ss"])
+        ctxs.append(c)
+        N = int(np.prod(wl["shape"]))
+        units += N * len(w)
+        nbytes += algorithmic_bytes_per_cell(len(w), 4, False, True) * N
+    b = rt.rt_batch_create(stream.cuda_stream)
+    for c in ctxs:
+        rt.rt_batch_add(b, c.ctx)
+    K = args.batch_steps
+    rt.rt_batch_step(b, 3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rt.rt_batch_step(b, K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    rt.rt_batch_destroy(b)
+    for c in ctxs:          # the same problems, one launch per problem per step
+        c.step(0.0)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(K):
+        for c in ctxs:
+            c.step(0.0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_one = e0.elapsed_time(e1) / K
+    for c in ctxs:
+        c.sync()
+        c.close()
+    peak, _ = _peaks()
+    return {"workload": "%d problems (half 1-D 64..4096 cells x 8..48 angles, half 2-D 32..256^2 x 8/24/48 angles), "
+                        "T live, float intensities" % len(wls),
+            "value": units / (ms / 1e3), "unit": "cell-angle updates/s", "ms_per_step": ms, "steps": K,
+            "cell_angles": units, "launches_per_step": 1,
+            "one_at_a_time": {"value": units / (ms_one / 1e3), "ms_per_step": ms_one, "launches_per_step": len(wls)},
+            "hbm": {"achieved": nbytes / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                    "frac": nbytes / (ms / 1e3) / 1e9 / peak}}
+
+
+def _submit_args(wl):
+    import ctypes
+    import paper_1403_6126_gb300 as rt
+    n, w = _angles(wl["angles"])
+    g = rt.rt_grid()
+    g.dim = wl["dim"]
+    nz, ny, nx = wl["shape"]
+    for d, nd in enumerate((nx, ny, nz)):
+        g.n[d] = nd
+        g.lo[d], g.hi[d] = wl["lo"][d], wl["hi"][d]
+        g.bc[d][0], g.bc[d][1] = wl["bc"][d]
+    a = rt.rt_angles()
+    a.m = len(w)
+    a.n = n.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    a.w = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    fields = [np.ascontiguousarray(wl[k], dtype=np.float64).reshape(-1) for k in ("rho", "T", "v", "sa", "ss")]
+    return g, a, (n, w), fields
+
+
+def bench_serving(args):
+    """Config 4 (scaled): a Poisson stream of 2-D / 3-D solves
+    into the continuous-batching server under an HBM budget; solves/s and
+    p50/p99 latency, against solving the same requests one at a time with
+    the FP64 path."""
+    import paper_1403_6126_gb300 as rt
+    from paper_1403_6126_gb300 import workloads as wlmod
+    wls = wlmod.serving(nreq=args.serve_n, steps=args.serve_steps)
+    reqs = [_submit_args(wl) for wl in wls]
+    o = rt.rt_options_default()
+    o.estimate_v, o.hold_T = 1, 0
+
+    def run(gaps):
+        server = rt.rt_server_create(int(args.serve_budget_gb * 2 ** 30), o)
+        t0 = time.perf_counter()
+        tickets = []
+        for (g, a, _, f), wl, gap in zip(reqs, wls, gaps):
+            while time.perf_counter() - t0 < gap:
+                time.sleep(0.0005)
+            tickets.append(rt.rt_submit(server, g, a, wl["C"], wl["P"], *f, wl["steps"]))
+        lat = []
+        for t in tickets:
+            rt.rt_server_wait(server, t, 600.0)
+            lat.append(rt.rt_poll(server, t))
+        makespan = time.perf_counter() - t0
+        steps = rt.rt_server_stats(server)["steps"]
+        rt.rt_server_destroy(server)
+        return makespan, np.array(lat), steps
+
+    burst, _, _ = run(np.zeros(len(reqs)))          # capacity: all at once
+    capacity = len(reqs) / burst
+    rng = np.random.default_rng(60)
+    arrivals = np.cumsum(rng.exponential(1.0 / (0.8 * capacity), len(reqs)))
+    arrivals -= arrivals[0]
+    makespan, lat, steps = run(arrivals)
+    # one at a time, FP64: time a subset, then scale to the whole stream by
+    # its cell-angle-steps (the subset's seconds per cell-angle-step)
+    work = [int(np.prod(wl["shape"])) * len(r[2][1]) * wl["steps"] for r, wl in zip(reqs, wls)]
+    k = max(1, min(len(reqs), args.serve_fp64_n))
+    t0 = time.perf_counter()
+    for (g, a, (n, w), f), wl in list(zip(reqs, wls))[:k]:
+        c = _context(wl, n, w, precision="fp64")
+        c.set_material(*f)
+        c.run(0.0, wl["steps"])
+        c.sync()
+        c.moments()
+        c.close()
+    fp64_s = time.perf_counter() - t0
+    fp64_rate = len(reqs) / (fp64_s * sum(work) / sum(work[:k]))
+    return {"workload": "%d requests: 2-D 64..512^2 and 3-D 64..192^3, 24/80 angles, %d steps each, box gas fields; "
+                        "Poisson arrivals at 0.8 x measured capacity" % (len(reqs), args.serve_steps),
+            "value": len(reqs) / makespan, "unit": "solves/s", "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)), "capacity_solves_s": capacity,
+            "batch_steps": steps, "budget_gb": args.serve_budget_gb,
+            "fp64_one_at_a_time": {"value": fp64_rate, "unit": "solves/s", "timed_requests": k,
+                                   "note": "first %d requests timed (%.1f s), scaled to the whole stream by "
+                                           "cell-angle-steps" % (k, fp64_s)}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -370,6 +508,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=32)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--batch-n", type=int, default=512)
+    ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--serve-n", type=int, default=32)
+    ap.add_argument("--serve-steps", type=int, default=200)
+    ap.add_argument("--serve-fp64-n", type=int, default=6)
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3

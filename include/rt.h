@@ -220,6 +220,43 @@ rt_status rt_batch_step(rt_batch *b, int nsteps);
 /* Frees the batch (not its contexts).  NULL is ignored. */
 void rt_batch_destroy(rt_batch *b);
 
+/* ---- serving: continuous batching of solves ---------------------------------
+ * A server runs one host thread.  rt_submit copies a request (the fields of
+ * rt_create / rt_set_material, host memory, plus a step count) and returns a
+ * ticket at once.  The thread admits queued requests in arrival order
+ * whenever the HBM budget has room (a request that does not fit yet does not
+ * block smaller ones behind it), keeps their state on the device, and
+ * advances every admitted problem one step per persistent launch (rt_batch),
+ * so requests arriving while others run join at the next step boundary.  A
+ * finished problem's E_r, F_r, P_r are copied to host memory and its device
+ * state is freed.  Requests run with RT_FP32, CFL time steps and the
+ * server's options (gamma, r_ideal, hold_T, estimate_v; stream and
+ * device_ptrs are the server's own).  Each result is bitwise the one the
+ * problem gets alone through rt_step with the same velocity setting. */
+typedef struct rt_server rt_server;
+typedef long long rt_ticket;
+
+/* hbm_budget_bytes bounds the device memory of the admitted problems (each
+ * costs about 8*M + 240 bytes per cell with float intensities). */
+rt_status rt_server_create(size_t hbm_budget_bytes, const rt_options *opts, rt_server **out);
+/* v is 3N, the others N; nsteps >= 1.  RT_E_BUDGET if the problem alone
+ * exceeds the budget, RT_E_INVALID for bad sizes or too many angles. */
+rt_status rt_submit(rt_server *s, const rt_grid *grid, const rt_angles *angles, double Crat, double Prat,
+                    const double *rho, const double *T, const double *v, const double *sigma_a,
+                    const double *sigma_s, int nsteps, rt_ticket *out);
+/* Non-blocking.  RT_PENDING while the request is queued or running.  Once
+ * it is done: RT_OK and E (N), F (3N), P (6N) copied out (NULL skips a
+ * field) with the submit-to-result latency in seconds, or the request's
+ * error status; either way the ticket is then released. */
+rt_status rt_poll(rt_server *s, rt_ticket t, double *E, double *F, double *P, double *latency_s);
+/* Blocks until the request is done (timeout_s < 0: no limit); RT_E_TIMEOUT
+ * when the limit passes first.  Does not release the ticket. */
+rt_status rt_server_wait(rt_server *s, rt_ticket t, double timeout_s);
+/* Steps launched so far, requests queued / running, device bytes in use. */
+rt_status rt_server_stats(rt_server *s, long long *steps, int *queued, int *running, size_t *bytes_in_use);
+/* Stops the thread and frees everything, including uncollected results. */
+void rt_server_destroy(rt_server *s);
+
 /* ---- one step without device allocation ------------------------------------
  * The paper has no counterpart: this is a service for callers that cannot
  * allocate device memory -- code running inside another framework's memory

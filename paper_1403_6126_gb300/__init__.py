@@ -92,6 +92,14 @@ def lib():
             "rt_batch_size": (I, [V]),
             "rt_batch_step": (I, [V, I]),
             "rt_batch_destroy": (None, [V]),
+            "rt_server_create": (I, [ctypes.c_size_t, ctypes.POINTER(rt_options), ctypes.POINTER(V)]),
+            "rt_submit": (I, [V, ctypes.POINTER(rt_grid), ctypes.POINTER(rt_angles), D, D, V, V, V, V, V, I,
+                              ctypes.POINTER(ctypes.c_longlong)]),
+            "rt_poll": (I, [V, ctypes.c_longlong, V, V, V, ctypes.POINTER(D)]),
+            "rt_server_wait": (I, [V, ctypes.c_longlong, D]),
+            "rt_server_stats": (I, [V, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(I), ctypes.POINTER(I),
+                                    ctypes.POINTER(ctypes.c_size_t)]),
+            "rt_server_destroy": (None, [V]),
             "rt_step_noalloc": (I, [ctypes.POINTER(rt_grid), ctypes.POINTER(rt_angles), D, D, ctypes.POINTER(rt_options),
                                     D, ctypes.POINTER(rt_noalloc_fields), ctypes.POINTER(I)]),
             "rt_last_error": (ctypes.c_char_p, []),
@@ -228,6 +236,44 @@ def rt_batch_step(b, nsteps):
 
 def rt_batch_destroy(b):
     lib().rt_batch_destroy(b)
+
+
+def rt_server_create(hbm_budget_bytes, opts):
+    out = ctypes.c_void_p()
+    _check(lib().rt_server_create(hbm_budget_bytes, ctypes.byref(opts), ctypes.byref(out)), "rt_server_create")
+    return out
+
+
+def rt_submit(server, grid, angles, Crat, Prat, rho, T, v, sigma_a, sigma_s, nsteps):
+    t = ctypes.c_longlong(0)
+    _check(lib().rt_submit(server, ctypes.byref(grid), ctypes.byref(angles), Crat, Prat, _ptr(rho), _ptr(T), _ptr(v),
+                           _ptr(sigma_a), _ptr(sigma_s), nsteps, ctypes.byref(t)), "rt_submit")
+    return t.value
+
+
+def rt_poll(server, ticket, E=None, F=None, P=None):
+    """Returns None while pending, else the latency in seconds (E, F, P filled)."""
+    lat = ctypes.c_double(0.0)
+    st = lib().rt_poll(server, ticket, _ptr(E), _ptr(F), _ptr(P), ctypes.byref(lat))
+    if st == RT_PENDING:
+        return None
+    _check(st, "rt_poll")
+    return lat.value
+
+
+def rt_server_wait(server, ticket, timeout_s=-1.0):
+    _check(lib().rt_server_wait(server, ticket, timeout_s), "rt_server_wait")
+
+
+def rt_server_stats(server):
+    steps, q, r, b = ctypes.c_longlong(0), ctypes.c_int(0), ctypes.c_int(0), ctypes.c_size_t(0)
+    _check(lib().rt_server_stats(server, ctypes.byref(steps), ctypes.byref(q), ctypes.byref(r), ctypes.byref(b)),
+           "rt_server_stats")
+    return dict(steps=steps.value, queued=q.value, running=r.value, bytes_in_use=b.value)
+
+
+def rt_server_destroy(server):
+    lib().rt_server_destroy(server)
 
 
 def rt_step_noalloc(grid, angles, Crat, Prat, opts, dt, fields, want_failures=True):

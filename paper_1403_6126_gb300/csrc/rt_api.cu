@@ -91,6 +91,12 @@ rtg::StepArgs<Real> rtg::make_args(rt_ctx *c, double dt) {
   return a;
 }
 
+size_t rtg::context_bytes(long long N, int M, bool fp64) {
+  const size_t rs = fp64 ? 8 : 4, Nz = (size_t)N, Mz = (size_t)M;
+  const size_t stage = sizeof(double) * std::max<size_t>(10 * Nz, 8 * Mz);
+  return rs * (2 * Mz * Nz + 2 * 10 * Nz + 6 * Nz + 3 * Nz + 10 * Mz) + 16 * Nz + 2 * sizeof(int) + stage;
+}
+
 template rtg::StepArgs<float> rtg::make_args<float>(rt_ctx *, double);
 template rtg::StepArgs<double> rtg::make_args<double>(rt_ctx *, double);
 

@@ -61,6 +61,13 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
 static_assert(kB1X == kBatchThreads && kB2X * kB2Y == kBatchThreads && kB3X * kB3Y * kB3Z == kBatchThreads,
               "every tile shape of the persistent kernel has one thread per cell");
 
+bool batch_fits(int dim, int M, bool vel) {
+  size_t sm = dim == 1   ? stepk::smem_bytes(1, M, vel, kB1X, 1, 1, 4)
+              : dim == 2 ? stepk::smem_bytes(2, M, vel, kB2X, kB2Y, 1, 4)
+                         : stepk::smem_bytes(3, M, vel, kB3X, kB3Y, kB3Z, 4);
+  return sm <= 227 * 1024;
+}
+
 }  // namespace rtg
 
 struct rt_batch {

@@ -48,4 +48,8 @@ StepArgs<Real> make_args(rt_ctx *c, double dt);
 bool velocity_on(const rt_ctx *c);
 // Records msg as this thread's last error and returns s.
 rt_status set_error(rt_status s, const std::string &msg);
+// Device bytes rt_create allocates for N cells and M angles.
+size_t context_bytes(long long N, int M, bool fp64);
+// Whether a problem of this dimension and angle count fits the batch tile.
+bool batch_fits(int dim, int M, bool vel);
 }  // namespace rtg

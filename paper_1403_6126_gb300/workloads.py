@@ -75,37 +75,105 @@ def shadow2d(nx=256, ny=128, angles="s8", steps=4000, precision="fp32"):
     )
 
 
-def box3d(n=128, angles="s8", seed=2, steps=500, precision="fp32"):
-    """3-D periodic box [0, 1]^3 (the sec. 6 performance setup, radiation
-    dominated): rho = exp(0.5 g - 1/8) with g a unit Gaussian random field,
-    P(k) ~ k^-2 on 1 <= |k| <= 16 (seed); v a Gaussian random vector field
+def _gas_fields(shape, C, seed, kmax):
+    """rho, v, sigma_a, sigma_s of the box recipe on a periodic grid of the
+    given shape: rho = exp(0.5 g - 1/8) with g a unit Gaussian random field,
+    P(k) ~ k^-2 on 1 <= |k| <= kmax (seed); v a Gaussian random vector field
     (seed + 1) scaled to rms |v| = 0.05 Crat, then |v|/Crat clipped into
     [0.01, 0.1] keeping the direction; sigma_a, sigma_s = 10^U(0, 3) per cell
-    (seed + 2); T0 = 1, I0 = 1/(4 pi); Crat = 100, Prat = 100, gamma = 5/3,
-    R = 1, Courant 0.4; T live, velocity estimate on."""
-    shape = (n, n, n)
-    C = 100.0
-    g = _spectral_field(np.random.default_rng(seed), shape, 1.0, min(16.0, n / 2), -2.0)
+    (seed + 2)."""
+    g = _spectral_field(np.random.default_rng(seed), shape, 1.0, kmax, -2.0)
     rho = np.exp(0.5 * g - 0.125)
     rv = np.random.default_rng(seed + 1)
-    v = np.stack([_spectral_field(rv, shape, 1.0, min(16.0, n / 2), -2.0) for _ in range(3)])
+    v = np.stack([_spectral_field(rv, shape, 1.0, kmax, -2.0) for _ in range(3)])
     speed = np.sqrt((v ** 2).sum(axis=0))
     v *= 0.05 * C / np.sqrt((speed ** 2).mean())
     speed = np.sqrt((v ** 2).sum(axis=0))
     target = np.clip(speed, 0.01 * C, 0.1 * C)
     v *= target / np.maximum(speed, 1e-300)
     ro = np.random.default_rng(seed + 2)
-    N = n ** 3
+    N = int(np.prod(shape))
     sa = 10.0 ** ro.uniform(0.0, 3.0, N)
     ss = 10.0 ** ro.uniform(0.0, 3.0, N)
+    return rho.reshape(N), v.reshape(3, N), sa, ss
+
+
+def box3d(n=128, angles="s8", seed=2, steps=500, precision="fp32", kmax=None):
+    """3-D periodic box [0, 1]^3 (the sec. 6 performance setup, radiation
+    dominated), gas fields from _gas_fields with kmax = min(16, n/2) unless
+    given; T0 = 1, I0 = 1/(4 pi); Crat = 100, Prat = 100, gamma = 5/3,
+    R = 1, Courant 0.4; T live, velocity estimate on."""
+    shape = (n, n, n)
+    C = 100.0
+    rho, v, sa, ss = _gas_fields(shape, C, seed, min(16.0, n / 2) if kmax is None else kmax)
+    N = n ** 3
     return dict(
         name="box3d", shape=shape, dim=3, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
         bc=((PERIODIC, PERIODIC),) * 3,
         angles=angles, C=C, P=100.0, gamma=5.0 / 3.0, R=1.0, cfl=0.4, hold_T=False, estimate_v=True,
         steps=steps, precision=precision,
-        rho=rho.reshape(N), T=np.ones(N), v=v.reshape(3, N), sa=sa, ss=ss,
+        rho=rho, T=np.ones(N), v=v, sa=sa, ss=ss,
         I0="isotropic_quarter_pi", inflow={},
     )
+
+
+def box2d(n=256, angles="s8", seed=2, steps=500, precision="fp32", kmax=None):
+    """The box recipe on a periodic square [0, 1]^2 (one cell in z): gas
+    fields from _gas_fields on (1, n, n), kmax = min(16, n/2) unless given,
+    the rest as in box3d."""
+    wl = box3d(n=2, angles=angles, seed=seed, steps=steps, precision=precision, kmax=1.0)
+    rho, v, sa, ss = _gas_fields((1, n, n), wl["C"], seed, min(16.0, n / 2) if kmax is None else kmax)
+    wl.update(name="box2d", shape=(1, n, n), dim=2, rho=rho, T=np.ones(n * n), v=v, sa=sa, ss=ss)
+    return wl
+
+
+def batched(nprob=512, seed=5, steps=200):
+    """Many independent problems of uneven size: half 1-D slabs (cells
+    log-uniform in 64..4096, Gauss-Legendre M in {8,16,24,32,40,48}, copy /
+    vacuum ends), half 2-D periodic boxes (nx, ny log-uniform in 32..256
+    independently, S2/S4/S6 = 8/24/48 angles).  Opacities as in slab1d
+    (sigma_a = 1e-2, sigma_s = 10^U(-1,2) per cell), rho = 1, T = 1 live,
+    v = 0, Crat = 10, Prat = 1, float intensities."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(nprob):
+        if i % 2 == 0:
+            n = int(round(np.exp(rng.uniform(np.log(64), np.log(4096)))))
+            M = int(rng.choice([8, 16, 24, 32, 40, 48]))
+            wl = slab1d(n=n, M=M, seed=int(rng.integers(1 << 30)), steps=steps)
+        else:
+            nx = int(round(np.exp(rng.uniform(np.log(32), np.log(256)))))
+            ny = int(round(np.exp(rng.uniform(np.log(32), np.log(256)))))
+            ang = str(rng.choice(["s2", "s4", "s6"]))
+            N = nx * ny
+            r2 = np.random.default_rng(int(rng.integers(1 << 30)))
+            wl = dict(name="box2d", shape=(1, ny, nx), dim=2, lo=(0.0, 0.0, 0.0), hi=(1.0, ny / nx, 1.0),
+                      bc=((PERIODIC, PERIODIC),) * 3, angles=ang, C=10.0, P=1.0, gamma=5.0 / 3.0, R=1.0, cfl=0.4,
+                      estimate_v=False, steps=steps, rho=np.ones(N), T=np.ones(N), v=np.zeros((3, N)),
+                      sa=np.full(N, 1e-2), ss=10.0 ** r2.uniform(-1.0, 2.0, N), I0="isotropic_quarter_pi",
+                      inflow={})
+        wl["hold_T"] = False
+        wl["precision"] = "fp32"
+        out.append(wl)
+    return out
+
+
+def serving(nreq=32, seed=6, steps=200, scale=1.0):
+    """Requests for the serving loop: even ones 2-D (side log-uniform in
+    64..512 x scale), odd ones 3-D (side log-uniform in 64..192 x scale),
+    24 or 80 angles (S4 / S8), gas fields as in box3d with the velocity
+    spectrum cut at side/8 (at least eight cells across its shortest
+    wavelength), each `steps` steps; the arrival gaps are drawn by the
+    caller."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(nreq):
+        ang = str(rng.choice(["s4", "s8"]))
+        lo, hi = (64, 512) if i % 2 == 0 else (64, 192)
+        side = max(4, int(round(np.exp(rng.uniform(np.log(lo * scale), np.log(hi * scale))))))
+        make = box2d if i % 2 == 0 else box3d
+        out.append(make(n=side, angles=ang, seed=int(rng.integers(1 << 20)), steps=steps, kmax=max(1.0, side / 8)))
+    return out
 
 
 def initial_intensity(wl, M):

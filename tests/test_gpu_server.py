@@ -1,0 +1,127 @@
+"""Serving loop: continuous batching.  Requests that arrive while others run
+are admitted as memory frees up, share the persistent launches, and each
+result is bitwise the one the problem gets alone."""
+import ctypes
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1403_6126_gb300 as rt
+from paper_1403_6126_gb300 import workloads as wlmod
+
+from _helpers import gpu_context
+
+pytestmark = pytest.mark.gpu
+
+
+def _request(wl):
+    n, w = oracle.angles.by_name(wl["angles"])
+    n, w = np.ascontiguousarray(n), np.ascontiguousarray(w)
+    g = rt.rt_grid()
+    g.dim = wl["dim"]
+    nz, ny, nx = wl["shape"]
+    for d, nd in enumerate((nx, ny, nz)):
+        g.n[d] = nd
+        g.lo[d], g.hi[d] = wl["lo"][d], wl["hi"][d]
+        g.bc[d][0], g.bc[d][1] = wl["bc"][d]
+    a = rt.rt_angles()
+    a.m = len(w)
+    a.n = n.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    a.w = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    fields = [np.ascontiguousarray(wl[k], dtype=np.float64).reshape(-1) for k in ("rho", "T", "v", "sa", "ss")]
+    return g, a, (n, w), fields
+
+
+def _problems():
+    out = []
+    for n, ang in ((10, "s4"), (12, "s2"), (8, "s6"), (14, "s2")):
+        out.append(wlmod.box3d(n=n, angles=ang, seed=n, steps=0))
+    for nx, ny, ang in ((40, 24, "s4"), (33, 17, "s2")):
+        wl = wlmod.shadow2d(nx=nx, ny=ny, angles=ang, steps=0)
+        wl["bc"] = ((0, 0), (0, 0), (0, 0))   # periodic: the server takes no inflow tables
+        wl["inflow"] = {}
+        wl["v"][0] = 0.04 * wl["C"]
+        out.append(wl)
+    for wl in out:
+        wl["estimate_v"], wl["hold_T"] = True, False
+    return out
+
+
+def _opts():
+    o = rt.rt_options_default()
+    o.estimate_v, o.hold_T = 1, 0
+    return o
+
+
+def _alone(wl, nsteps):
+    n, w = oracle.angles.by_name(wl["angles"])
+    ctx = gpu_context(wl, n, w, "fp32")
+    ctx.set_material(wl["rho"], wl["T"], wl["v"], wl["sa"], wl["ss"])
+    for _ in range(nsteps):
+        ctx.step(0.0)
+    ctx.sync()
+    out = ctx.moments()
+    ctx.close()
+    return out
+
+
+def test_server_results_equal_each_problem_alone():
+    probs = _problems()
+    steps = [3, 5, 2, 4, 6, 1]
+    # budget: room for the two largest requests at a time, so the rest queue
+    N = [int(np.prod(p["shape"])) for p in probs]
+    M = [len(oracle.angles.by_name(p["angles"])[1]) for p in probs]
+    per = sorted((Ni * (8 * Mi + 240) * 2 for Ni, Mi in zip(N, M)), reverse=True)
+    server = rt.rt_server_create(per[0] + per[1], _opts())
+    keep, tickets = [], []
+    for i, wl in enumerate(probs[:3]):
+        g, a, angs, fields = _request(wl)
+        keep.append((g, a, angs, fields))
+        tickets.append(rt.rt_submit(server, g, a, wl["C"], wl["P"], *fields, steps[i]))
+    rt.rt_server_wait(server, tickets[0], 60.0)
+    for i, wl in enumerate(probs[3:], start=3):   # arrive while others run
+        g, a, angs, fields = _request(wl)
+        keep.append((g, a, angs, fields))
+        tickets.append(rt.rt_submit(server, g, a, wl["C"], wl["P"], *fields, steps[i]))
+    results = []
+    for i, t in enumerate(tickets):
+        rt.rt_server_wait(server, t, 120.0)
+        E, F, P = np.zeros(N[i]), np.zeros((3, N[i])), np.zeros((6, N[i]))
+        lat = rt.rt_poll(server, t, E, F, P)
+        assert lat is not None and lat > 0
+        results.append((E, F, P))
+    stats = rt.rt_server_stats(server)
+    assert stats["queued"] == 0 and stats["running"] == 0 and stats["bytes_in_use"] == 0
+    assert stats["steps"] >= max(steps)
+    rt.rt_server_destroy(server)
+    for wl, s, (E, F, P) in zip(probs, steps, results):
+        Ea, Fa, Pa = _alone(wl, s)
+        np.testing.assert_array_equal(E, Ea)
+        np.testing.assert_array_equal(F, Fa)
+        np.testing.assert_array_equal(P, Pa)
+
+
+def test_server_errors_and_timeouts():
+    # a long request in a static medium (no velocity: stays in equilibrium)
+    wl = wlmod.box3d(n=32, angles="s8", steps=0)
+    wl["v"] = np.zeros_like(wl["v"])
+    g, a, angs, fields = _request(wl)
+    small = rt.rt_server_create(1 << 20, _opts())
+    with pytest.raises(rt.RTError) as e:
+        rt.rt_submit(small, g, a, wl["C"], wl["P"], *fields, 10)
+    assert e.value.status == rt.RT_E_BUDGET
+    rt.rt_server_destroy(small)
+    server = rt.rt_server_create(8 << 30, _opts())
+    t = rt.rt_submit(server, g, a, wl["C"], wl["P"], *fields, 400)
+    with pytest.raises(rt.RTError) as e:
+        rt.rt_server_wait(server, t, 0.0)
+    assert e.value.status == rt.RT_E_TIMEOUT
+    assert rt.rt_poll(server, t) is None          # still pending
+    rt.rt_server_wait(server, t, 300.0)
+    assert rt.rt_poll(server, t) > 0
+    with pytest.raises(rt.RTError) as e:
+        rt.rt_poll(server, t)                      # ticket released
+    assert e.value.status == rt.RT_E_INVALID
+    rt.rt_server_destroy(server)
