@@ -16,6 +16,12 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "librt_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
+# Units that instantiate the float step kernel (rt_step_pair.cuh).  Its
+# per-angle arithmetic spells out every fused multiply-add it wants; these
+# units are compiled without implicit contraction so that the per-cell code
+# rounds the same way wherever it is inlined: the single-problem, batch and
+# allocation-free kernels then give bitwise equal results.
+NO_CONTRACT = {"rt_step_f3.cu", "rt_step_f12.cu", "rt_batch.cu", "rt_noalloc.cu"}
 
 
 def _sources():
@@ -24,7 +30,7 @@ def _sources():
 
 def _inputs():
     return (_sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
-            + glob.glob(os.path.join(INCLUDE, "*.h")))
+            + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)])
 
 
 def up_to_date():
@@ -45,6 +51,8 @@ def build(force=False, verbose=False):
         obj = os.path.join(objdir, os.path.basename(src) + ".o")
         cmd = [NVCC] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
                                "-c", src, "-o", obj]
+        if os.path.basename(src) in NO_CONTRACT:
+            cmd += ["-fmad=false"]
         if src.endswith(".cu"):
             cmd += ["-Xptxas", "-warn-spills"] if verbose else []
         procs.append((src, obj, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

@@ -16,7 +16,7 @@
 
 #include "rt.h"
 #include "rt_ctx.h"
-#include "rt_step_kernel.cuh"
+#include "rt_step_pair.cuh"
 
 namespace rtg {
 
@@ -49,11 +49,11 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
     for (int i = tid; i < (int)(sizeof(StepArgs<float>) / sizeof(int)); i += kBatchThreads) dst[i] = src[i];
     __syncthreads();
     if (desc.dim == 3)
-      stepk::process_tile<float, 3, VEL, kB3X, kB3Y, kB3Z>(desc, tid, w.tbx, w.tby, w.tbz, smem);
+      stepk::process_tile2<3, VEL, kB3X, kB3Y, kB3Z>(desc, tid, w.tbx, w.tby, w.tbz, smem);
     else if (desc.dim == 2)
-      stepk::process_tile<float, 2, VEL, kB2X, kB2Y, 1>(desc, tid, w.tbx, w.tby, 0, smem);
+      stepk::process_tile2<2, VEL, kB2X, kB2Y, 1>(desc, tid, w.tbx, w.tby, 0, smem);
     else
-      stepk::process_tile<float, 1, VEL, kB1X, 1, 1>(desc, tid, w.tbx, 0, 0, smem);
+      stepk::process_tile2<1, VEL, kB1X, 1, 1>(desc, tid, w.tbx, 0, 0, smem);
     __syncthreads();   // every thread has read s_item and desc
   }
 }
@@ -62,9 +62,9 @@ static_assert(kB1X == kBatchThreads && kB2X * kB2Y == kBatchThreads && kB3X * kB
               "every tile shape of the persistent kernel has one thread per cell");
 
 bool batch_fits(int dim, int M, bool vel) {
-  size_t sm = dim == 1   ? stepk::smem_bytes(1, M, vel, kB1X, 1, 1, 4)
-              : dim == 2 ? stepk::smem_bytes(2, M, vel, kB2X, kB2Y, 1, 4)
-                         : stepk::smem_bytes(3, M, vel, kB3X, kB3Y, kB3Z, 4);
+  size_t sm = dim == 1   ? stepk::smem_bytes2(1, M, vel, kB1X, 1, 1)
+              : dim == 2 ? stepk::smem_bytes2(2, M, vel, kB2X, kB2Y, 1)
+                         : stepk::smem_bytes2(3, M, vel, kB3X, kB3Y, kB3Z);
   return sm <= 227 * 1024;
 }
 
@@ -126,9 +126,9 @@ rt_status rebuild(rt_batch *b) {
         for (int x = 0; x < (c->n[0] + tx - 1) / tx; ++x) items.push_back({i, x, y, z});
   }
   size_t smem = 0;
-  if (dims[1]) smem = std::max(smem, rtg::stepk::smem_bytes(1, Mmax, b->vel, rtg::kB1X, 1, 1, 4));
-  if (dims[2]) smem = std::max(smem, rtg::stepk::smem_bytes(2, Mmax, b->vel, rtg::kB2X, rtg::kB2Y, 1, 4));
-  if (dims[3]) smem = std::max(smem, rtg::stepk::smem_bytes(3, Mmax, b->vel, rtg::kB3X, rtg::kB3Y, rtg::kB3Z, 4));
+  if (dims[1]) smem = std::max(smem, rtg::stepk::smem_bytes2(1, Mmax, b->vel, rtg::kB1X, 1, 1));
+  if (dims[2]) smem = std::max(smem, rtg::stepk::smem_bytes2(2, Mmax, b->vel, rtg::kB2X, rtg::kB2Y, 1));
+  if (dims[3]) smem = std::max(smem, rtg::stepk::smem_bytes2(3, Mmax, b->vel, rtg::kB3X, rtg::kB3Y, rtg::kB3Z));
   if (smem > 227 * 1024)
     return rtg::set_error(RT_E_INVALID, "rt_batch: the largest angle set does not fit the batch tile in shared memory");
   b->smem = smem;

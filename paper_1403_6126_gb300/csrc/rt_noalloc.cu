@@ -21,7 +21,7 @@
 
 #include "rt.h"
 #include "rt_ctx.h"
-#include "rt_step_kernel.cuh"
+#include "rt_step_pair.cuh"
 
 namespace rtg {
 
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, 1) noalloc_kernel(const StepArgs
     __syncthreads();
     const int it = s_item;
     if (it >= ntiles) break;
-    stepk::process_tile<float, DIM, true, TX, TY, TZ>(a, threadIdx.x, it % ntx, (it / ntx) % nty, it / (ntx * nty),
+    stepk::process_tile2<DIM, true, TX, TY, TZ>(a, threadIdx.x, it % ntx, (it / ntx) % nty, it / (ntx * nty),
                                                      smem);
     __syncthreads();
   }
@@ -81,7 +81,7 @@ rt_status scratch_for_current_device(unsigned char **out) {
 
 template <int DIM, int TX, int TY, int TZ>
 cudaError_t launch_noalloc(const StepArgs<float> &a, int *counter, cudaStream_t s) {
-  const size_t sm = stepk::smem_bytes(DIM, a.M, true, TX, TY, TZ, sizeof(float));
+  const size_t sm = stepk::smem_bytes2(DIM, a.M, true, TX, TY, TZ);
   auto kern = noalloc_kernel<DIM, TX, TY, TZ>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
@@ -133,9 +133,9 @@ extern "C" rt_status rt_step_noalloc(const rt_grid *g, const rt_angles *ang, dou
   if (!(dt > 0) || !std::isfinite(dt) || !(Crat > 0) || !(Prat > 0) || !(opts->gamma > 1) || !(opts->r_ideal > 0))
     return set_error(RT_E_INVALID, "rt_step_noalloc: need dt, Crat, Prat, r_ideal > 0 and gamma > 1");
   if (opts->precision != RT_FP32) return set_error(RT_E_INVALID, "rt_step_noalloc: float intensities only (RT_FP32)");
-  const size_t sm_need = g->dim == 1   ? rtg::stepk::smem_bytes(1, M, true, 512, 1, 1, 4)
-                         : g->dim == 2 ? rtg::stepk::smem_bytes(2, M, true, 32, 16, 1, 4)
-                                       : rtg::stepk::smem_bytes(3, M, true, 16, 8, 4, 4);
+  const size_t sm_need = g->dim == 1   ? rtg::stepk::smem_bytes2(1, M, true, 512, 1, 1)
+                         : g->dim == 2 ? rtg::stepk::smem_bytes2(2, M, true, 32, 16, 1)
+                                       : rtg::stepk::smem_bytes2(3, M, true, 16, 8, 4);
   if (sm_need > 227 * 1024) return set_error(RT_E_INVALID, "rt_step_noalloc: too many angles for one tile's shared memory");
   double wsum = 0;
   for (int m = 0; m < M; ++m) {

@@ -1,7 +1,8 @@
-// Tile choice and dispatch of the fused step kernel (rt_step_kernel.cuh):
+// Tile choice and dispatch of the fused step kernels (rt_step_pair.cuh for
+// float intensities, rt_step_kernel.cuh for double):
 // the compiled shapes are listed in rt_shapes.h.
 #include "rt_shapes.h"
-#include "rt_step_kernel.cuh"
+#include "rt_step_pair.cuh"
 
 namespace rtg {
 
@@ -24,6 +25,15 @@ int shape_list(int dim, TileShape *out) {
   return n;
 }
 
+// Shared memory of a shape within the opt-in limit: the pair kernel for
+// float, the scalar kernel for double.
+template <typename Real>
+bool fits(int dim, int M, bool has_v, TileShape t) {
+  const size_t sm = sizeof(Real) == 4 ? stepk::smem_bytes2(dim, M, has_v, t.tx, t.ty, t.tz)
+                                      : stepk::smem_bytes(dim, M, has_v, t.tx, t.ty, t.tz, sizeof(Real));
+  return sm <= 227 * 1024;
+}
+
 }  // namespace
 
 template <typename Real>
@@ -32,7 +42,7 @@ bool tile_ok(int dim, int M, bool has_v, TileShape t) {
   int n = shape_list<Real>(dim, list);
   for (int i = 0; i < n; ++i)
     if (list[i].tx == t.tx && list[i].ty == t.ty && list[i].tz == t.tz)
-      return stepk::shape_fits(dim, M, has_v, t, sizeof(Real));
+      return fits<Real>(dim, M, has_v, t);
   return false;
 }
 
@@ -41,7 +51,7 @@ bool choose_tile(int dim, int M, bool has_v, TileShape *out) {
   TileShape list[8];
   int n = shape_list<Real>(dim, list);
   for (int i = 0; i < n; ++i) {
-    if (stepk::shape_fits(dim, M, has_v, list[i], sizeof(Real))) {
+    if (fits<Real>(dim, M, has_v, list[i])) {
       *out = list[i];
       return true;
     }

@@ -1,0 +1,638 @@
+// Fused radiation-transfer step with float intensities, two angles per
+// thread (Jiang, Stone & Davis 2014, arXiv:1403.6126, secs. 3-4).
+//
+// Same algorithm, tile geometry and phases as process_tile in
+// rt_step_kernel.cuh, with every per-angle quantity carried as a pair
+// (angles 2k and 2k + 1) through the packed FP32 instructions of sm_100-class
+// GPUs (__ffma2_rn, __fadd2_rn, __fmul2_rn): one instruction does the
+// arithmetic of both angles, one 64-bit shared-memory access moves both, and
+// one barrier serves both.  An odd angle count is padded with a weightless
+// dummy angle (n = 0, W = 0): it adds nothing to any angle sum and is never
+// stored.
+//
+// Two further differences from the scalar kernel:
+//  * The right-hand sides Q_m of the implicit steps go to the output
+//    intensity array instead of shared memory.  Each thread writes Q_m of its
+//    cell for every angle, and after the cell solve reads them back and
+//    overwrites them with I^{n+1}.  A tile's Q (cells x angles x 4 bytes)
+//    stays in L2 between the two passes, so HBM sees one write per value,
+//    and shared memory holds only the staging arrays: a 512-cell tile keeps
+//    its shape for any angle count up to 256.
+//  * The Step 4 / Step 5 sums that depend only on the velocity and the
+//    opacities (powers of vn over d_m, the coefficient sums of the 2x2
+//    system) are taken in a separate loop after the transport loop, which
+//    keeps them out of the registers the transport phases need.
+#pragma once
+
+#include "rt_step_kernel.cuh"
+
+namespace rtg {
+
+namespace stepk {
+
+using f2 = float2;
+
+__device__ __forceinline__ f2 dup(float x) { return make_float2(x, x); }
+__device__ __forceinline__ f2 p_add(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 p_mul(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 p_fma(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+// a - b: the negation is exact, so one fused multiply-add rounds once
+__device__ __forceinline__ f2 p_sub(f2 a, f2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ f2 p_rcp(f2 a) { return make_float2(fast_rcp(a.x), fast_rcp(a.y)); }
+
+// Half van Leer slopes of two angles (see vl_half).
+__device__ __forceinline__ f2 vl_half2(f2 qm, f2 q0, f2 qp) {
+  const f2 dl = p_sub(q0, qm), dr = p_sub(qp, q0);
+  const f2 pr = p_mul(dl, dr);
+  const f2 h = p_mul(pr, p_rcp(p_add(dl, dr)));
+  return make_float2(pr.x > 0.0f ? h.x : 0.0f, pr.y > 0.0f ? h.y : 0.0f);
+}
+
+// Compensated accumulator of pairs: both lanes go into one Kahan sum when
+// folded.
+struct KSum2 {
+  f2 part;
+  float hi, lo;
+  __device__ __forceinline__ void zero() {
+    part = dup(0.0f);
+    hi = lo = 0.0f;
+  }
+  __device__ __forceinline__ void fold() {
+    const float y = (part.x + part.y) - lo;
+    const float t = hi + y;
+    lo = (t - hi) - y;
+    hi = t;
+    part = dup(0.0f);
+  }
+  __device__ __forceinline__ float total() {
+    fold();
+    return hi;
+  }
+};
+
+// Face flux of two angles (see face_flux): al, hv, wl belong to the face,
+// hc, hca, mud to the angles.
+template <bool VEL>
+__device__ __forceinline__ f2 face_flux2(f2 qL, f2 sL, f2 qR, f2 sR, f2 pL, f2 tL, f2 pR, f2 tR, f2 al, f2 hv, f2 wl,
+                                         f2 hc, f2 hca, f2 mud) {
+  const f2 ha = p_mul(hca, al);                       // alpha C |mu| dt / 2dx
+  const f2 hl2 = p_fma(ha, dup(-2.0f), dup(1.0f));    // 1 - nu
+  const f2 L = p_fma(hl2, sL, qL), R = p_sub(qR, p_mul(hl2, sR));
+  f2 flux = p_fma(hc, p_add(L, R), p_mul(ha, p_sub(L, R)));
+  if (VEL) {
+    const f2 Lv = p_fma(hv, tL, pL), Rv = p_sub(pR, p_mul(hv, tR));
+    flux = p_fma(mud, p_fma(wl, p_sub(Lv, Rv), Rv), flux);
+  }
+  return flux;
+}
+
+// Per-pair table entries (float2: angle 2k, angle 2k + 1): n (0-2), W (3),
+// C mu dt/2dx (4-6), C |mu| dt/2dx (7-9), mu dt/dx (10-12), W n (13-15).
+constexpr int kTab2 = 16;
+
+// Shared-memory bytes of one CTA of the pair kernel: the pair table and the
+// float2 staging arrays (I~, IV, their slopes, one flux per face).
+__host__ __device__ inline size_t smem_bytes2(int dim, int M, bool has_v, int tx, int ty, int tz) {
+  Geo g;
+  g.init(dim, tx, ty, tz);
+  const size_t q = has_v ? 2 : 1, pairs = (size_t)(M + 1) / 2;
+  const size_t n2 = kTab2 * pairs + q * g.nbox + q * g.sl_off[3] + g.fx_off[3];
+  return n2 * sizeof(f2) + 16;
+}
+
+// One tile of one problem, float intensities: arguments as process_tile.
+template <int DIM, bool VEL, int TX, int TY, int TZ>
+__device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid, int tbx, int tby, int tbz,
+                                              unsigned char *smem_raw) {
+  using G = GeoT<DIM, TX, TY, TZ>;
+  constexpr int nthr = G::ncell;
+  constexpr int kSlots = slots_for(DIM, TX, TY, TZ);
+  constexpr int kExt = (G::next + nthr - 1) / nthr;   // slope-extension items per thread
+  constexpr int kLow = (G::nlow + nthr - 1) / nthr;   // lowest-face items per thread
+  static_assert(kSlots <= 4 && kExt <= 2 && kLow <= 2, "tile halo too large for the per-thread work items");
+  const int M = a.M, K = (M + 1) / 2;
+  const long long N = a.N;
+  const int org[3] = {tbx * TX, tby * TY, tbz * TZ};
+  const int bstride[3] = {1, G::B0, G::B0 * G::B1};
+
+  __syncthreads();   // the previous tile of a persistent CTA is done with shared memory
+  f2 *s_tab = reinterpret_cast<f2 *>(smem_raw);   // [K][kTab2]
+  f2 *s_It = s_tab + kTab2 * K;                    // [nbox]
+  f2 *s_IV = s_It + G::nbox;                       // [nbox]   (VEL)
+  f2 *s_sI = s_IV + (VEL ? G::nbox : 0);           // slopes of I~
+  f2 *s_sV = s_sI + G::SL3;                        // slopes of IV (VEL)
+  f2 *s_fx = s_sV + (VEL ? G::SL3 : 0);            // face fluxes
+
+  const float C = a.C, invC = a.invC, dt = a.dt;
+
+  // ---- pair table ------------------------------------------------------------
+  for (int i = tid; i < kTab2 * K; i += nthr) {
+    const int k = i / kTab2, j = i % kTab2;
+    float v[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int m = 2 * k + h;
+      float val = 0.0f;
+      if (m < M) {
+        const float W = a.ang[4 * m + 3];
+        if (j < 3) {
+          val = a.ang[4 * m + j];
+        } else if (j == 3) {
+          val = W;
+        } else {
+          const int d = (j - 4) % 3, kind = (j - 4) / 3;
+          const float mu = a.ang[4 * m + d], amu = mu < 0.0f ? -mu : mu;
+          val = kind == 0   ? 0.5f * C * mu * a.dtdx[d]
+                : kind == 1 ? 0.5f * C * amu * a.dtdx[d]
+                : kind == 2 ? mu * a.dtdx[d]
+                            : W * mu;
+        }
+      }
+      v[h] = val;
+    }
+    s_tab[i] = make_float2(v[0], v[1]);
+  }
+
+  // ---- own cell ---------------------------------------------------------------
+  const int loc[3] = {tid % TX, tid / (TX * TZ), (tid / TX) % TZ};
+  const int gx = org[0] + loc[0], gy = org[1] + loc[1], gz = org[2] + loc[2];
+  const bool valid = gx < a.n[0] && gy < a.n[1] && gz < a.n[2];
+  const long long c = valid ? gx + (long long)a.n[0] * (gy + (long long)a.n[1] * gz) : 0;
+  int bo = 0;
+  for (int d = 0; d < DIM; ++d) bo += (loc[d] + kHalo) * bstride[d];
+  int own_sl[3], own_fx[3];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    own_sl[d] = G::sl_off(d) + G::sl_idx(d, loc[0], loc[1], loc[2]);
+    own_fx[d] = G::fx_off(d) + G::fx_idx(d, loc[d], loc[0], loc[1], loc[2]);   // face below the cell
+  }
+
+  // ---- staging slots (see process_tile) ---------------------------------------
+  int sl_box[kSlots], sl_code[kSlots], sl_g[kSlots];
+  float sl_w[kSlots][3];
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) {
+    const int k = tid + s * nthr;
+    sl_box[s] = -1; sl_code[s] = 0; sl_g[s] = 0;
+    sl_w[s][0] = sl_w[s][1] = sl_w[s][2] = 0.0f;
+    if (k >= G::ncross) continue;
+    int b[3] = {0, 0, 0};
+    if (k < G::ncell) {
+      b[0] = k % TX + (DIM >= 1 ? kHalo : 0);
+      b[2] = (k / TX) % TZ + (DIM >= 3 ? kHalo : 0);
+      b[1] = k / (TX * TZ) + (DIM >= 2 ? kHalo : 0);
+    } else {
+      int kk = k - G::ncell;
+      int d = 0;
+      while (kk >= 2 * kHalo * G::P(d)) { kk -= 2 * kHalo * G::P(d); ++d; }
+      const int layer = kk / G::P(d), o = kk % G::P(d);
+      const int side = layer / kHalo, h = layer % kHalo;
+      const int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;
+      const int bd = side == 0 ? h : G::T(d) + kHalo + h;
+      const int b1v = o % G::T(a1) + (a1 < DIM ? kHalo : 0), b2v = o / G::T(a1) + (a2 < DIM ? kHalo : 0);
+      b[0] = d == 0 ? bd : (a1 == 0 ? b1v : b2v);
+      b[1] = d == 1 ? bd : (a1 == 1 ? b1v : b2v);
+      b[2] = d == 2 ? bd : (a1 == 2 ? b1v : b2v);
+    }
+    sl_box[s] = b[0] + G::B0 * (b[1] + G::B1 * b[2]);
+    int g[3], code = 0;
+    for (int d = 0; d < 3; ++d) {
+      g[d] = d < DIM ? org[d] + b[d] - kHalo : 0;
+      if (d < DIM && (g[d] < 0 || g[d] >= a.n[d])) {
+        if (code == 0) code = 1 + 2 * d + (g[d] >= a.n[d] ? 1 : 0);
+        g[d] = map_in(g[d], a.n[d], a.bc[d][0], a.bc[d][1]);
+      }
+    }
+    if (code) {
+      const int axis = (code - 1) >> 1, side = (code - 1) & 1;
+      const int kind = a.bc[axis][side];
+      code = (kind == BC_VACUUM || kind == BC_INFLOW) ? (1 | (kind == BC_INFLOW ? 2 : 0) | (axis << 2) | (side << 4)) : 0;
+    }
+    sl_code[s] = code;
+    sl_g[s] = (int)(g[0] + (long long)a.n[0] * (g[1] + (long long)a.n[1] * g[2]));
+    if (VEL) {
+      const long long cc = sl_g[s];
+      const float w3 = float(3.0 / (4.0 * kPi)) * a.mom_in[cc];
+      sl_w[s][0] = w3 * a.v[cc];
+      sl_w[s][1] = w3 * a.v[N + cc];
+      sl_w[s][2] = w3 * a.v[2 * N + cc];
+    }
+  }
+
+  // ---- slope-extension items (see process_tile) -------------------------------
+  int ext_bb[kExt > 0 ? kExt : 1], ext_st[kExt > 0 ? kExt : 1], ext_si[kExt > 0 ? kExt : 1];
+#pragma unroll
+  for (int j = 0; j < kExt; ++j) {
+    ext_bb[j] = 0; ext_st[j] = 0; ext_si[j] = -1;
+    const int e = tid + j * nthr;
+    if (e >= G::next) continue;
+    int ee = e, d = 0;
+    while (ee >= 2 * G::P(d)) { ee -= 2 * G::P(d); ++d; }
+    const int side = ee / G::P(d), o = ee % G::P(d);
+    const int a1x = d == 0 ? 1 : 0;
+    const int ld = side == 0 ? -1 : G::T(d), l1v = o % G::T(a1x), l2v = o / G::T(a1x);
+    const int l0 = d == 0 ? ld : (a1x == 0 ? l1v : l2v);
+    const int l1 = d == 1 ? ld : (a1x == 1 ? l1v : l2v);
+    const int l2 = d == 2 ? ld : (a1x == 2 ? l1v : l2v);
+    ext_bb[j] = (l0 + kHalo) + G::B0 * ((DIM >= 2 ? l1 + kHalo : 0) + G::B1 * (DIM >= 3 ? l2 + kHalo : 0));
+    ext_st[j] = G::bstride(d);
+    ext_si[j] = G::sl_off(d) + G::sl_idx(d, l0, l1, l2);
+  }
+
+  // ---- face constants (see process_tile) ---------------------------------------
+  float fu_al[3], fu_hv[3], fu_wl[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) { fu_al[d] = 1.0f; fu_hv[d] = 1.0f; fu_wl[d] = 0.5f; }
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    int gl[3] = {min(gx, a.n[0] - 1), min(gy, a.n[1] - 1), min(gz, a.n[2] - 1)};
+    int gu[3] = {gl[0], gl[1], gl[2]};
+    gu[d] = map_in((d == 0 ? gx : d == 1 ? gy : gz) + 1, a.n[d], a.bc[d][0], a.bc[d][1]);
+    face_consts<float, VEL>(a, d, gl, gu, &fu_al[d], &fu_hv[d], &fu_wl[d]);
+  }
+  int lf_d[kLow > 0 ? kLow : 1], lf_bb[kLow > 0 ? kLow : 1], lf_si[kLow > 0 ? kLow : 1],
+      lf_sstep[kLow > 0 ? kLow : 1], lf_fx[kLow > 0 ? kLow : 1];
+  float lf_al[kLow > 0 ? kLow : 1], lf_hv[kLow > 0 ? kLow : 1], lf_wl[kLow > 0 ? kLow : 1];
+#pragma unroll
+  for (int j = 0; j < kLow; ++j) {
+    lf_d[j] = 0; lf_bb[j] = 0; lf_si[j] = 0; lf_sstep[j] = 1; lf_fx[j] = -1;
+    lf_al[j] = 1.0f; lf_hv[j] = 1.0f; lf_wl[j] = 0.5f;
+    int e = tid + j * nthr;
+    if (e >= G::nlow) continue;
+    int d = 0;
+    while (e >= G::P(d)) { e -= G::P(d); ++d; }
+    const int a1x = d == 0 ? 1 : 0;
+    const int l1v = e % G::T(a1x), l2v = e / G::T(a1x);
+    const int l[3] = {d == 0 ? 0 : (a1x == 0 ? l1v : l2v), d == 1 ? 0 : (a1x == 1 ? l1v : l2v),
+                      d == 2 ? 0 : (a1x == 2 ? l1v : l2v)};
+    const int bb = (l[0] + kHalo) + G::B0 * ((DIM >= 2 ? l[1] + kHalo : 0) + G::B1 * (DIM >= 3 ? l[2] + kHalo : 0));
+    const int st = G::bstride(d);
+    lf_d[j] = d;
+    lf_bb[j] = bb - st;
+    lf_si[j] = G::sl_off(d) + G::sl_idx(d, d == 0 ? -1 : l[0], d == 1 ? -1 : l[1], d == 2 ? -1 : l[2]);
+    lf_sstep[j] = G::sl_step(d);
+    lf_fx[j] = G::fx_off(d) + G::fx_idx(d, 0, l[0], l[1], l[2]);
+    int gu[3] = {min(org[0] + l[0], a.n[0] - 1), min(org[1] + (DIM >= 2 ? l[1] : 0), a.n[1] - 1),
+                 min(org[2] + (DIM >= 3 ? l[2] : 0), a.n[2] - 1)};
+    int gl[3] = {gu[0], gu[1], gu[2]};
+    const int od = d == 0 ? org[0] : d == 1 ? org[1] : org[2], nd = d == 0 ? a.n[0] : d == 1 ? a.n[1] : a.n[2];
+    const int kl = d == 0 ? a.bc[0][0] : d == 1 ? a.bc[1][0] : a.bc[2][0];
+    const int kh = d == 0 ? a.bc[0][1] : d == 1 ? a.bc[1][1] : a.bc[2][1];
+    const int gud = min(od, nd - 1), gld = map_in(od - 1, nd, kl, kh);
+    if (d == 0) { gu[0] = gud; gl[0] = gld; } else if (d == 1) { gu[1] = gud; gl[1] = gld; } else { gu[2] = gud; gl[2] = gld; }
+    face_consts<float, VEL>(a, d, gl, gu, &lf_al[j], &lf_hv[j], &lf_wl[j]);
+  }
+
+  // ---- per-cell constants of the implicit steps (see process_tile) -------------
+  float rho = 1, sa = 0, ss = 0, vt[3] = {0, 0, 0}, vin[3] = {0, 0, 0};
+  double T0 = 1.0;
+  if (valid) {
+    rho = a.rho[c]; sa = a.sa[c]; ss = a.ss[c];
+    T0 = a.T_in[c];
+    if (VEL) {
+      for (int d = 0; d < 3; ++d) vin[d] = a.v[d * N + c];
+      if (a.estimate_v) {
+        const float E = a.mom_in[c];
+        const float h = 0.5f * dt * (sa + ss);
+        for (int d = 0; d < 3; ++d) {
+          const float Fd = a.mom_in[(1 + d) * N + c], Pdd = a.mom_in[(4 + d) * N + c];
+          const float num = rho * vin[d] + h * (C * rho * vin[d] + a.P * Fd);
+          const float den = rho + h * (C * rho + a.P * (E + Pdd) / C);
+          vt[d] = num / den;
+        }
+      } else {
+        vt[0] = vin[0]; vt[1] = vin[1]; vt[2] = vin[2];
+      }
+    }
+  }
+  const bool to_scat = ss > sa;
+  const float v2 = vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2];
+  const float A0 = 1.0f + dt * C * sa, A1 = dt * sa, kap = dt * sa / C;
+  const float a0 = 1.0f + dt * C * ss, a1 = dt * ss;
+  const float bq0 = -dt * C * ss - dt * ss * v2 / C, bq1 = 2.0f * dt * ss, bq2 = -dt * ss / C;
+  const float cq = -3.0f * dt * ss;
+  const float apb0 = 1.0f - a1 * v2 * invC, apb2 = -a1 * invC;
+  const float rd0 = VEL ? 0.0f : fast_rcp(A0);
+  const float ra0 = VEL ? 0.0f : fast_rcp(a0);
+
+  // intensity-dependent sums: U_k = sum W vn^k r / d, AQ = sum Q / a,
+  // BQ = sum b Q / a, pre = sum W n (I^n + Delta F)
+  KSum2 U0, AQ;
+  U0.zero();
+  AQ.zero();
+  f2 U1 = dup(0.0f), U2 = dup(0.0f), BQ = dup(0.0f), pre0 = dup(0.0f), pre1 = dup(0.0f), pre2 = dup(0.0f);
+
+  // prefetch pair 0
+  f2 pf[kSlots];
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s)
+    pf[s] = sl_box[s] >= 0 ? make_float2(a.I_in[sl_g[s]], M > 1 ? a.I_in[N + sl_g[s]] : 0.0f) : dup(0.0f);
+  const float *I_next = a.I_in;
+  __syncthreads();
+
+  for (int k = 0; k < K; ++k) {
+    const f2 *t = s_tab + kTab2 * k;
+    const f2 nx = t[0], ny = t[1], nz = t[2], Wm = t[3];
+    const int m = 2 * k;
+    const bool second = m + 1 < M;
+    // ---- phase 1: stage I~ and IV of the cross cells -------------------------
+    f2 I0 = dup(0.0f), q0 = dup(0.0f), p0 = dup(0.0f);
+#pragma unroll
+    for (int s = 0; s < kSlots; ++s) {
+      if (sl_box[s] < 0) continue;
+      f2 I = pf[s];
+      if (sl_code[s]) {
+        const int axis = (sl_code[s] >> 2) & 3, side = (sl_code[s] >> 4) & 1;
+        const f2 mu = t[axis];
+        const bool in0 = side ? (mu.x < 0.0f) : (mu.x > 0.0f);
+        const bool in1 = second && (side ? (mu.y < 0.0f) : (mu.y > 0.0f));
+        const float *row = a.inflow + (axis * 2 + side) * M + m;
+        if (in0) I.x = (sl_code[s] & 2) ? row[0] : 0.0f;
+        if (in1) I.y = (sl_code[s] & 2) ? row[1] : 0.0f;
+      }
+      f2 IV = dup(0.0f), It = I;
+      if (VEL) {
+        IV = p_fma(nx, dup(sl_w[s][0]), p_fma(ny, dup(sl_w[s][1]), p_mul(nz, dup(sl_w[s][2]))));
+        It = p_fma(IV, dup(-invC), I);
+        s_IV[sl_box[s]] = IV;
+      }
+      s_It[sl_box[s]] = It;
+      if (s == 0) { I0 = I; q0 = It; p0 = IV; }
+    }
+    if (k + 1 < K) {
+      I_next += 2 * N;
+      const bool next2 = m + 3 < M;
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s)
+        if (sl_box[s] >= 0) pf[s] = make_float2(I_next[sl_g[s]], next2 ? I_next[N + sl_g[s]] : 0.0f);
+    }
+    __syncthreads();
+
+    // ---- phase 2: half slopes of the own cell and of the extension cells -----
+    f2 sI[3], sV[3];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const int st = bstride[d];
+      sI[d] = vl_half2(s_It[bo - st], q0, s_It[bo + st]);
+      s_sI[own_sl[d]] = sI[d];
+      if (VEL) {
+        sV[d] = vl_half2(s_IV[bo - st], p0, s_IV[bo + st]);
+        s_sV[own_sl[d]] = sV[d];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kExt; ++j) {
+      if (ext_si[j] < 0) continue;
+      const int bb = ext_bb[j], st = ext_st[j];
+      s_sI[ext_si[j]] = vl_half2(s_It[bb - st], s_It[bb], s_It[bb + st]);
+      if (VEL) s_sV[ext_si[j]] = vl_half2(s_IV[bb - st], s_IV[bb], s_IV[bb + st]);
+    }
+    __syncthreads();
+
+    // ---- phase 3: face fluxes (pre-multiplied by dt/dx) ----------------------
+    f2 fhi[3];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const int st = bstride[d];
+      const int sn = own_sl[d] + G::sl_step(d);
+      fhi[d] = face_flux2<VEL>(q0, sI[d], s_It[bo + st], s_sI[sn], p0, VEL ? sV[d] : dup(0.0f),
+                               VEL ? s_IV[bo + st] : dup(0.0f), VEL ? s_sV[sn] : dup(0.0f), dup(fu_al[d]),
+                               dup(fu_hv[d]), dup(fu_wl[d]), t[4 + d], t[7 + d], t[10 + d]);
+      s_fx[own_fx[d] + G::fx_step(d)] = fhi[d];
+    }
+#pragma unroll
+    for (int j = 0; j < kLow; ++j) {
+      if (lf_fx[j] < 0) continue;
+      const int d = lf_d[j], bb = lf_bb[j], st = d == 0 ? 1 : bstride[d == 1 ? 1 : 2];
+      const int si = lf_si[j], si1 = lf_si[j] + lf_sstep[j];
+      s_fx[lf_fx[j]] = face_flux2<VEL>(s_It[bb], s_sI[si], s_It[bb + st], s_sI[si1], VEL ? s_IV[bb] : dup(0.0f),
+                                       VEL ? s_sV[si] : dup(0.0f), VEL ? s_IV[bb + st] : dup(0.0f),
+                                       VEL ? s_sV[si1] : dup(0.0f), dup(lf_al[j]), dup(lf_hv[j]), dup(lf_wl[j]),
+                                       t[4 + d], t[7 + d], t[10 + d]);
+    }
+    __syncthreads();
+
+    // ---- phase 4: Delta F, Q_m to the output array, intensity sums -----------
+    f2 dF = dup(0.0f);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) dF = p_add(dF, p_sub(s_fx[own_fx[d]], fhi[d]));
+    const f2 full = p_add(I0, dF);
+    f2 vn = dup(0.0f), rd = dup(rd0), ra = dup(ra0);
+    if (VEL) {
+      vn = p_fma(nx, dup(vt[0]), p_fma(ny, dup(vt[1]), p_mul(nz, dup(vt[2]))));
+      rd = p_rcp(p_fma(dup(-A1), vn, dup(A0)));
+      ra = p_rcp(p_fma(dup(-a1), vn, dup(a0)));
+    }
+    const f2 qa = p_mul(to_scat ? I0 : full, rd);   // r_m / d_m
+    const f2 Q = to_scat ? p_add(qa, dF) : qa;
+    if (valid) {
+      a.I_out[(long long)m * N + c] = Q.x;
+      if (second) a.I_out[(long long)(m + 1) * N + c] = Q.y;
+    }
+    const f2 wq = p_mul(Wm, qa);
+    U0.part = p_add(U0.part, wq);
+    if (VEL) {
+      const f2 y1 = p_mul(wq, vn);
+      U1 = p_add(U1, y1);
+      U2 = p_fma(y1, vn, U2);
+    }
+    const f2 wa = p_mul(Wm, ra);   // W / a'
+    AQ.part = p_fma(wa, Q, AQ.part);
+    const f2 bm = VEL ? p_fma(vn, p_fma(dup(bq2), vn, dup(bq1)), dup(bq0)) : dup(bq0);
+    BQ = p_fma(p_mul(bm, wa), Q, BQ);
+    pre0 = p_fma(t[13], full, pre0);
+    pre1 = p_fma(t[14], full, pre1);
+    pre2 = p_fma(t[15], full, pre2);
+    if ((k & 3) == 3) { U0.fold(); AQ.fold(); }
+  }
+
+  if (!valid) return;
+
+  // ---- sums that depend on the velocity and the opacities only ---------------
+  // T_k = sum W vn^k / d; Step 5: Ap = sum pe/a, Ad = sum 1/(d a), As1 = sum
+  // 1/a, Acc = sum c/a, Bp, Bd, Bcc the b-weighted ones, B1p = sum (a'+b)/a
+  f2 T0p = dup(0.0f), T1p = dup(0.0f), T2p = dup(0.0f), T3p = dup(0.0f);
+  f2 Apk = dup(0.0f), Adk = dup(0.0f), As1k = dup(0.0f), Acck = dup(0.0f);
+  f2 Bpk = dup(0.0f), Bdk = dup(0.0f), Bcck = dup(0.0f), B1pk = dup(0.0f);
+  for (int k = 0; k < K; ++k) {
+    const f2 *t = s_tab + kTab2 * k;
+    const f2 nx = t[0], ny = t[1], nz = t[2], Wm = t[3];
+    f2 vn = dup(0.0f), rd = dup(rd0), ra = dup(ra0);
+    if (VEL) {
+      vn = p_fma(nx, dup(vt[0]), p_fma(ny, dup(vt[1]), p_mul(nz, dup(vt[2]))));
+      rd = p_rcp(p_fma(dup(-A1), vn, dup(A0)));
+      ra = p_rcp(p_fma(dup(-a1), vn, dup(a0)));
+    }
+    const f2 wrd = p_mul(Wm, rd);
+    T0p = p_add(T0p, wrd);
+    if (VEL) {
+      const f2 x1 = p_mul(wrd, vn), x2 = p_mul(x1, vn);
+      T1p = p_add(T1p, x1);
+      T2p = p_add(T2p, x2);
+      T3p = p_fma(x2, vn, T3p);
+    }
+    const f2 pe = p_mul(dup(A1), p_mul(p_fma(dup(3.0f), vn, dup(C)), rd));   // e_m / d_m
+    const f2 wa = p_mul(Wm, ra);
+    Apk = p_fma(wa, pe, Apk);
+    Adk = p_fma(wa, rd, Adk);
+    As1k = p_add(As1k, wa);
+    if (VEL) {
+      const f2 bm = p_fma(vn, p_fma(dup(bq2), vn, dup(bq1)), dup(bq0));
+      const f2 cm = p_mul(dup(cq), vn);
+      const f2 bwa = p_mul(bm, wa);
+      Acck = p_fma(cm, wa, Acck);
+      Bpk = p_fma(bwa, pe, Bpk);
+      Bdk = p_fma(bwa, rd, Bdk);
+      Bcck = p_fma(cm, bwa, Bcck);
+      B1pk = p_fma(wa, p_fma(vn, p_fma(dup(apb2), vn, dup(a1)), dup(apb0)), B1pk);
+    } else {
+      const f2 bwa = p_mul(dup(bq0), wa);
+      Bpk = p_fma(bwa, pe, Bpk);
+      Bdk = p_fma(bwa, rd, Bdk);
+      B1pk = p_add(B1pk, wa);
+    }
+  }
+  const float T0s = T0p.x + T0p.y, T1s = T1p.x + T1p.y, T2s = T2p.x + T2p.y, T3s = T3p.x + T3p.y;
+  const float Ap = Apk.x + Apk.y, Ad = Adk.x + Adk.y, As1 = As1k.x + As1k.y, Acc = Acck.x + Acck.y;
+  const float Bp = Bpk.x + Bpk.y, Bd = Bdk.x + Bdk.y, Bcc = Bcck.x + Bcck.y, B1p = B1pk.x + B1pk.y;
+
+  // ---- Step 4 solve (see process_tile) -----------------------------------------
+  const float Wr = U0.total(), Vr = U1.x + U1.y, Gr = v2 * Wr + (U2.x + U2.y);
+  const float W1 = T0s, V1 = T1s, G1 = v2 * T0s + T2s;
+  const float Ve = A1 * (C * T1s + 3.0f * T2s);
+  const float Ge = A1 * (C * (v2 * T0s + T2s) + 3.0f * (v2 * T1s + T3s));
+  const float Wq = T0s - 4.0f * A1 * T1s;     // sum W (d - e) / d
+  const float den = 1.0f + kap * G1;
+  const float S0 = Gr / den, S1 = Ge / den;
+  const float J0 = Wr - kap * S0 * W1;
+  const float H0 = Vr - kap * S0 * V1, H1 = Ve - kap * S1 * V1;
+  const float omJ1 = Wq + kap * S1 * W1;   // 1 - dJ/dtheta, cancellation-free
+  const double kv = (double)rho * a.kv_per_rho;
+  double T1 = T0;
+  if (!a.hold_T) {
+    const float beta = a.P * C * (1.0f - v2 * invC * invC) * sa;
+    const float c0r = dt * (float(8.0 * kPi) * a.P * sa * (H0 - S0 * invC) - float(4.0 * kPi) * beta * J0);
+    const float c4 = dt * (2.0f * a.P * sa * (H1 - S1 * invC) + beta * omJ1);
+    // Newton on delta = T - T^n in float, then one double-precision step
+    const float T0f = (float)T0, kvf = (float)kv;
+    float d = 0.0f;
+    int extra = -1, it;
+    for (it = 0; it < 40; ++it) {
+      const float T = T0f + d, T2 = T * T;
+      const float f = c4 * T2 * T2 + kvf * d + c0r;
+      const float fp = 4.0f * c4 * T2 * T + kvf;
+      float dn = d - f / fp;
+      if (!(T0f + dn > 0.0f)) dn = 0.5f * T - T0f;
+      const float step = dn - d;
+      d = dn;
+      if (extra == 0) break;
+      if (extra < 0 && fabsf(step) <= 2e-7f * (T0f + d)) extra = 0;
+    }
+    double dd = (double)d;
+    const double T = T0 + dd, T2 = T * T;
+    const double f = (double)c4 * T2 * T2 + kv * dd + (double)c0r;
+    const float fp = 4.0f * c4 * (float)(T2 * T) + kvf;
+    dd -= f * (double)(1.0f / fp);
+    if (!(it < 40 && (T0 + dd) > 0.0)) atomicAdd(a.status, 1);
+    T1 = T0 + dd;
+  }
+  const float T1r = (float)T1, T1sq = T1r * T1r;
+  const float th = T1sq * T1sq * float(1.0 / (4.0 * kPi));
+  const float S = S0 + th * S1;
+  const float kS = kap * S;
+
+  // ---- Step 5 solve: (1+B1) s1 + Bc s2 = Br,  A1 s1 + (1+Ac) s2 = Ar -------
+  const float Ar = AQ.total() + th * Ap - kS * Ad;
+  const float Br = (BQ.x + BQ.y) + th * Bp - kS * Bd;
+  const float m11 = B1p, m12 = Bcc, m21 = As1, m22 = 1.0f + Acc;
+  const float det = m11 * m22 - m12 * m21;
+  const float s1 = (Br * m22 - m12 * Ar) / det;
+  const float s2 = (m11 * Ar - m21 * Br) / det;
+
+  // ---- I^{n+1} over Q_m, quadrature (sec. 3) ---------------------------------
+  KSum2 mE, mF[3], mP[6];
+  mE.zero();
+  for (int i = 0; i < 3; ++i) mF[i].zero();
+  for (int i = 0; i < 6; ++i) mP[i].zero();
+  float *out = a.I_out + c;
+#pragma unroll 2
+  for (int k = 0; k < K; ++k) {
+    const f2 *t = s_tab + kTab2 * k;
+    const f2 nx = t[0], ny = t[1], nz = t[2], Wm = t[3];
+    const int m = 2 * k;
+    const bool second = m + 1 < M;
+    const f2 Q = make_float2(out[(long long)m * N], second ? out[(long long)(m + 1) * N] : 0.0f);
+    f2 vn = dup(0.0f), rd = dup(rd0), ra = dup(ra0);
+    if (VEL) {
+      vn = p_fma(nx, dup(vt[0]), p_fma(ny, dup(vt[1]), p_mul(nz, dup(vt[2]))));
+      rd = p_rcp(p_fma(dup(-A1), vn, dup(A0)));
+      ra = p_rcp(p_fma(dup(-a1), vn, dup(a0)));
+    }
+    const f2 pe = p_mul(dup(A1), p_mul(p_fma(dup(3.0f), vn, dup(C)), rd));
+    const f2 rs = p_fma(pe, dup(th), p_fma(rd, dup(-kS), Q));        // r'_m
+    const f2 cm = p_mul(dup(cq), vn);
+    const f2 I1 = p_mul(p_fma(cm, dup(-s2), p_sub(rs, dup(s1))), ra);
+    out[(long long)m * N] = I1.x;
+    if (second) out[(long long)(m + 1) * N] = I1.y;
+    const f2 wi = p_mul(Wm, I1);
+    mE.part = p_add(mE.part, wi);
+    const f2 wx = p_mul(nx, wi), wy = p_mul(ny, wi), wz = p_mul(nz, wi);
+    mF[0].part = p_add(mF[0].part, wx);
+    mF[1].part = p_add(mF[1].part, wy);
+    mF[2].part = p_add(mF[2].part, wz);
+    mP[0].part = p_fma(nx, wx, mP[0].part);
+    mP[1].part = p_fma(ny, wy, mP[1].part);
+    mP[2].part = p_fma(nz, wz, mP[2].part);
+    mP[3].part = p_fma(ny, wx, mP[3].part);
+    mP[4].part = p_fma(nz, wx, mP[4].part);
+    mP[5].part = p_fma(nz, wy, mP[5].part);
+    if ((k & 3) == 3) {
+      mE.fold();
+      for (int i = 0; i < 3; ++i) mF[i].fold();
+      for (int i = 0; i < 6; ++i) mP[i].fold();
+    }
+  }
+  const float fourpi = float(4.0 * kPi);
+  a.mom_out[c] = fourpi * mE.total();
+  float post[3];
+  for (int i = 0; i < 3; ++i) {
+    post[i] = mF[i].total();
+    a.mom_out[(1 + i) * N + c] = fourpi * post[i];
+  }
+  for (int i = 0; i < 6; ++i) a.mom_out[(4 + i) * N + c] = fourpi * mP[i].total();
+
+  // ---- gas sources (sec. 4.3: Delta E_T, eqs. momentumchange, kinetichange)
+  const float kmom = -fourpi * a.P * invC;
+  float dEK = 0.0f;
+  const float pre[3] = {pre0.x + pre0.y, pre1.x + pre1.y, pre2.x + pre2.y};
+  for (int i = 0; i < 3; ++i) {
+    const float dmom = kmom * (post[i] - pre[i]);
+    a.dMom[i * N + c] = dmom;
+    const float m0 = rho * vin[i];
+    dEK += ((m0 + dmom) * (m0 + dmom) - m0 * m0) / (2.0f * rho);
+  }
+  a.T_out[c] = T1;
+  a.dEgas[c] = kv * (T1 - T0) + (double)dEK;
+}
+
+template <int DIM, bool VEL, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(TX * TY * TZ, 1) step_kernel2(const StepArgs<float> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  process_tile2<DIM, VEL, TX, TY, TZ>(a, threadIdx.x, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+}
+
+template <int DIM, bool VEL, int TX, int TY, int TZ>
+cudaError_t launch_shape2(const StepArgs<float> &a, cudaStream_t s) {
+  const size_t sm = smem_bytes2(DIM, a.M, VEL, TX, TY, TZ);
+  auto kern = step_kernel2<DIM, VEL, TX, TY, TZ>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  dim3 block(TX * TY * TZ);
+  dim3 grid((a.n[0] + TX - 1) / TX, (a.n[1] + TY - 1) / TY, (a.n[2] + TZ - 1) / TZ);
+  kern<<<grid, block, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace stepk
+
+}  // namespace rtg
