@@ -152,13 +152,30 @@ rt_status rt_set_inflow(rt_ctx *ctx, int axis, int side, const double *I_ghost);
 
 /* Tile of cells one CTA of the step kernel owns (tx x ty x tz, one thread
  * per cell; ty = 1 for 1-D, tz = 1 below 3-D).  (0, 0, 0) restores the
- * default choice.  RT_E_INVALID when the shape exceeds the kernel's thread
- * bound (512 for RT_FP32, 256 for RT_FP64), the 227 KB of shared memory
- * (which grows with the angle count) or the staging capacity of its halo.
- * Results do not depend on the tile; only speed does.  This is the hook
- * the tile autotuner uses. */
+ * default choice.  RT_E_INVALID when the shape is not one of the compiled
+ * shapes or exceeds the 227 KB of shared memory (which grows with the angle
+ * count).  Float results do not depend on the tile (bitwise); double
+ * results may differ in the last bit, as the compiler fuses multiply-adds
+ * differently per tile shape.  The paper has no counterpart (its code runs
+ * on CPUs). */
 rt_status rt_set_tile(rt_ctx *ctx, int tx, int ty, int tz);
 rt_status rt_get_tile(const rt_ctx *ctx, int *tx, int *ty, int *tz);
+
+/* Measured time of one candidate tile shape: ms per step. */
+typedef struct {
+  int tx, ty, tz;
+  double ms;
+} rt_tile_time;
+
+/* Tile autotuner: times trial_steps (>= 1, after one untimed step) of every
+ * compiled tile shape that can run this context, on its stream with CUDA
+ * events, and keeps the fastest (as rt_set_tile would).  The trial steps
+ * write only scratch: I, T, the moments and the step sources are restored,
+ * so the state afterwards is bitwise what it was.  times (may be NULL)
+ * receives up to cap entries, *ntimes (may be NULL) their count.  Waits for
+ * the stream.  Needs rt_set_material and an intensity (RT_E_STATE); a
+ * context in a batch is tuned through rt_batch_autotune (RT_E_STATE). */
+rt_status rt_autotune(rt_ctx *ctx, int trial_steps, rt_tile_time *times, int cap, int *ntimes);
 
 /* Step 1 of sec. 4.1: the time step cfl * min_d dx_d / Crat. */
 double rt_cfl_dt(const rt_ctx *ctx);
@@ -217,6 +234,15 @@ int rt_batch_size(const rt_batch *b);
  * and one persistent launch per step) when the stream is not NULL.
  * Stream-ordered.  RT_E_INVALID if the largest angle set does not fit. */
 rt_status rt_batch_step(rt_batch *b, int nsteps);
+/* Tile-set autotuner of the persistent kernel.  Three variants are
+ * compiled: 512, 256 and 128 threads per CTA (tiles 512 / 32x16 / 16x8x4,
+ * 256 / 16x16 / 8x8x4 and 128 / 16x8 / 8x4x4 cells for 1-D / 2-D / 3-D
+ * members).  Times trial_steps (>= 1, after one untimed step) of each on the
+ * batch's stream and keeps the fastest for later rt_batch_step calls.  The
+ * members' state is restored afterwards (bitwise).  ms (may be NULL)
+ * receives the three times in the order above, *chosen (may be NULL) the
+ * index kept.  Waits for the stream. */
+rt_status rt_batch_autotune(rt_batch *b, int trial_steps, double *ms, int *chosen);
 /* Frees the batch (not its contexts).  NULL is ignored. */
 void rt_batch_destroy(rt_batch *b);
 

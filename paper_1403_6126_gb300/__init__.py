@@ -49,6 +49,10 @@ class rt_noalloc_fields(ctypes.Structure):
                                                "mom_out", "dE_gas", "dMom", "inflow")]
 
 
+class rt_tile_time(ctypes.Structure):
+    _fields_ = [("tx", ctypes.c_int), ("ty", ctypes.c_int), ("tz", ctypes.c_int), ("ms", ctypes.c_double)]
+
+
 class RTError(RuntimeError):
     def __init__(self, status, where, msg):
         super().__init__("%s: %s (%s)" % (where, _STATUS_NAMES.get(status, status), msg))
@@ -79,6 +83,8 @@ def lib():
             "rt_cfl_dt": (D, [V]),
             "rt_set_tile": (I, [V, I, I, I]),
             "rt_get_tile": (I, [V, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
+            "rt_autotune": (I, [V, I, ctypes.POINTER(rt_tile_time), I, ctypes.POINTER(I)]),
+            "rt_batch_autotune": (I, [V, I, _DP, ctypes.POINTER(I)]),
             "rt_step": (I, [V, D]),
             "rt_run": (I, [V, D, I]),
             "rt_sync": (I, [V]),
@@ -180,6 +186,15 @@ def rt_get_tile(ctx):
     return tuple(x.value for x in t)
 
 
+def rt_autotune(ctx, trial_steps=3):
+    """Times every compiled tile that fits, keeps the fastest; returns
+    [(tx, ty, tz, ms per step), ...]."""
+    buf = (rt_tile_time * 8)()
+    n = ctypes.c_int(0)
+    _check(lib().rt_autotune(ctx, trial_steps, buf, 8, ctypes.byref(n)), "rt_autotune")
+    return [(t.tx, t.ty, t.tz, t.ms) for t in buf[: n.value]]
+
+
 def rt_cfl_dt(ctx):
     return lib().rt_cfl_dt(ctx)
 
@@ -232,6 +247,16 @@ def rt_batch_size(b):
 
 def rt_batch_step(b, nsteps):
     _check(lib().rt_batch_step(b, nsteps), "rt_batch_step")
+
+
+def rt_batch_autotune(b, trial_steps=3):
+    """Times the three compiled tile sets; returns (ms per step of each,
+    -1 where a set does not fit, index kept)."""
+    ms = np.zeros(3)
+    chosen = ctypes.c_int(-1)
+    _check(lib().rt_batch_autotune(b, trial_steps, ms.ctypes.data_as(_DP), ctypes.byref(chosen)),
+           "rt_batch_autotune")
+    return ms.tolist(), chosen.value
 
 
 def rt_batch_destroy(b):
@@ -357,6 +382,9 @@ class Context:
 
     def tile(self):
         return rt_get_tile(self.ctx)
+
+    def autotune(self, trial_steps=3):
+        return rt_autotune(self.ctx, trial_steps)
 
     def step(self, dt=0.0):
         rt_step(self.ctx, dt)

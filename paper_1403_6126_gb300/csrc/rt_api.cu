@@ -393,6 +393,77 @@ rt_status rt_set_tile(rt_ctx *c, int tx, int ty, int tz) {
   return RT_OK;
 }
 
+rt_status rt_autotune(rt_ctx *c, int trial_steps, rt_tile_time *times, int cap, int *ntimes) {
+  if (!c) return fail(RT_E_INVALID, "rt_autotune: NULL context");
+  if (trial_steps < 1) return fail(RT_E_INVALID, "rt_autotune: trial_steps < 1");
+  if (cap < 0 || (cap > 0 && !times)) return fail(RT_E_INVALID, "rt_autotune: bad times buffer");
+  if (!c->material_set || !c->intensity_set) return fail(RT_E_STATE, "rt_autotune: set material and intensity first");
+  if (c->batch) return fail(RT_E_STATE, "rt_autotune: the context belongs to a batch; use rt_batch_autotune");
+  const bool vel = rtg::velocity_on(c);
+  rtg::TileShape cand[8];
+  const int nc = c->fp64 ? rtg::tile_candidates<double>(c->dim, c->M, true, cand)
+                         : rtg::tile_candidates<float>(c->dim, c->M, true, cand);
+  if (nc == 0) return fail(RT_E_INVALID, "rt_autotune: no compiled tile fits");
+  // The trial steps read I[cur] and write only I[1 - cur], mom[1 - cur]
+  // (scratch until the next real step), T in place and the step sources:
+  // save those three and the Newton-failure word, restore them afterwards.
+  const size_t N = (size_t)c->N;
+  double *save_T = c->stage, *save_dE = c->stage + N, *save_dM = c->stage + 2 * N;
+  int flag0 = 0;
+  RT_CUDA(cudaMemcpyAsync(&flag0, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  RT_CUDA(cudaMemcpyAsync(save_T, c->T, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  RT_CUDA(cudaMemcpyAsync(save_dE, c->dEgas, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  RT_CUDA(cudaMemcpyAsync(save_dM, c->dMom, 3 * N * c->rs, cudaMemcpyDeviceToDevice, c->stream));
+  const double dt = rt_cfl_dt(c);
+  cudaEvent_t e0, e1;
+  RT_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(RT_E_CUDA, "rt_autotune: event");
+  }
+  const rtg::TileShape keep = c->tile;
+  rtg::TileShape best = keep;
+  double best_ms = 0;
+  cudaError_t e = cudaSuccess;
+  int n_out = 0;
+  for (int i = 0; i < nc && e == cudaSuccess; ++i) {
+    float ms = 0;
+    for (int k = 0; k <= trial_steps && e == cudaSuccess; ++k) {
+      if (k == 1) e = cudaEventRecord(e0, c->stream);
+      if (e == cudaSuccess)
+        e = c->fp64 ? rtg::launch_step<double>(rtg::make_args<double>(c, dt), c->dim, vel, cand[i], c->stream)
+                    : rtg::launch_step<float>(rtg::make_args<float>(c, dt), c->dim, vel, cand[i], c->stream);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) break;
+    const double per = (double)ms / trial_steps;
+    if (n_out < cap) times[n_out++] = rt_tile_time{cand[i].tx, cand[i].ty, cand[i].tz, per};
+    if (i == 0 || per < best_ms) {
+      best_ms = per;
+      best = cand[i];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(e, "rt_autotune: trial steps");
+  RT_CUDA(cudaMemcpyAsync(c->T, save_T, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  RT_CUDA(cudaMemcpyAsync(c->dEgas, save_dE, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  RT_CUDA(cudaMemcpyAsync(c->dMom, save_dM, 3 * N * c->rs, cudaMemcpyDeviceToDevice, c->stream));
+  RT_CUDA(cudaMemcpyAsync(c->flags, &flag0, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  RT_CUDA(cudaStreamSynchronize(c->stream));
+  if (ntimes) *ntimes = n_out;
+  if (best.tx != keep.tx || best.ty != keep.ty || best.tz != keep.tz) {
+    c->tile = best;
+    if (c->graph) {
+      cudaGraphExecDestroy(c->graph);
+      c->graph = nullptr;
+    }
+  }
+  return RT_OK;
+}
+
 rt_status rt_get_tile(const rt_ctx *c, int *tx, int *ty, int *tz) {
   if (!c || !tx || !ty || !tz) return fail(RT_E_INVALID, "rt_get_tile: NULL argument");
   *tx = c->tile.tx;

@@ -2,12 +2,14 @@
 //
 // A batch holds contexts created with rt_create (float intensities).  For a
 // step, a device work list names every (problem, tile) pair; a grid of
-// persistent CTAs (one per SM at the shared-memory size the largest angle set
-// needs) pulls items through an atomic counter and runs the same per-tile
-// code as the single-problem kernel, so each problem's result is bitwise the
-// one it gets alone.  Items are ordered by decreasing angle count so the long
-// tiles start first.  Steps are captured in a CUDA graph (a counter reset and
-// a kernel per step) and replayed.
+// persistent CTAs (as many as fit on the GPU at the shared-memory size the
+// largest angle set needs) pulls items through an atomic counter and runs the
+// same per-tile code as the single-problem kernel, so each problem's result
+// is bitwise the one it gets alone.  Items are ordered by decreasing angle
+// count so the long tiles start first.  Steps are captured in a CUDA graph (a
+// counter reset and a kernel per step) and replayed.  Three tile sets are
+// compiled (rt_batch_k*.cu); rt_batch_autotune times them on the batch's own
+// members and keeps the fastest.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -15,57 +17,24 @@
 #include <vector>
 
 #include "rt.h"
+#include "rt_batch_kernel.cuh"
 #include "rt_ctx.h"
-#include "rt_step_pair.cuh"
 
 namespace rtg {
 
-struct WorkItem {
-  int prob, tbx, tby, tbz;
-};
-
-// Tile shapes of the persistent kernel, per grid dimension.
-constexpr int kB1X = 512;
-constexpr int kB2X = 32, kB2Y = 16;
-constexpr int kB3X = 16, kB3Y = 8, kB3Z = 4;
-constexpr int kBatchThreads = 512;
-
-template <bool VEL>
-__global__ void __launch_bounds__(kBatchThreads, 1)
-    batch_kernel(const StepArgs<float> *__restrict__ descs, const WorkItem *__restrict__ items, int nitems,
-                 int *counter) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ StepArgs<float> desc;
-  __shared__ int s_item;
-  const int tid = threadIdx.x;
-  for (;;) {
-    if (tid == 0) s_item = atomicAdd(counter, 1);
-    __syncthreads();
-    const int it = s_item;
-    if (it >= nitems) break;
-    const WorkItem w = items[it];
-    const int *src = reinterpret_cast<const int *>(descs + w.prob);
-    int *dst = reinterpret_cast<int *>(&desc);
-    for (int i = tid; i < (int)(sizeof(StepArgs<float>) / sizeof(int)); i += kBatchThreads) dst[i] = src[i];
-    __syncthreads();
-    if (desc.dim == 3)
-      stepk::process_tile2<3, VEL, kB3X, kB3Y, kB3Z>(desc, tid, w.tbx, w.tby, w.tbz, smem);
-    else if (desc.dim == 2)
-      stepk::process_tile2<2, VEL, kB2X, kB2Y, 1>(desc, tid, w.tbx, w.tby, 0, smem);
-    else
-      stepk::process_tile2<1, VEL, kB1X, 1, 1>(desc, tid, w.tbx, 0, 0, smem);
-    __syncthreads();   // every thread has read s_item and desc
-  }
+const BatchVariant &batch_variant(int i) {
+  static const BatchVariant table[kBatchVariants] = {batch_variant_512(), batch_variant_256(), batch_variant_128()};
+  return table[i];
 }
 
-static_assert(kB1X == kBatchThreads && kB2X * kB2Y == kBatchThreads && kB3X * kB3Y * kB3Z == kBatchThreads,
-              "every tile shape of the persistent kernel has one thread per cell");
+static size_t variant_smem(const BatchVariant &v, int dim, int M, bool vel) {
+  const TileShape t = dim == 1 ? v.t1 : dim == 2 ? v.t2 : v.t3;
+  return stepk::smem_bytes2(dim, M, vel, t.tx, t.ty, t.tz);
+}
 
 bool batch_fits(int dim, int M, bool vel) {
-  size_t sm = dim == 1   ? stepk::smem_bytes2(1, M, vel, kB1X, 1, 1)
-              : dim == 2 ? stepk::smem_bytes2(2, M, vel, kB2X, kB2Y, 1)
-                         : stepk::smem_bytes2(3, M, vel, kB3X, kB3Y, kB3Z);
-  return sm <= 227 * 1024;
+  // the default variant's tile must hold the angle set
+  return variant_smem(batch_variant(0), dim, M, vel) <= 227 * 1024;
 }
 
 }  // namespace rtg
@@ -75,7 +44,7 @@ struct rt_batch {
   std::vector<rt_ctx *> ctxs;
   bool dirty = true;
   bool vel = false;
-  int nitems = 0, grid = 0, phase = 0;
+  int nitems = 0, grid = 0, phase = 0, variant = 0;
   size_t smem = 0;
   rtg::WorkItem *d_items = nullptr;
   rtg::StepArgs<float> *d_desc[2] = {nullptr, nullptr};
@@ -109,6 +78,7 @@ rt_status rebuild(rt_batch *b) {
   std::vector<int> order(b->ctxs.size());
   for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->ctxs[x]->M > b->ctxs[y]->M; });
+  const rtg::BatchVariant &var = rtg::batch_variant(b->variant);
   std::vector<rtg::WorkItem> items;
   int Mmax = 1;
   bool dims[4] = {false, false, false, false};
@@ -118,17 +88,15 @@ rt_status rebuild(rt_batch *b) {
     rt_ctx *c = b->ctxs[i];
     Mmax = std::max(Mmax, c->M);
     dims[c->dim] = true;
-    int tx = c->dim == 1 ? rtg::kB1X : c->dim == 2 ? rtg::kB2X : rtg::kB3X;
-    int ty = c->dim == 2 ? rtg::kB2Y : c->dim == 3 ? rtg::kB3Y : 1;
-    int tz = c->dim == 3 ? rtg::kB3Z : 1;
+    const rtg::TileShape t = c->dim == 1 ? var.t1 : c->dim == 2 ? var.t2 : var.t3;
+    const int tx = t.tx, ty = t.ty, tz = t.tz;
     for (int z = 0; z < (c->n[2] + tz - 1) / tz; ++z)
       for (int y = 0; y < (c->n[1] + ty - 1) / ty; ++y)
         for (int x = 0; x < (c->n[0] + tx - 1) / tx; ++x) items.push_back({i, x, y, z});
   }
   size_t smem = 0;
-  if (dims[1]) smem = std::max(smem, rtg::stepk::smem_bytes2(1, Mmax, b->vel, rtg::kB1X, 1, 1));
-  if (dims[2]) smem = std::max(smem, rtg::stepk::smem_bytes2(2, Mmax, b->vel, rtg::kB2X, rtg::kB2Y, 1));
-  if (dims[3]) smem = std::max(smem, rtg::stepk::smem_bytes2(3, Mmax, b->vel, rtg::kB3X, rtg::kB3Y, rtg::kB3Z));
+  for (int d = 1; d <= 3; ++d)
+    if (dims[d]) smem = std::max(smem, rtg::variant_smem(var, d, Mmax, b->vel));
   if (smem > 227 * 1024)
     return rtg::set_error(RT_E_INVALID, "rt_batch: the largest angle set does not fit the batch tile in shared memory");
   b->smem = smem;
@@ -164,10 +132,8 @@ rt_status rebuild(rt_batch *b) {
       RT_BCUDA(cudaMemcpyAsync(b->d_desc[p], desc[p].data(), sizeof(rtg::StepArgs<float>) * desc[p].size(),
                                cudaMemcpyHostToDevice, b->stream));
   RT_BCUDA(cudaStreamSynchronize(b->stream));
-  auto kern = b->vel ? rtg::batch_kernel<true> : rtg::batch_kernel<false>;
-  RT_BCUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
   int per_sm = 0, dev = 0, sms = 0;
-  RT_BCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, rtg::kBatchThreads, b->smem));
+  RT_BCUDA(var.prepare(b->vel, b->smem, &per_sm));
   RT_BCUDA(cudaGetDevice(&dev));
   RT_BCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   b->grid = std::max(1, std::min(b->nitems, sms * std::max(1, per_sm)));
@@ -179,9 +145,8 @@ rt_status rebuild(rt_batch *b) {
 // Queues one step: counter reset and one persistent launch.
 rt_status enqueue_step(rt_batch *b, int parity) {
   RT_BCUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream));
-  auto kern = b->vel ? rtg::batch_kernel<true> : rtg::batch_kernel<false>;
-  kern<<<b->grid, rtg::kBatchThreads, b->smem, b->stream>>>(b->d_desc[parity], b->d_items, b->nitems, b->d_counter);
-  RT_BCUDA(cudaGetLastError());
+  RT_BCUDA(rtg::batch_variant(b->variant)
+                .launch(b->vel, b->grid, b->smem, b->d_desc[parity], b->d_items, b->nitems, b->d_counter, b->stream));
   return RT_OK;
 }
 
@@ -264,6 +229,73 @@ rt_status rt_batch_step(rt_batch *b, int nsteps) {
   if (nsteps & 1)
     for (rt_ctx *c : b->ctxs) c->cur = 1 - c->cur;
   b->phase = (b->phase + nsteps) & 1;
+  return RT_OK;
+}
+
+rt_status rt_batch_autotune(rt_batch *b, int trial_steps, double *ms, int *chosen) {
+  if (!b) return rtg::set_error(RT_E_INVALID, "rt_batch_autotune: NULL batch");
+  if (trial_steps < 1) return rtg::set_error(RT_E_INVALID, "rt_batch_autotune: trial_steps < 1");
+  if (b->ctxs.empty()) {
+    if (chosen) *chosen = b->variant;
+    return RT_OK;
+  }
+  // Trial launches all use the current parity: they read each member's
+  // I[cur] and mom[cur] and write only I[1 - cur] and mom[1 - cur] (scratch
+  // until the next real step), T in place and the step sources.  Save those
+  // and the Newton-failure words, restore them afterwards.
+  std::vector<int> flags(b->ctxs.size(), 0);
+  for (size_t i = 0; i < b->ctxs.size(); ++i) {
+    rt_ctx *c = b->ctxs[i];
+    const size_t N = (size_t)c->N;
+    RT_BCUDA(cudaMemcpyAsync(c->stage, c->T, N * sizeof(double), cudaMemcpyDeviceToDevice, b->stream));
+    RT_BCUDA(cudaMemcpyAsync(c->stage + N, c->dEgas, N * sizeof(double), cudaMemcpyDeviceToDevice, b->stream));
+    RT_BCUDA(cudaMemcpyAsync(c->stage + 2 * N, c->dMom, 3 * N * c->rs, cudaMemcpyDeviceToDevice, b->stream));
+    RT_BCUDA(cudaMemcpyAsync(&flags[i], c->flags, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  }
+  RT_BCUDA(cudaStreamSynchronize(b->stream));
+  const int keep = b->variant;
+  double t[rtg::kBatchVariants];
+  int best = -1;
+  cudaEvent_t e0, e1;
+  RT_BCUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return rtg::set_error(RT_E_CUDA, "rt_batch_autotune: event");
+  }
+  rt_status st = RT_OK;
+  for (int v = 0; v < rtg::kBatchVariants && st == RT_OK; ++v) {
+    t[v] = -1.0;
+    b->variant = v;
+    if (rebuild(b) != RT_OK) continue;   // this variant's tiles do not fit the largest angle set
+    st = enqueue_step(b, 0);
+    if (st == RT_OK && cudaEventRecord(e0, b->stream) != cudaSuccess) st = RT_E_CUDA;
+    for (int k = 0; k < trial_steps && st == RT_OK; ++k) st = enqueue_step(b, 0);
+    float el = 0;
+    if (st == RT_OK && (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                        cudaEventElapsedTime(&el, e0, e1) != cudaSuccess))
+      st = rtg::set_error(RT_E_CUDA, "rt_batch_autotune: timing");
+    if (st != RT_OK) break;
+    t[v] = (double)el / trial_steps;
+    if (best < 0 || t[v] < t[best]) best = v;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->variant = best >= 0 ? best : keep;
+  b->dirty = true;
+  for (size_t i = 0; i < b->ctxs.size(); ++i) {
+    rt_ctx *c = b->ctxs[i];
+    const size_t N = (size_t)c->N;
+    RT_BCUDA(cudaMemcpyAsync(c->T, c->stage, N * sizeof(double), cudaMemcpyDeviceToDevice, b->stream));
+    RT_BCUDA(cudaMemcpyAsync(c->dEgas, c->stage + N, N * sizeof(double), cudaMemcpyDeviceToDevice, b->stream));
+    RT_BCUDA(cudaMemcpyAsync(c->dMom, c->stage + 2 * N, 3 * N * c->rs, cudaMemcpyDeviceToDevice, b->stream));
+    RT_BCUDA(cudaMemcpyAsync(c->flags, &flags[i], sizeof(int), cudaMemcpyHostToDevice, b->stream));
+  }
+  RT_BCUDA(cudaStreamSynchronize(b->stream));
+  if (st != RT_OK) return st;
+  if (best < 0) return rtg::set_error(RT_E_INVALID, "rt_batch_autotune: no variant fits the largest angle set");
+  if (ms)
+    for (int v = 0; v < rtg::kBatchVariants; ++v) ms[v] = t[v];
+  if (chosen) *chosen = best;
   return RT_OK;
 }
 

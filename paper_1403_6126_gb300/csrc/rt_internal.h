@@ -59,6 +59,11 @@ bool choose_tile(int dim, int M, bool has_v, TileShape *out);
 template <typename Real>
 bool tile_ok(int dim, int M, bool has_v, TileShape t);
 
+// The compiled shapes that can run (dim, M, has_v), preferred first; out
+// holds up to 8.  Returns their count.
+template <typename Real>
+int tile_candidates(int dim, int M, bool has_v, TileShape *out);
+
 // Elementwise helpers (all stream-ordered).
 template <typename Real>
 cudaError_t launch_convert_in(const double *src, Real *dst, long long n, cudaStream_t s);

@@ -37,6 +37,15 @@ bool fits(int dim, int M, bool has_v, TileShape t) {
 }  // namespace
 
 template <typename Real>
+int tile_candidates(int dim, int M, bool has_v, TileShape *out) {
+  TileShape list[8];
+  int n = shape_list<Real>(dim, list), k = 0;
+  for (int i = 0; i < n; ++i)
+    if (fits<Real>(dim, M, has_v, list[i])) out[k++] = list[i];
+  return k;
+}
+
+template <typename Real>
 bool tile_ok(int dim, int M, bool has_v, TileShape t) {
   TileShape list[8];
   int n = shape_list<Real>(dim, list);
@@ -72,6 +81,8 @@ cudaError_t launch_step<double>(const StepArgs<double> &a, int dim, bool has_v, 
 template bool choose_tile<float>(int, int, bool, TileShape *);
 template bool choose_tile<double>(int, int, bool, TileShape *);
 template bool tile_ok<float>(int, int, bool, TileShape);
+template int tile_candidates<float>(int, int, bool, TileShape *);
+template int tile_candidates<double>(int, int, bool, TileShape *);
 template bool tile_ok<double>(int, int, bool, TileShape);
 
 }  // namespace rtg

@@ -130,10 +130,11 @@ def box2d(n=256, angles="s8", seed=2, steps=500, precision="fp32", kmax=None):
 def batched(nprob=512, seed=5, steps=200):
     """Many independent problems of uneven size: half 1-D slabs (cells
     log-uniform in 64..4096, Gauss-Legendre M in {8,16,24,32,40,48}, copy /
-    vacuum ends), half 2-D periodic boxes (nx, ny log-uniform in 32..256
-    independently, S2/S4/S6 = 8/24/48 angles).  Opacities as in slab1d
-    (sigma_a = 1e-2, sigma_s = 10^U(-1,2) per cell), rho = 1, T = 1 live,
-    v = 0, Crat = 10, Prat = 1, float intensities."""
+    vacuum ends), half 2-D slabs (nx, ny log-uniform in 32..256
+    independently, S2/S4/S6 = 8/24/48 angles) with the slab's boundaries
+    along x (x = 0 copies all rays, x = 1 vacuum) and periodic in y.
+    Opacities as in slab1d (sigma_a = 1e-2, sigma_s = 10^U(-1,2) per cell),
+    rho = 1, T = 1 live, v = 0, Crat = 10, Prat = 1, float intensities."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(nprob):
@@ -147,8 +148,9 @@ def batched(nprob=512, seed=5, steps=200):
             ang = str(rng.choice(["s2", "s4", "s6"]))
             N = nx * ny
             r2 = np.random.default_rng(int(rng.integers(1 << 30)))
-            wl = dict(name="box2d", shape=(1, ny, nx), dim=2, lo=(0.0, 0.0, 0.0), hi=(1.0, ny / nx, 1.0),
-                      bc=((PERIODIC, PERIODIC),) * 3, angles=ang, C=10.0, P=1.0, gamma=5.0 / 3.0, R=1.0, cfl=0.4,
+            wl = dict(name="slab2d", shape=(1, ny, nx), dim=2, lo=(0.0, 0.0, 0.0), hi=(1.0, ny / nx, 1.0),
+                      bc=((COPY, VACUUM), (PERIODIC, PERIODIC), (PERIODIC, PERIODIC)), angles=ang, C=10.0, P=1.0,
+                      gamma=5.0 / 3.0, R=1.0, cfl=0.4,
                       estimate_v=False, steps=steps, rho=np.ones(N), T=np.ones(N), v=np.zeros((3, N)),
                       sa=np.full(N, 1e-2), ss=10.0 ** r2.uniform(-1.0, 2.0, N), I0="isotropic_quarter_pi",
                       inflow={})
