@@ -30,7 +30,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PROFILE = os.path.join(ROOT, "profiles", "step_kernel_box3d.md")
-KERNEL_SRC = os.path.join(ROOT, "paper_1403_6126_gb300", "csrc", "rt_step_kernel.cuh")
+# sources of the float step kernel (the pair kernel and the tile geometry it shares)
+KERNEL_SRCS = [os.path.join(ROOT, "paper_1403_6126_gb300", "csrc", f) for f in ("rt_step_pair.cuh", "rt_step_kernel.cuh")]
+NOMINAL_HBM_GBS = 8000.0
 
 
 def algorithmic_bytes_per_cell(M, rs, velocity, live_T):
@@ -48,9 +50,12 @@ def algorithmic_bytes_per_cell(M, rs, velocity, live_T):
     return b
 
 
-def _sha(path):
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def kernel_sha():
+    h = hashlib.sha256()
+    for path in KERNEL_SRCS:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def _profile_traffic():
@@ -65,7 +70,7 @@ def _profile_traffic():
         if line.startswith("- ") and ":" in line:
             k, v = line[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel_source_sha256_16") != _sha(KERNEL_SRC):
+    if vals.get("kernel_source_sha256_16") != kernel_sha():
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -235,8 +240,11 @@ def run_gpu(args):
     ctx.set_intensity(wlmod.initial_intensity(wl, M))
     ctx.set_material(wl["rho"], wl["T"], wl["v"], wl["sa"], wl["ss"])
     dt = ctx.cfl_dt()
+    tuned = None
     if args.tile:
         ctx.set_tile(*[int(x) for x in args.tile.split("x")])
+    elif not args.no_autotune:
+        tuned = [dict(tile="%dx%dx%d" % t[:3], ms=t[3]) for t in ctx.autotune(3)]
     tile = ctx.tile()
     velocity = bool(np.any(wl["v"] != 0)) or wl["estimate_v"]
     rs = 8 if wl["precision"] == "fp64" else 4
@@ -288,8 +296,12 @@ def run_gpu(args):
     traffic = _profile_traffic()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
                 "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
-                "kernel": "step_kernel<float,3,true,%d,%d,%d>" % tile}
+                "kernel": ("step_kernel2<%d,%s,%d,%d,%d>" % ((wl["dim"], "true" if velocity else "false") + tile)
+                           if rs == 4 else "step_kernel<double,%d,%s,%d,%d,%d>"
+                           % ((wl["dim"], "true" if velocity else "false") + tile)),
+                "tile": "%dx%dx%d" % tile, "autotune": tuned}
 
     # end to end through the C ABI with host buffers: per step the gas
     # fields go host->device, the moments and sources come back
@@ -299,7 +311,9 @@ def run_gpu(args):
     clocks = sampler.summary()
     ctx.close()
 
-    batched = serving = None
+    batched = serving = small = None
+    if world == 1 and not args.no_small:
+        small = bench_small(stream)
     if world == 1 and not args.no_batch:
         batched = bench_batched(args, stream)
     if world == 1 and not args.no_serve:
@@ -321,7 +335,7 @@ def run_gpu(args):
                        "l2": "inputs larger than L2: %.2f GB of intensity read per step" % (N * M * rs / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
-            "batched": batched, "serving": serving,
+            "small_configs": small, "batched": batched, "serving": serving,
         }
         print(json.dumps(line))
     if world > 1:
@@ -385,6 +399,7 @@ def bench_batched(args, stream):
     b = rt.rt_batch_create(stream.cuda_stream)
     for c in ctxs:
         rt.rt_batch_add(b, c.ctx)
+    tune_ms, chosen = rt.rt_batch_autotune(b, 3)
     K = args.batch_steps
     rt.rt_batch_step(b, 3)
     torch.cuda.synchronize()
@@ -413,9 +428,54 @@ def bench_batched(args, stream):
                         "T live, float intensities" % len(wls),
             "value": units / (ms / 1e3), "unit": "cell-angle updates/s", "ms_per_step": ms, "steps": K,
             "cell_angles": units, "launches_per_step": 1,
+            "autotune": {"ms_per_step": dict(zip(("512 threads", "256 threads", "128 threads"), tune_ms)),
+                         "chosen": ("512 threads", "256 threads", "128 threads")[chosen]},
             "one_at_a_time": {"value": units / (ms_one / 1e3), "ms_per_step": ms_one, "launches_per_step": len(wls)},
             "hbm": {"achieved": nbytes / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                     "frac": nbytes / (ms / 1e3) / 1e9 / peak}}
+
+
+def bench_small(stream):
+    """Configs 0 and 1: the 1-D slab (512 cells x 8 angles, FP64, 2000
+    steps in one captured graph; launch/latency bound, so microseconds per
+    step) and the 2-D shadow problem (256 x 128 cells x 80 angles, 4000
+    steps, FP64 and FP32 intensities; its working set fits in L2, so the
+    bandwidth is reported against the HBM peaks with that caveat)."""
+    import torch
+    from paper_1403_6126_gb300 import workloads as wlmod
+    peak, _ = _peaks()
+    out = {}
+    runs = [("slab1d", wlmod.slab1d(), "fp64"), ("shadow2d_fp64", wlmod.shadow2d(), "fp64"),
+            ("shadow2d_fp32", wlmod.shadow2d(), "fp32")]
+    for key, wl, prec in runs:
+        n, w = _angles(wl["angles"])
+        M, N = len(w), int(np.prod(wl["shape"]))
+        c = _context(wl, n, w, stream=stream.cuda_stream, precision=prec)
+        c.set_intensity(wlmod.initial_intensity(wl, M))
+        c.set_material(wl["rho"], wl["T"], wl["v"], wl["sa"], wl["ss"])
+        dt = c.cfl_dt()
+        tuned = [dict(tile="x".join(str(v) for v in t[:3]), ms=t[3]) for t in c.autotune(5)]
+        c.run(dt, 10)           # warm-up, and the graph for 10 steps
+        c.sync()
+        steps = wl["steps"]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c.run(dt, steps)        # capture the graph for the timed length
+        c.sync()
+        e0.record(stream)
+        c.run(dt, steps)
+        e1.record(stream)
+        c.sync()
+        ms = e0.elapsed_time(e1) / steps
+        rs = 8 if prec == "fp64" else 4
+        bpc = algorithmic_bytes_per_cell(M, rs, False, not wl["hold_T"]) * N
+        out[key] = {"workload": "%s: %s cells x %d angles, %s intensities, %d steps in one CUDA graph"
+                                % (wl["name"], "x".join(str(x) for x in wl["shape"][::-1] if x > 1) or "1", M, prec, steps),
+                    "us_per_step": ms * 1e3, "steps_per_s": 1e3 / ms, "cell_angle_updates_per_s": N * M / (ms / 1e3),
+                    "algorithmic_gb_s": bpc / (ms / 1e3) / 1e9, "frac_of_measured_hbm": bpc / (ms / 1e3) / 1e9 / peak,
+                    "working_set_mb": bpc / 1e6, "tile": "x".join(str(v) for v in c.tile()), "autotune": tuned,
+                    "note": "working set fits in L2 (126 MB): a bandwidth fraction here is an L2 figure"}
+        c.close()
+    return out
 
 
 def _submit_args(wl):
@@ -469,9 +529,13 @@ def bench_serving(args):
     burst, _, _ = run(np.zeros(len(reqs)))          # capacity: all at once
     capacity = len(reqs) / burst
     rng = np.random.default_rng(60)
-    arrivals = np.cumsum(rng.exponential(1.0 / (0.8 * capacity), len(reqs)))
+    gaps = rng.exponential(1.0, len(reqs))
+    arrivals = np.cumsum(gaps / (0.8 * capacity))
     arrivals -= arrivals[0]
     makespan, lat, steps = run(arrivals)
+    over = np.cumsum(gaps / (2.0 * capacity))      # the same stream at 2x capacity
+    over -= over[0]
+    over_makespan, over_lat, _ = run(over)
     # one at a time, FP64: time a subset, then scale to the whole stream by
     # its cell-angle-steps (the subset's seconds per cell-angle-step)
     work = [int(np.prod(wl["shape"])) * len(r[2][1]) * wl["steps"] for r, wl in zip(reqs, wls)]
@@ -486,11 +550,14 @@ def bench_serving(args):
         c.close()
     fp64_s = time.perf_counter() - t0
     fp64_rate = len(reqs) / (fp64_s * sum(work) / sum(work[:k]))
-    return {"workload": "%d requests: 2-D 64..512^2 and 3-D 64..192^3, 24/80 angles, %d steps each, box gas fields; "
+    return {"workload": "%d requests: 2-D 64..512^2 and 3-D 64..192^3 (sides in steps of 32), 24/80 angles, %d steps each, box gas fields; "
                         "Poisson arrivals at 0.8 x measured capacity" % (len(reqs), args.serve_steps),
             "value": len(reqs) / makespan, "unit": "solves/s", "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)), "capacity_solves_s": capacity,
             "batch_steps": steps, "budget_gb": args.serve_budget_gb,
+            "overload_2x": {"value": len(reqs) / over_makespan, "unit": "solves/s",
+                            "p50_latency_s": float(np.percentile(over_lat, 50)),
+                            "p99_latency_s": float(np.percentile(over_lat, 99))},
             "fp64_one_at_a_time": {"value": fp64_rate, "unit": "solves/s", "timed_requests": k,
                                    "note": "first %d requests timed (%.1f s), scaled to the whole stream by "
                                            "cell-angle-steps" % (k, fp64_s)}}
@@ -509,10 +576,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=32)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-n", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=20)
-    ap.add_argument("--serve-n", type=int, default=32)
+    ap.add_argument("--serve-n", type=int, default=64)
     ap.add_argument("--serve-steps", type=int, default=200)
     ap.add_argument("--serve-fp64-n", type=int, default=6)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)

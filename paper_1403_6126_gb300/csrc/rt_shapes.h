@@ -1,18 +1,20 @@
 // Tile shapes (cells per CTA along x, y, z; one thread per cell) compiled
 // for each precision and grid dimension, preferred shape first.  A larger
-// tile stages a smaller halo per cell but needs more shared memory (the
-// per-cell angle array grows with the angle count), so big angle sets fall
-// back to smaller tiles.  X-macro lists: X(tx, ty, tz).
+// tile stages a smaller halo per cell but needs more shared memory (in the
+// double-precision kernel a per-cell angle array grows with the angle
+// count, so big angle sets fall back to smaller tiles); the smallest shapes
+// (32 threads) spread small grids over more SMs.  rt_autotune times the
+// shapes that fit.  X-macro lists: X(tx, ty, tz).
 #pragma once
 
 #include "rt_internal.h"
 
 #define RT_SHAPES_F3(X) X(16, 8, 4) X(8, 8, 4) X(8, 4, 4) X(4, 4, 4)
-#define RT_SHAPES_F2(X) X(32, 16, 1) X(16, 16, 1) X(16, 8, 1) X(8, 8, 1)
-#define RT_SHAPES_F1(X) X(512, 1, 1) X(256, 1, 1) X(128, 1, 1) X(64, 1, 1)
+#define RT_SHAPES_F2(X) X(32, 16, 1) X(16, 16, 1) X(16, 8, 1) X(8, 8, 1) X(8, 4, 1)
+#define RT_SHAPES_F1(X) X(512, 1, 1) X(256, 1, 1) X(128, 1, 1) X(64, 1, 1) X(32, 1, 1)
 #define RT_SHAPES_D3(X) X(8, 8, 4) X(8, 4, 4) X(4, 4, 4)
-#define RT_SHAPES_D2(X) X(16, 16, 1) X(16, 8, 1) X(8, 8, 1)
-#define RT_SHAPES_D1(X) X(256, 1, 1) X(128, 1, 1) X(64, 1, 1)
+#define RT_SHAPES_D2(X) X(16, 16, 1) X(16, 8, 1) X(8, 8, 1) X(8, 4, 1)
+#define RT_SHAPES_D1(X) X(256, 1, 1) X(128, 1, 1) X(64, 1, 1) X(32, 1, 1)
 
 namespace rtg {
 // Launchers of the compiled shapes, one translation unit per group; they

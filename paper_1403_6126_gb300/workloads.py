@@ -163,18 +163,30 @@ def batched(nprob=512, seed=5, steps=200):
 def serving(nreq=32, seed=6, steps=200, scale=1.0):
     """Requests for the serving loop: even ones 2-D (side log-uniform in
     64..512 x scale), odd ones 3-D (side log-uniform in 64..192 x scale),
-    24 or 80 angles (S4 / S8), gas fields as in box3d with the velocity
-    spectrum cut at side/8 (at least eight cells across its shortest
-    wavelength), each `steps` steps; the arrival gaps are drawn by the
-    caller."""
+    sides rounded to multiples of 32 (8 when scale < 1), 24 or 80 angles
+    (S4 / S8), gas fields as in box3d with the velocity spectrum cut at
+    side/8 (at least eight cells across its shortest wavelength), each
+    `steps` steps.  Density and velocity are drawn once per (dimension,
+    side); every request draws its own sigma_a, sigma_s (10^U(0, 3) per
+    cell), so long streams stay cheap to generate.  The arrival gaps are
+    drawn by the caller."""
     rng = np.random.default_rng(seed)
+    q = 32 if scale >= 1 else 8
+    cache = {}
     out = []
     for i in range(nreq):
         ang = str(rng.choice(["s4", "s8"]))
         lo, hi = (64, 512) if i % 2 == 0 else (64, 192)
-        side = max(4, int(round(np.exp(rng.uniform(np.log(lo * scale), np.log(hi * scale))))))
+        side = max(q, int(round(np.exp(rng.uniform(np.log(lo * scale), np.log(hi * scale))) / q)) * q)
         make = box2d if i % 2 == 0 else box3d
-        out.append(make(n=side, angles=ang, seed=int(rng.integers(1 << 20)), steps=steps, kmax=max(1.0, side / 8)))
+        key = (make.__name__, side)
+        if key not in cache:
+            cache[key] = make(n=side, angles="s4", seed=1000 + side, steps=steps, kmax=max(1.0, side / 8))
+        base = cache[key]
+        ro = np.random.default_rng(int(rng.integers(1 << 30)))
+        N = int(np.prod(base["shape"]))
+        out.append(dict(base, angles=ang, steps=steps, sa=10.0 ** ro.uniform(0.0, 3.0, N),
+                        ss=10.0 ** ro.uniform(0.0, 3.0, N)))
     return out
 
 
