@@ -209,6 +209,24 @@ rt_status rt_sources(rt_ctx *ctx, double *dE_gas, double *dMom, double *T_new);
 /* Copies the current intensity out (M*N values, angle-major). */
 rt_status rt_get_intensity(rt_ctx *ctx, double *I);
 
+/* ---- checkpoint / resume -----------------------------------------------------
+ * The restartable state of a context: the current intensity and its moments
+ * in the storage type, T, the material (rho, sigma_a, sigma_s, v), the
+ * inflow tables and the sources of the last step, behind a header that
+ * names the grid, angle count, precision, Crat and Prat.  A fresh context
+ * made by rt_create with the same grid, angles and options, loaded with
+ * rt_load_state, continues bitwise as the saved one would have.  buf is
+ * host memory owned by the caller.  The paper has no counterpart (its
+ * restart files are Athena++'s). */
+size_t rt_state_bytes(const rt_ctx *ctx);
+/* Waits for the context's stream, then copies the state into buf (bytes >=
+ * rt_state_bytes).  RT_E_STATE before rt_set_material. */
+rt_status rt_save_state(rt_ctx *ctx, void *buf, size_t bytes);
+/* Restores a saved state.  RT_E_INVALID when the header does not match this
+ * context (grid, angle count, precision, Crat, Prat) or bytes is short;
+ * RT_E_STATE for a context that belongs to a batch.  Waits for the stream. */
+rt_status rt_load_state(rt_ctx *ctx, const void *buf, size_t bytes);
+
 /* Frees the context and its device state (removing it from its batch
  * first).  NULL is ignored. */
 void rt_destroy(rt_ctx *ctx);

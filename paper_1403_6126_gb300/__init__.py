@@ -85,6 +85,9 @@ def lib():
             "rt_get_tile": (I, [V, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
             "rt_autotune": (I, [V, I, ctypes.POINTER(rt_tile_time), I, ctypes.POINTER(I)]),
             "rt_batch_autotune": (I, [V, I, _DP, ctypes.POINTER(I)]),
+            "rt_state_bytes": (ctypes.c_size_t, [V]),
+            "rt_save_state": (I, [V, V, ctypes.c_size_t]),
+            "rt_load_state": (I, [V, V, ctypes.c_size_t]),
             "rt_step": (I, [V, D]),
             "rt_run": (I, [V, D, I]),
             "rt_sync": (I, [V]),
@@ -193,6 +196,22 @@ def rt_autotune(ctx, trial_steps=3):
     n = ctypes.c_int(0)
     _check(lib().rt_autotune(ctx, trial_steps, buf, 8, ctypes.byref(n)), "rt_autotune")
     return [(t.tx, t.ty, t.tz, t.ms) for t in buf[: n.value]]
+
+
+def rt_state_bytes(ctx):
+    return lib().rt_state_bytes(ctx)
+
+
+def rt_save_state(ctx):
+    """The context's restartable state as a uint8 numpy array."""
+    buf = np.empty(rt_state_bytes(ctx), dtype=np.uint8)
+    _check(lib().rt_save_state(ctx, buf.ctypes.data, buf.nbytes), "rt_save_state")
+    return buf
+
+
+def rt_load_state(ctx, buf):
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(lib().rt_load_state(ctx, buf.ctypes.data, buf.nbytes), "rt_load_state")
 
 
 def rt_cfl_dt(ctx):
@@ -385,6 +404,12 @@ class Context:
 
     def autotune(self, trial_steps=3):
         return rt_autotune(self.ctx, trial_steps)
+
+    def save_state(self):
+        return rt_save_state(self.ctx)
+
+    def load_state(self, buf):
+        rt_load_state(self.ctx, buf)
 
     def step(self, dt=0.0):
         rt_step(self.ctx, dt)

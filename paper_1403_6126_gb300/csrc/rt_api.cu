@@ -464,6 +464,112 @@ rt_status rt_autotune(rt_ctx *c, int trial_steps, rt_tile_time *times, int cap, 
   return RT_OK;
 }
 
+namespace {
+
+struct StateHeader {
+  char magic[8];
+  int dim, n[3], M, rs, has_v, intensity_set;
+  long long N;
+  double C, P;
+};
+const char kStateMagic[8] = {'R', 'T', 'S', 'T', 'A', 'T', 'E', '1'};
+
+// (device pointer, bytes) of every saved array, in file order.
+int state_parts(rt_ctx *c, void **ptr, size_t *bytes) {
+  const size_t N = (size_t)c->N, M = (size_t)c->M, rs = c->rs;
+  int k = 0;
+  auto add = [&](void *p, size_t b) { ptr[k] = p; bytes[k] = b; ++k; };
+  add(c->I[c->cur], rs * M * N);
+  add(c->mom[c->cur], rs * 10 * N);
+  add(c->T, 8 * N);
+  add(c->rho, rs * N);
+  add(c->sa, rs * N);
+  add(c->ss, rs * N);
+  add(c->v, rs * 3 * N);
+  add(c->dEgas, 8 * N);
+  add(c->dMom, rs * 3 * N);
+  add(c->inflow, rs * 6 * M);
+  return k;
+}
+
+}  // namespace
+
+size_t rt_state_bytes(const rt_ctx *c) {
+  if (!c) return 0;
+  void *p[16];
+  size_t b[16], total = sizeof(StateHeader) + sizeof(double) * 6 * (size_t)c->M;
+  const int k = state_parts(const_cast<rt_ctx *>(c), p, b);
+  for (int i = 0; i < k; ++i) total += b[i];
+  return total;
+}
+
+rt_status rt_save_state(rt_ctx *c, void *buf, size_t bytes) {
+  if (!c || !buf) return fail(RT_E_INVALID, "rt_save_state: NULL argument");
+  if (bytes < rt_state_bytes(c)) return fail(RT_E_INVALID, "rt_save_state: buffer smaller than rt_state_bytes");
+  if (!c->material_set) return fail(RT_E_STATE, "rt_save_state: call rt_set_material first");
+  RT_CUDA(cudaStreamSynchronize(c->stream));
+  StateHeader h{};
+  std::memcpy(h.magic, kStateMagic, 8);
+  h.dim = c->dim;
+  for (int d = 0; d < 3; ++d) h.n[d] = c->n[d];
+  h.M = c->M;
+  h.rs = (int)c->rs;
+  h.has_v = c->has_v;
+  h.intensity_set = c->intensity_set;
+  h.N = c->N;
+  h.C = c->C;
+  h.P = c->P;
+  char *out = static_cast<char *>(buf);
+  std::memcpy(out, &h, sizeof h);
+  out += sizeof h;
+  std::memcpy(out, c->host_inflow.data(), sizeof(double) * 6 * (size_t)c->M);
+  out += sizeof(double) * 6 * (size_t)c->M;
+  void *p[16];
+  size_t b[16];
+  const int k = state_parts(c, p, b);
+  for (int i = 0; i < k; ++i) {
+    RT_CUDA(cudaMemcpyAsync(out, p[i], b[i], cudaMemcpyDeviceToHost, c->stream));
+    out += b[i];
+  }
+  RT_CUDA(cudaStreamSynchronize(c->stream));
+  return RT_OK;
+}
+
+rt_status rt_load_state(rt_ctx *c, const void *buf, size_t bytes) {
+  if (!c || !buf) return fail(RT_E_INVALID, "rt_load_state: NULL argument");
+  if (c->batch) return fail(RT_E_STATE, "rt_load_state: the context belongs to a batch");
+  if (bytes < sizeof(StateHeader)) return fail(RT_E_INVALID, "rt_load_state: buffer too short");
+  StateHeader h;
+  std::memcpy(&h, buf, sizeof h);
+  bool same = std::memcmp(h.magic, kStateMagic, 8) == 0 && h.dim == c->dim && h.M == c->M &&
+              h.rs == (int)c->rs && h.N == c->N && h.C == c->C && h.P == c->P;
+  for (int d = 0; d < 3; ++d) same = same && h.n[d] == c->n[d];
+  if (!same) return fail(RT_E_INVALID, "rt_load_state: the state was saved from a different grid, angle set, precision or Crat/Prat");
+  if (bytes < rt_state_bytes(c)) return fail(RT_E_INVALID, "rt_load_state: buffer shorter than the saved state");
+  RT_CUDA(cudaStreamSynchronize(c->stream));
+  c->cur = 0;
+  const char *in = static_cast<const char *>(buf) + sizeof h;
+  std::memcpy(c->host_inflow.data(), in, sizeof(double) * 6 * (size_t)c->M);
+  in += sizeof(double) * 6 * (size_t)c->M;
+  void *p[16];
+  size_t b[16];
+  const int k = state_parts(c, p, b);
+  for (int i = 0; i < k; ++i) {
+    RT_CUDA(cudaMemcpyAsync(p[i], in, b[i], cudaMemcpyHostToDevice, c->stream));
+    in += b[i];
+  }
+  RT_CUDA(cudaMemsetAsync(c->flags, 0, 2 * sizeof(int), c->stream));
+  RT_CUDA(cudaStreamSynchronize(c->stream));
+  c->has_v = h.has_v != 0;
+  c->intensity_set = h.intensity_set != 0;
+  c->material_set = true;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return RT_OK;
+}
+
 rt_status rt_get_tile(const rt_ctx *c, int *tx, int *ty, int *tz) {
   if (!c || !tx || !ty || !tz) return fail(RT_E_INVALID, "rt_get_tile: NULL argument");
   *tx = c->tile.tx;
