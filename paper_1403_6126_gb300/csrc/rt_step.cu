@@ -3,6 +3,7 @@
 // the compiled shapes are listed in rt_shapes.h.
 #include "rt_shapes.h"
 #include "rt_step_pair.cuh"
+#include "rt_split.cuh"
 
 namespace rtg {
 
@@ -15,7 +16,12 @@ int shape_list(int dim, TileShape *out) {
   if (sizeof(Real) == 4) {
     if (dim == 1) { RT_SHAPES_F1(RT_ADD) }
     else if (dim == 2) { RT_SHAPES_F2(RT_ADD) }
-    else { RT_SHAPES_F3(RT_ADD) }
+    else {
+      RT_SHAPES_F3(RT_ADD)
+#define RT_ADD2(X, Y) out[n++] = TileShape{X, Y, 0};
+      RT_SHAPES_S3(RT_ADD2)
+#undef RT_ADD2
+    }
   } else {
     if (dim == 1) { RT_SHAPES_D1(RT_ADD) }
     else if (dim == 2) { RT_SHAPES_D2(RT_ADD) }
@@ -29,6 +35,7 @@ int shape_list(int dim, TileShape *out) {
 // float, the scalar kernel for double.
 template <typename Real>
 bool fits(int dim, int M, bool has_v, TileShape t) {
+  if (t.tz == 0) return true;   // the two-kernel path stages one x-y layer: a few KB
   const size_t sm = sizeof(Real) == 4 ? stepk::smem_bytes2(dim, M, has_v, t.tx, t.ty, t.tz)
                                       : stepk::smem_bytes(dim, M, has_v, t.tx, t.ty, t.tz, sizeof(Real));
   return sm <= 227 * 1024;
@@ -38,7 +45,7 @@ bool fits(int dim, int M, bool has_v, TileShape t) {
 
 template <typename Real>
 int tile_candidates(int dim, int M, bool has_v, TileShape *out) {
-  TileShape list[8];
+  TileShape list[16];
   int n = shape_list<Real>(dim, list), k = 0;
   for (int i = 0; i < n; ++i)
     if (fits<Real>(dim, M, has_v, list[i])) out[k++] = list[i];
@@ -47,7 +54,7 @@ int tile_candidates(int dim, int M, bool has_v, TileShape *out) {
 
 template <typename Real>
 bool tile_ok(int dim, int M, bool has_v, TileShape t) {
-  TileShape list[8];
+  TileShape list[16];
   int n = shape_list<Real>(dim, list);
   for (int i = 0; i < n; ++i)
     if (list[i].tx == t.tx && list[i].ty == t.ty && list[i].tz == t.tz)
@@ -57,7 +64,7 @@ bool tile_ok(int dim, int M, bool has_v, TileShape t) {
 
 template <typename Real>
 bool choose_tile(int dim, int M, bool has_v, TileShape *out) {
-  TileShape list[8];
+  TileShape list[16];
   int n = shape_list<Real>(dim, list);
   for (int i = 0; i < n; ++i) {
     if (fits<Real>(dim, M, has_v, list[i])) {
@@ -67,6 +74,8 @@ bool choose_tile(int dim, int M, bool has_v, TileShape *out) {
   }
   return false;
 }
+
+size_t split_scratch_bytes(long long N) { return split::scratch_bytes(N); }
 
 template <>
 cudaError_t launch_step<float>(const StepArgs<float> &a, int dim, bool has_v, TileShape t, cudaStream_t s) {
