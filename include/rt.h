@@ -151,12 +151,8 @@ rt_status rt_set_intensity(rt_ctx *ctx, const double *I);
 rt_status rt_set_inflow(rt_ctx *ctx, int axis, int side, const double *I_ghost);
 
 /* Tile of cells one CTA of the step kernel owns (tx x ty x tz, one thread
- * per cell; ty = 1 for 1-D, tz = 1 below 3-D).  In 3-D with RT_FP32, tz = 0
- * selects the two-kernel path instead: the transport (sec. 4.2) marched
- * along z over a tx x ty column of cells, then the implicit steps and the
- * quadrature one thread per cell (same results, bitwise; it allocates
- * 64 bytes per cell of scratch the first time it is chosen).  (0, 0, 0)
- * restores the default choice.  RT_E_INVALID when the shape is not one of the compiled
+ * per cell; ty = 1 for 1-D, tz = 1 below 3-D).  (0, 0, 0) restores the
+ * default choice.  RT_E_INVALID when the shape is not one of the compiled
  * shapes or exceeds the 227 KB of shared memory (which grows with the angle
  * count).  Float results do not depend on the tile (bitwise); double
  * results may differ in the last bit, as the compiler fuses multiply-adds

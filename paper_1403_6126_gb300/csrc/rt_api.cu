@@ -45,7 +45,7 @@ namespace {
 void free_all(rt_ctx *c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   void *ptrs[] = {c->I[0], c->I[1], c->mom[0], c->mom[1], c->rho, c->sa, c->ss, c->v,
-                  c->T, c->dEgas, c->dMom, c->ang, c->inflow, c->flags, c->stage, c->split_scr};
+                  c->T, c->dEgas, c->dMom, c->ang, c->inflow, c->flags, c->stage};
   for (void *p : ptrs)
     if (p) cudaFree(p);
 }
@@ -88,23 +88,7 @@ rtg::StepArgs<Real> rtg::make_args(rt_ctx *c, double dt) {
   a.dEgas = c->dEgas;
   a.dMom = (Real *)c->dMom;
   a.status = c->flags;
-  a.scr_w = nullptr;
-  a.scr_face = nullptr;
-  if (sizeof(Real) == 4 && c->split_scr) {
-    a.scr_w = static_cast<float4 *>(c->split_scr);
-    a.scr_face = reinterpret_cast<float2 *>(static_cast<char *>(c->split_scr) + sizeof(float4) * (size_t)c->N);
-  }
   return a;
-}
-
-rt_status rtg::ensure_split_scratch(rt_ctx *c) {
-  if (c->fp64 || c->dim != 3 || c->split_scr) return RT_OK;
-  if (cudaMalloc(&c->split_scr, rtg::split_scratch_bytes(c->N)) != cudaSuccess) {
-    cudaGetLastError();
-    c->split_scr = nullptr;
-    return fail(RT_E_NOMEM, "two-kernel path: device allocation of its per-cell scratch failed");
-  }
-  return RT_OK;
 }
 
 size_t rtg::context_bytes(long long N, int M, bool fp64) {
@@ -400,10 +384,6 @@ rt_status rt_set_tile(rt_ctx *c, int tx, int ty, int tz) {
   } else {
     bool ok = c->fp64 ? rtg::tile_ok<double>(c->dim, c->M, true, t) : rtg::tile_ok<float>(c->dim, c->M, true, t);
     if (!ok) return fail(RT_E_INVALID, "rt_set_tile: shape exceeds the thread, shared-memory or staging limits");
-    if (t.tz == 0) {
-      rt_status st = rtg::ensure_split_scratch(c);
-      if (st != RT_OK) return st;
-    }
   }
   c->tile = t;
   if (c->graph) {
@@ -421,19 +401,8 @@ rt_status rt_autotune(rt_ctx *c, int trial_steps, rt_tile_time *times, int cap, 
   if (c->batch) return fail(RT_E_STATE, "rt_autotune: the context belongs to a batch; use rt_batch_autotune");
   const bool vel = rtg::velocity_on(c);
   rtg::TileShape cand[16];
-  int nc = c->fp64 ? rtg::tile_candidates<double>(c->dim, c->M, true, cand)
-                   : rtg::tile_candidates<float>(c->dim, c->M, true, cand);
-  {
-    // the two-kernel path needs its scratch; without it, drop those shapes
-    bool any_split = false;
-    for (int i = 0; i < nc; ++i) any_split = any_split || cand[i].tz == 0;
-    if (any_split && rtg::ensure_split_scratch(c) != RT_OK) {
-      int k = 0;
-      for (int i = 0; i < nc; ++i)
-        if (cand[i].tz != 0) cand[k++] = cand[i];
-      nc = k;
-    }
-  }
+  const int nc = c->fp64 ? rtg::tile_candidates<double>(c->dim, c->M, true, cand)
+                         : rtg::tile_candidates<float>(c->dim, c->M, true, cand);
   if (nc == 0) return fail(RT_E_INVALID, "rt_autotune: no compiled tile fits");
   // The trial steps read I[cur] and write only I[1 - cur], mom[1 - cur]
   // (scratch until the next real step), T in place and the step sources:

@@ -38,7 +38,6 @@ struct rt_ctx {
   int graph_steps = 0, graph_cur = -1;
   bool graph_vel = false;
   void *batch = nullptr;  // the rt_batch this context belongs to, if any
-  void *split_scr = nullptr;  // per-cell scratch of the two-kernel 3-D path, allocated when first chosen
 };
 
 namespace rtg {
@@ -51,9 +50,6 @@ bool velocity_on(const rt_ctx *c);
 rt_status set_error(rt_status s, const std::string &msg);
 // Device bytes rt_create allocates for N cells and M angles.
 size_t context_bytes(long long N, int M, bool fp64);
-// Allocates the two-kernel path's scratch if the context can use it and has
-// none yet.
-rt_status ensure_split_scratch(rt_ctx *c);
 // Whether a problem of this dimension and angle count fits the batch tile.
 bool batch_fits(int dim, int M, bool vel);
 }  // namespace rtg

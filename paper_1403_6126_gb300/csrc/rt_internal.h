@@ -38,20 +38,13 @@ struct StepArgs {
   double *dEgas;      // [N]
   Real *dMom;         // [3][N]
   int *status;        // [0]: cells whose T Newton failed
-  // scratch of the two-kernel 3-D path (rt_split.cuh): IV weights [N] and
-  // face data [6][N]; null elsewhere
-  float4 *scr_w;
-  float2 *scr_face;
 };
 
 struct TileShape {
   int tx, ty, tz;
 };
 
-// Launch the step; returns the CUDA error of the launch.  In 3-D with float
-// intensities a tile with tz == 0 selects the two-kernel path (transport
-// marched along z over a tx x ty column, then the per-cell sources), which
-// needs a.scr_w / a.scr_face (split_scratch_bytes).
+// Launch the fused step; returns the CUDA error of the launch.
 template <typename Real>
 cudaError_t launch_step(const StepArgs<Real> &a, int dim, bool has_v, TileShape tile, cudaStream_t s);
 
@@ -70,10 +63,6 @@ bool tile_ok(int dim, int M, bool has_v, TileShape t);
 // holds up to 8.  Returns their count.
 template <typename Real>
 int tile_candidates(int dim, int M, bool has_v, TileShape *out);
-
-// Bytes of the two-kernel path's per-cell scratch.
-size_t split_scratch_bytes(long long N);
-cudaError_t launch_split(const StepArgs<float> &a, bool vel, TileShape t, cudaStream_t s);
 
 // Elementwise helpers (all stream-ordered).
 template <typename Real>

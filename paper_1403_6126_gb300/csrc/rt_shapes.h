@@ -10,9 +10,6 @@
 #include "rt_internal.h"
 
 #define RT_SHAPES_F3(X) X(16, 8, 4) X(8, 8, 4) X(8, 4, 4) X(4, 4, 4)
-// two-kernel 3-D path: x-y column tiles of the z-marching transport kernel
-// (listed with tz = 0)
-#define RT_SHAPES_S3(X) X(32, 8) X(16, 16) X(16, 8)
 #define RT_SHAPES_F2(X) X(32, 16, 1) X(16, 16, 1) X(16, 8, 1) X(8, 8, 1) X(8, 4, 1)
 #define RT_SHAPES_F1(X) X(512, 1, 1) X(256, 1, 1) X(128, 1, 1) X(64, 1, 1) X(32, 1, 1)
 #define RT_SHAPES_D3(X) X(8, 8, 4) X(8, 4, 4) X(4, 4, 4)
@@ -22,7 +19,7 @@
 namespace rtg {
 // Launchers of the compiled shapes, one translation unit per group; they
 // return cudaErrorInvalidConfiguration for a shape that is not compiled.
-cudaError_t launch_f3(const StepArgs<float> &a, bool vel, TileShape t, cudaStream_t s);  // tz == 0: launch_split
+cudaError_t launch_f3(const StepArgs<float> &a, bool vel, TileShape t, cudaStream_t s);
 cudaError_t launch_f12(const StepArgs<float> &a, int dim, bool vel, TileShape t, cudaStream_t s);
 cudaError_t launch_d(const StepArgs<double> &a, int dim, bool vel, TileShape t, cudaStream_t s);
 }  // namespace rtg

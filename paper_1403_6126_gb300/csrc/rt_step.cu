@@ -3,7 +3,6 @@
 // the compiled shapes are listed in rt_shapes.h.
 #include "rt_shapes.h"
 #include "rt_step_pair.cuh"
-#include "rt_split.cuh"
 
 namespace rtg {
 
@@ -16,12 +15,7 @@ int shape_list(int dim, TileShape *out) {
   if (sizeof(Real) == 4) {
     if (dim == 1) { RT_SHAPES_F1(RT_ADD) }
     else if (dim == 2) { RT_SHAPES_F2(RT_ADD) }
-    else {
-      RT_SHAPES_F3(RT_ADD)
-#define RT_ADD2(X, Y) out[n++] = TileShape{X, Y, 0};
-      RT_SHAPES_S3(RT_ADD2)
-#undef RT_ADD2
-    }
+    else { RT_SHAPES_F3(RT_ADD) }
   } else {
     if (dim == 1) { RT_SHAPES_D1(RT_ADD) }
     else if (dim == 2) { RT_SHAPES_D2(RT_ADD) }
@@ -35,7 +29,6 @@ int shape_list(int dim, TileShape *out) {
 // float, the scalar kernel for double.
 template <typename Real>
 bool fits(int dim, int M, bool has_v, TileShape t) {
-  if (t.tz == 0) return true;   // the two-kernel path stages one x-y layer: a few KB
   const size_t sm = sizeof(Real) == 4 ? stepk::smem_bytes2(dim, M, has_v, t.tx, t.ty, t.tz)
                                       : stepk::smem_bytes(dim, M, has_v, t.tx, t.ty, t.tz, sizeof(Real));
   return sm <= 227 * 1024;
@@ -74,8 +67,6 @@ bool choose_tile(int dim, int M, bool has_v, TileShape *out) {
   }
   return false;
 }
-
-size_t split_scratch_bytes(long long N) { return split::scratch_bytes(N); }
 
 template <>
 cudaError_t launch_step<float>(const StepArgs<float> &a, int dim, bool has_v, TileShape t, cudaStream_t s) {

@@ -5,7 +5,6 @@
 namespace rtg {
 
 cudaError_t launch_f3(const StepArgs<float> &a, bool vel, TileShape t, cudaStream_t s) {
-  if (t.tz == 0) return launch_split(a, vel, t, s);
 #define RT_CASE(X, Y, Z)                                                          \
   if (t.tx == X && t.ty == Y && t.tz == Z)                                        \
     return vel ? stepk::launch_shape2<3, true, X, Y, Z>(a, s)               \
