@@ -145,3 +145,86 @@ def test_batched_full_size_sampled_problems():
         assert errF <= TOL, (i, errF)
     for c in ctxs:
         c.close()
+
+
+def test_largest_grid_sampled_cells():
+    # The largest grid the ABI accepts (just under 2^28 cells), 9 angles (an
+    # odd count: the padded pair too): the intensity array holds 2.4e9
+    # values, past 32-bit indexing.  Fields are
+    # drawn on the device and passed as device pointers; one step from the
+    # isotropic equilibrium of a non-uniform temperature; sampled cells
+    # (including the last one) recomputed by the oracle on 5^3 windows.
+    import torch
+    nx, ny, nz = 1023, 512, 512
+    N = nx * ny * nz
+    M = 9
+    assert N < 2 ** 28 and M * N > 2 ** 31
+    dev = torch.device("cuda", 0)
+    gen = torch.Generator(device=dev).manual_seed(1403)
+    u = lambda: torch.rand(N, generator=gen, device=dev, dtype=torch.float64)
+    C = 10.0
+    f = dict(rho=1.0 + 0.5 * u(), T=1.0 + 0.2 * u(), sa=10.0 ** (2.0 * u()), ss=10.0 ** (2.0 * u()))
+    f["v"] = (0.05 * C) * (2.0 * torch.rand(3 * N, generator=gen, device=dev, dtype=torch.float64) - 1.0)
+    nn = np.random.default_rng(9).normal(size=(M, 3))
+    nn /= np.linalg.norm(nn, axis=1, keepdims=True)
+    w = np.full(M, 1.0 / M)
+    wl = dict(name="largest", shape=(nz, ny, nx), dim=3, lo=(0.0, 0.0, 0.0), hi=(nx / 512.0, 1.0, 1.0),
+              bc=((0, 0), (0, 0), (0, 0)), angles=None, C=C, P=1.0, gamma=5.0 / 3.0, R=1.0, cfl=0.4,
+              hold_T=False, estimate_v=True, inflow={})
+    ctx = gpu_context(wl, nn, w, "fp32", device_ptrs=True)
+    ctx.set_material(f["rho"], f["T"], f["v"], f["sa"], f["ss"])
+    ctx.set_intensity(None)                      # T^4 / (4 pi) of each cell
+    picks = [(0, 0, 0), (nx - 1, ny - 1, nz - 1), (nx - 1, 0, nz // 2), (511, 255, 300)]
+    rng = np.random.default_rng(4)
+    while len(picks) < 12:
+        picks.append((int(rng.integers(nx)), int(rng.integers(ny)), int(rng.integers(nz))))
+    rad, side = 2, 5
+    off = np.arange(-rad, rad + 1)
+    wins = []
+    for (x, y, z) in picks:
+        zi, yi, xi = (z + off) % nz, (y + off) % ny, (x + off) % nx
+        idx = (xi[None, None, :] + nx * (yi[None, :, None] + ny * zi[:, None, None])).reshape(-1)
+        wins.append(torch.as_tensor(idx, device=dev))
+    # inputs of each window as the device holds them (float-rounded fields)
+    I0 = torch.empty(M * N, dtype=torch.float64, device=dev)
+    rt.rt_get_intensity(ctx.ctx, I0)
+    torch.cuda.synchronize()
+    I0 = I0.view(M, N)
+    host = []
+    for idx in wins:
+        r = lambda t: t[idx].to(torch.float32).double().cpu().numpy()
+        host.append(dict(I=I0[:, idx].cpu().numpy(), T=f["T"][idx].cpu().numpy(), rho=r(f["rho"]), sa=r(f["sa"]),
+                         ss=r(f["ss"]), v=np.stack([r(f["v"][d * N:(d + 1) * N]) for d in range(3)])))
+    ctx._keep = None            # the library holds its own copies once the stream is done
+    del I0, f
+    torch.cuda.empty_cache()
+    dt = ctx.cfl_dt()
+    ctx.step(dt)
+    ctx.sync()
+    I1 = torch.empty(M * N, dtype=torch.float64, device=dev)
+    rt.rt_get_intensity(ctx.ctx, I1)
+    E = torch.empty(N, dtype=torch.float64, device=dev)
+    Fm = torch.empty(3 * N, dtype=torch.float64, device=dev)
+    Pm = torch.empty(6 * N, dtype=torch.float64, device=dev)
+    rt.rt_moments(ctx.ctx, E, Fm, Pm)
+    Tn = torch.empty(N, dtype=torch.float64, device=dev)
+    dE = torch.empty(N, dtype=torch.float64, device=dev)
+    dM = torch.empty(3 * N, dtype=torch.float64, device=dev)
+    rt.rt_sources(ctx.ctx, dE, dM, Tn)
+    torch.cuda.synchronize()
+    ctx.close()
+    wwl = dict(wl, shape=(side, side, side), hi=(side / 512.0, side / 512.0, side / 512.0))
+    p = oracle_problem(wwl, nn, w)
+    assert abs(oracle.cfl_dt(p, wl["cfl"]) - dt) <= 1e-15 * dt
+    ctr = rad + side * (rad + side * rad)
+    for (x, y, z), h in zip(picks, host):
+        out = oracle.step(p, dt, h["I"], h["T"], h["rho"], h["v"], h["sa"], h["ss"])
+        assert out["failures"] == 0
+        c = x + nx * (y + ny * z)
+        gI = I1.view(M, N)[:, c].cpu().numpy()
+        assert rel_err(gI, out["I"][:, ctr]) <= 1e-4, (x, y, z)
+        assert abs(E[c].item() - out["E"][ctr]) <= TOL * abs(out["E"][ctr]), (x, y, z)
+        gF = np.array([Fm[d * N + c].item() for d in range(3)])
+        assert np.linalg.norm(gF - out["F"][:, ctr]) <= TOL * max(np.linalg.norm(out["F"][:, ctr]),
+                                                                 1e-3 * out["E"][ctr]), (x, y, z)
+        assert abs(Tn[c].item() - out["T"][ctr]) <= TOL * out["T"][ctr], (x, y, z)
