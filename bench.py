@@ -154,7 +154,7 @@ def _angles(name):
 def _context(wl, n, w, stream=None, precision=None):
     import paper_1403_6126_gb300 as rt
     from paper_1403_6126_gb300 import workloads as wlmod
-    prec = {"fp64": rt.RT_FP64, "fp32": rt.RT_FP32}[precision or wl["precision"]]
+    prec = {"fp64": rt.RT_FP64, "fp32": rt.RT_FP32, "bf16": rt.RT_BF16}[precision or wl["precision"]]
     ctx = rt.Context(wl["shape"], n, w, wl["C"], wl["P"], dim=wl["dim"], lo=wl["lo"], hi=wl["hi"], bc=wl["bc"],
                      precision=prec, cfl=wl["cfl"], gamma=wl["gamma"], r_ideal=wl["R"], hold_T=wl["hold_T"],
                      estimate_v=wl["estimate_v"], stream=stream)

@@ -67,7 +67,13 @@ enum { RT_BC_PERIODIC = 0, RT_BC_VACUUM = 1, RT_BC_COPY = 2, RT_BC_INFLOW = 3 };
 /* Storage precision of the intensity.  RT_FP64: everything in double.
  * RT_FP32: intensities, transport and angle sums in float (compensated
  * sums), the T^4 solve finished in double, T and the gas energy source in
- * double.  RT_BF16 is reserved and rejected with RT_E_INVALID. */
+ * double.  RT_BF16: the RT_FP32 arithmetic with each intensity stored in
+ * 16 bits as its deviation from the cell's mean intensity, delta_m =
+ * I_m / J - 1 with J = E_r / (4 pi) (bf16 keeps 8 significant bits, so
+ * storing I_m costs a relative error up to 2^-8 |delta_m|); an extra float
+ * M x N scratch holds the implicit right-hand sides; one tile shape per
+ * dimension; not for batches or the server.  An experiment: the paper
+ * stores double intensities. */
 enum { RT_FP64 = 0, RT_FP32 = 1, RT_BF16 = 2 };
 
 /* Angle-set generators for rt_angle_set. */

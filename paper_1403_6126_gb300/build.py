@@ -21,7 +21,7 @@ NVCC = os.environ.get("NVCC", "nvcc")
 # units are compiled without implicit contraction so that the per-cell code
 # rounds the same way wherever it is inlined: the single-problem, batch and
 # allocation-free kernels then give bitwise equal results.
-NO_CONTRACT = {"rt_step_f3.cu", "rt_step_f12.cu", "rt_batch_k512.cu", "rt_batch_k256.cu", "rt_batch_k128.cu",
+NO_CONTRACT = {"rt_step_f3.cu", "rt_step_f12.cu", "rt_step_b16.cu", "rt_batch_k512.cu", "rt_batch_k256.cu", "rt_batch_k128.cu",
                "rt_noalloc.cu"}
 
 

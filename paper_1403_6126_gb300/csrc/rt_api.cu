@@ -45,7 +45,7 @@ namespace {
 void free_all(rt_ctx *c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   void *ptrs[] = {c->I[0], c->I[1], c->mom[0], c->mom[1], c->rho, c->sa, c->ss, c->v,
-                  c->T, c->dEgas, c->dMom, c->ang, c->inflow, c->flags, c->stage};
+                  c->T, c->dEgas, c->dMom, c->ang, c->inflow, c->flags, c->stage, c->qscr};
   for (void *p : ptrs)
     if (p) cudaFree(p);
 }
@@ -77,6 +77,16 @@ rtg::StepArgs<Real> rtg::make_args(rt_ctx *c, double dt) {
   a.inflow = (const Real *)c->inflow;
   a.I_in = (const Real *)c->I[c->cur];
   a.I_out = (Real *)c->I[1 - c->cur];
+  a.I16_in = nullptr;
+  a.I16_out = nullptr;
+  a.Q = nullptr;
+  if (c->bf16) {
+    a.I_in = nullptr;
+    a.I_out = nullptr;
+    a.I16_in = (const unsigned short *)c->I[c->cur];
+    a.I16_out = (unsigned short *)c->I[1 - c->cur];
+    a.Q = c->qscr;
+  }
   a.rho = (const Real *)c->rho;
   a.sa = (const Real *)c->sa;
   a.ss = (const Real *)c->ss;
@@ -128,10 +138,13 @@ rt_status convert_out(rt_ctx *c, const void *src, double *dst, long long n) {
   return e == cudaSuccess ? RT_OK : cuda_fail(e, "convert");
 }
 
+// Moments of the intensity just set (for bf16 storage: of the float field in
+// the Q scratch, before encoding).
 rt_status recompute_moments(rt_ctx *c) {
-  cudaError_t e = c->fp64 ? rtg::launch_moments<double>((const double *)c->I[c->cur], (const double *)c->ang, c->M,
+  const void *I = c->bf16 ? (const void *)c->qscr : c->I[c->cur];
+  cudaError_t e = c->fp64 ? rtg::launch_moments<double>((const double *)I, (const double *)c->ang, c->M,
                                                         c->N, (double *)c->mom[c->cur], c->stream)
-                          : rtg::launch_moments<float>((const float *)c->I[c->cur], (const float *)c->ang, c->M,
+                          : rtg::launch_moments<float>((const float *)I, (const float *)c->ang, c->M,
                                                        c->N, (float *)c->mom[c->cur], c->stream);
   return e == cudaSuccess ? RT_OK : cuda_fail(e, "moments");
 }
@@ -215,8 +228,8 @@ rt_status rt_create(const rt_grid *g, const rt_angles *ang, double Crat, double 
   rt_options o;
   rt_options_default(&o);
   if (opts) o = *opts;
-  if (o.precision != RT_FP64 && o.precision != RT_FP32)
-    return fail(RT_E_INVALID, "rt_create: precision must be RT_FP64 or RT_FP32");
+  if (o.precision != RT_FP64 && o.precision != RT_FP32 && o.precision != RT_BF16)
+    return fail(RT_E_INVALID, "rt_create: precision must be RT_FP64, RT_FP32 or RT_BF16");
   if (!(o.cfl > 0) || !(o.gamma > 1.0) || !(o.r_ideal > 0))
     return fail(RT_E_INVALID, "rt_create: need cfl > 0, gamma > 1, r_ideal > 0");
 
@@ -236,7 +249,9 @@ rt_status rt_create(const rt_grid *g, const rt_angles *ang, double Crat, double 
   c->opt = o;
   c->stream = (cudaStream_t)o.stream;
   c->fp64 = o.precision == RT_FP64;
+  c->bf16 = o.precision == RT_BF16;
   c->rs = c->fp64 ? 8 : 4;
+  c->rsI = c->bf16 ? 2 : c->rs;
   c->host_n.assign(ang->n, ang->n + 3 * M);
   c->host_w.assign(ang->w, ang->w + M);
   c->host_inflow.assign(6 * (size_t)M, 0.0);
@@ -253,14 +268,16 @@ rt_status rt_create(const rt_grid *g, const rt_angles *ang, double Crat, double 
     void **p;
     size_t bytes;
   } allocs[] = {
-      {&c->I[0], rs * Mz * Nz},  {&c->I[1], rs * Mz * Nz},         {&c->mom[0], rs * 10 * Nz},
+      {&c->I[0], c->rsI * Mz * Nz},  {&c->I[1], c->rsI * Mz * Nz},  {&c->mom[0], rs * 10 * Nz},
       {&c->mom[1], rs * 10 * Nz}, {&c->rho, rs * Nz},               {&c->sa, rs * Nz},
       {&c->ss, rs * Nz},         {&c->v, rs * 3 * Nz},             {(void **)&c->T, 8 * Nz},
       {(void **)&c->dEgas, 8 * Nz}, {&c->dMom, rs * 3 * Nz},       {&c->ang, rs * 4 * Mz},
       {&c->inflow, rs * 6 * Mz}, {(void **)&c->flags, 2 * sizeof(int)},
       {(void **)&c->stage, sizeof(double) * (size_t)c->stage_len},
+      {(void **)&c->qscr, c->bf16 ? sizeof(float) * Mz * Nz : 0},
   };
   for (auto &a : allocs) {
+    if (a.bytes == 0) continue;
     if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
       cudaGetLastError();
       free_all(c);
@@ -329,10 +346,14 @@ rt_status rt_set_material(rt_ctx *c, const double *rho, const double *T, const d
 rt_status rt_set_intensity(rt_ctx *c, const double *I) {
   if (!c) return fail(RT_E_INVALID, "rt_set_intensity: NULL context");
   const long long N = c->N;
+  // bf16 storage: the float field goes to the Q scratch first; its moments
+  // set J for the encoding below
+  void *dst = c->bf16 ? (void *)c->qscr : c->I[c->cur];
+  const size_t rsd = c->bf16 ? sizeof(float) : c->rs;
   if (!I) {
     if (!c->material_set) return fail(RT_E_STATE, "rt_set_intensity(NULL) needs rt_set_material first");
-    cudaError_t e = c->fp64 ? rtg::launch_isotropic<double>(c->T, (double *)c->I[c->cur], c->M, N, c->stream)
-                            : rtg::launch_isotropic<float>(c->T, (float *)c->I[c->cur], c->M, N, c->stream);
+    cudaError_t e = c->fp64 ? rtg::launch_isotropic<double>(c->T, (double *)dst, c->M, N, c->stream)
+                            : rtg::launch_isotropic<float>(c->T, (float *)dst, c->M, N, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "isotropic");
   } else {
     // check everything first (finite, >= 0), then convert chunk by chunk
@@ -352,12 +373,15 @@ rt_status rt_set_intensity(rt_ctx *c, const double *I) {
       long long n = std::min(chunk, (long long)c->M * N - off);
       rt_status st = fetch(c, I + off, c->stage, n);
       if (st != RT_OK) return st;
-      st = convert_in(c, c->stage, (char *)c->I[c->cur] + off * c->rs, n);
+      st = convert_in(c, c->stage, (char *)dst + off * rsd, n);
       if (st != RT_OK) return st;
     }
   }
   rt_status st = recompute_moments(c);
   if (st != RT_OK) return st;
+  if (c->bf16)
+    RT_CUDA(rtg::launch_encode_b16(c->qscr, (const float *)c->mom[c->cur], (unsigned short *)c->I[c->cur], c->M, N,
+                                   c->stream));
   c->intensity_set = true;
   return RT_OK;
 }
@@ -383,6 +407,10 @@ rt_status rt_set_tile(rt_ctx *c, int tx, int ty, int tz) {
     if (!ok) return fail(RT_E_INVALID, "rt_set_tile: no default tile fits");
   } else {
     bool ok = c->fp64 ? rtg::tile_ok<double>(c->dim, c->M, true, t) : rtg::tile_ok<float>(c->dim, c->M, true, t);
+    if (ok && c->bf16) {
+      rtg::TileShape d;
+      ok = rtg::choose_tile<float>(c->dim, c->M, true, &d) && d.tx == t.tx && d.ty == t.ty && d.tz == t.tz;
+    }
     if (!ok) return fail(RT_E_INVALID, "rt_set_tile: shape exceeds the thread, shared-memory or staging limits");
   }
   c->tile = t;
@@ -401,8 +429,9 @@ rt_status rt_autotune(rt_ctx *c, int trial_steps, rt_tile_time *times, int cap, 
   if (c->batch) return fail(RT_E_STATE, "rt_autotune: the context belongs to a batch; use rt_batch_autotune");
   const bool vel = rtg::velocity_on(c);
   rtg::TileShape cand[16];
-  const int nc = c->fp64 ? rtg::tile_candidates<double>(c->dim, c->M, true, cand)
-                         : rtg::tile_candidates<float>(c->dim, c->M, true, cand);
+  int nc = c->fp64 ? rtg::tile_candidates<double>(c->dim, c->M, true, cand)
+                   : rtg::tile_candidates<float>(c->dim, c->M, true, cand);
+  if (c->bf16) nc = rtg::choose_tile<float>(c->dim, c->M, true, &cand[0]) ? 1 : 0;   // one compiled tile
   if (nc == 0) return fail(RT_E_INVALID, "rt_autotune: no compiled tile fits");
   // The trial steps read I[cur] and write only I[1 - cur], mom[1 - cur]
   // (scratch until the next real step), T in place and the step sources:
@@ -479,7 +508,7 @@ int state_parts(rt_ctx *c, void **ptr, size_t *bytes) {
   const size_t N = (size_t)c->N, M = (size_t)c->M, rs = c->rs;
   int k = 0;
   auto add = [&](void *p, size_t b) { ptr[k] = p; bytes[k] = b; ++k; };
-  add(c->I[c->cur], rs * M * N);
+  add(c->I[c->cur], c->rsI * M * N);
   add(c->mom[c->cur], rs * 10 * N);
   add(c->T, 8 * N);
   add(c->rho, rs * N);
@@ -513,7 +542,7 @@ rt_status rt_save_state(rt_ctx *c, void *buf, size_t bytes) {
   h.dim = c->dim;
   for (int d = 0; d < 3; ++d) h.n[d] = c->n[d];
   h.M = c->M;
-  h.rs = (int)c->rs;
+  h.rs = (int)c->rsI;   // bytes per stored intensity: tells the three precisions apart
   h.has_v = c->has_v;
   h.intensity_set = c->intensity_set;
   h.N = c->N;
@@ -542,7 +571,7 @@ rt_status rt_load_state(rt_ctx *c, const void *buf, size_t bytes) {
   StateHeader h;
   std::memcpy(&h, buf, sizeof h);
   bool same = std::memcmp(h.magic, kStateMagic, 8) == 0 && h.dim == c->dim && h.M == c->M &&
-              h.rs == (int)c->rs && h.N == c->N && h.C == c->C && h.P == c->P;
+              h.rs == (int)c->rsI && h.N == c->N && h.C == c->C && h.P == c->P;
   for (int d = 0; d < 3; ++d) same = same && h.n[d] == c->n[d];
   if (!same) return fail(RT_E_INVALID, "rt_load_state: the state was saved from a different grid, angle set, precision or Crat/Prat");
   if (bytes < rt_state_bytes(c)) return fail(RT_E_INVALID, "rt_load_state: buffer shorter than the saved state");
@@ -690,7 +719,14 @@ rt_status rt_get_intensity(rt_ctx *c, double *I) {
   long long total = (long long)c->M * c->N, chunk = c->stage_len;
   for (long long off = 0; off < total; off += chunk) {
     long long n = std::min(chunk, total - off);
-    rt_status st = convert_out(c, (const char *)c->I[c->cur] + off * c->rs, c->stage, n);
+    rt_status st = RT_OK;
+    if (c->bf16) {
+      cudaError_t e = rtg::launch_decode_b16((const unsigned short *)c->I[c->cur], (const float *)c->mom[c->cur],
+                                             c->stage, off, n, c->N, c->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "decode");
+    } else {
+      st = convert_out(c, (const char *)c->I[c->cur] + off * c->rs, c->stage, n);
+    }
     if (st != RT_OK) return st;
     if ((st = deliver(c, c->stage, I + off, n)) != RT_OK) return st;
   }

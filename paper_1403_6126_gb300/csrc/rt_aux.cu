@@ -1,6 +1,7 @@
 // Elementwise device helpers of the runtime: precision conversion, the
 // isotropic equilibrium intensity, the sec. 3 quadrature of a given field,
 // and input scans.  All grid-stride, sized as a multiple of the SM count.
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include "rt_internal.h"
@@ -43,6 +44,31 @@ __global__ void isotropic_kernel(const double *__restrict__ T, Real *__restrict_
     double t = T[c];
     Real b = (Real)(t * t * t * t / (4.0 * kPi));
     for (int m = 0; m < M; ++m) I[(long long)m * N + c] = b;
+  }
+}
+
+// bf16 storage: delta = I / J - 1 with J = E / (4 pi) of the cell (the same
+// arithmetic as the step kernel's b16_* helpers in rt_step_pair.cuh).
+constexpr float kInv4PiF = float(1.0 / (4.0 * 3.14159265358979323846));
+
+__global__ void encode_b16_kernel(const float *__restrict__ I, const float *__restrict__ E,
+                                  unsigned short *__restrict__ out, int M, long long N) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+    const float J = E[c] * kInv4PiF;
+    const float rJ = J > 1e-30f ? 1.0f / J : 0.0f;
+    for (int m = 0; m < M; ++m) {
+      const long long i = (long long)m * N + c;
+      out[i] = __bfloat16_as_ushort(__float2bfloat16_rn(fmaf(I[i], rJ, -1.0f)));
+    }
+  }
+}
+
+__global__ void decode_b16_kernel(const unsigned short *__restrict__ in, const float *__restrict__ E,
+                                  double *__restrict__ out, long long off, long long n, long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long g = off + i;
+    const float J = E[g % N] * kInv4PiF;
+    out[i] = (double)fmaf(J, __bfloat162float(__ushort_as_bfloat16(in[g])), J);
   }
 }
 
@@ -106,6 +132,17 @@ cudaError_t launch_moments(const Real *I, const Real *ang, int M, long long N, R
 cudaError_t launch_check(const double *x, long long n, double lo, int strict, int nzbit, int *flag, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   check_kernel<<<grid_for(n, 256), 256, 0, s>>>(x, n, lo, strict, nzbit, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_encode_b16(const float *I, const float *E, unsigned short *out, int M, long long N, cudaStream_t s) {
+  encode_b16_kernel<<<grid_for(N, 256), 256, 0, s>>>(I, E, out, M, N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decode_b16(const unsigned short *in, const float *E, double *out, long long off, long long n,
+                              long long N, cudaStream_t s) {
+  decode_b16_kernel<<<grid_for(n, 256), 256, 0, s>>>(in, E, out, off, n, N);
   return cudaGetLastError();
 }
 

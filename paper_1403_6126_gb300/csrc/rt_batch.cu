@@ -171,7 +171,7 @@ rt_status rt_batch_create(void *stream, rt_batch **out) {
 
 rt_status rt_batch_add(rt_batch *b, rt_ctx *c) {
   if (!b || !c) return rtg::set_error(RT_E_INVALID, "rt_batch_add: NULL argument");
-  if (c->fp64) return rtg::set_error(RT_E_INVALID, "rt_batch_add: batches run float intensities (RT_FP32)");
+  if (c->fp64 || c->bf16) return rtg::set_error(RT_E_INVALID, "rt_batch_add: batches run float intensities (RT_FP32)");
   if (c->stream != b->stream) return rtg::set_error(RT_E_INVALID, "rt_batch_add: context and batch streams differ");
   if (!c->material_set) return rtg::set_error(RT_E_STATE, "rt_batch_add: call rt_set_material first");
   if (std::find(b->ctxs.begin(), b->ctxs.end(), c) != b->ctxs.end())

@@ -18,7 +18,10 @@ struct rt_ctx {
   rt_options opt{};
   cudaStream_t stream = nullptr;
   bool fp64 = false;
-  size_t rs = 4;  // bytes per stored real
+  bool bf16 = false;  // intensities stored as bf16 deviations (RT_BF16)
+  size_t rs = 4;      // bytes per stored real (cell data; intensities too unless bf16)
+  size_t rsI = 4;     // bytes per stored intensity
+  float *qscr = nullptr;  // bf16 storage: float [M][N] scratch for Q_m
   bool has_v = false, material_set = false, intensity_set = false;
   rtg::TileShape tile{0, 0, 0};
   // device state (Real = double or float)

@@ -38,6 +38,13 @@ struct StepArgs {
   double *dEgas;      // [N]
   Real *dMom;         // [3][N]
   int *status;        // [0]: cells whose T Newton failed
+  // bf16 storage (RT_BF16, float kernels only): the stored value of angle m
+  // in cell c is delta = I / J - 1 with J = E / (4 pi) of the cell's stored
+  // moments; I_in / I_out are unused then and Q is a float [M][N] scratch
+  // for the right-hand sides Q_m.  Null otherwise.
+  const unsigned short *I16_in;
+  unsigned short *I16_out;
+  float *Q;
 };
 
 struct TileShape {
@@ -64,6 +71,10 @@ bool tile_ok(int dim, int M, bool has_v, TileShape t);
 template <typename Real>
 int tile_candidates(int dim, int M, bool has_v, TileShape *out);
 
+// The bf16-storage step (RT_BF16): one compiled tile per dimension, the
+// default shape of the float kernel.
+cudaError_t launch_b16(const StepArgs<float> &a, int dim, bool vel, TileShape t, cudaStream_t s);
+
 // Elementwise helpers (all stream-ordered).
 template <typename Real>
 cudaError_t launch_convert_in(const double *src, Real *dst, long long n, cudaStream_t s);
@@ -73,6 +84,13 @@ template <typename Real>
 cudaError_t launch_isotropic(const double *T, Real *I, int M, long long N, cudaStream_t s);
 template <typename Real>
 cudaError_t launch_moments(const Real *I, const Real *ang, int M, long long N, Real *mom, cudaStream_t s);
+
+// bf16 storage: encode a float intensity array [M][N] as deviations from
+// the mean intensity of each cell (E [N] its energy density), and decode
+// elements [off, off + n) of a stored array to doubles.
+cudaError_t launch_encode_b16(const float *I, const float *E, unsigned short *out, int M, long long N, cudaStream_t s);
+cudaError_t launch_decode_b16(const unsigned short *in, const float *E, double *out, long long off, long long n,
+                              long long N, cudaStream_t s);
 
 // Scans n doubles: ORs bit 0 into *flag for a non-finite value or one below
 // `lo` (or equal to it when strict), and ORs `nzbit` for a nonzero value.

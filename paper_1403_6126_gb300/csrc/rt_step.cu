@@ -70,6 +70,7 @@ bool choose_tile(int dim, int M, bool has_v, TileShape *out) {
 
 template <>
 cudaError_t launch_step<float>(const StepArgs<float> &a, int dim, bool has_v, TileShape t, cudaStream_t s) {
+  if (a.I16_in) return launch_b16(a, dim, has_v, t, s);
   return dim == 3 ? launch_f3(a, has_v, t, s) : launch_f12(a, dim, has_v, t, s);
 }
 

@@ -24,11 +24,26 @@
 //    keeps them out of the registers the transport phases need.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "rt_step_kernel.cuh"
 
 namespace rtg {
 
 namespace stepk {
+
+// bf16 storage as deviations from the cell's mean intensity J = E / (4 pi):
+// delta = I / J - 1, I = J (1 + delta).  Cells with J ~ 0 store delta = -1,
+// which decodes to 0.
+constexpr float kInv4Pi = float(1.0 / (4.0 * 3.14159265358979323846));
+__host__ __device__ __forceinline__ float b16_mean(float E) { return E * kInv4Pi; }
+__device__ __forceinline__ float b16_inv(float J) { return J > 1e-30f ? 1.0f / J : 0.0f; }
+__device__ __forceinline__ float b16_decode(unsigned short d, float J) {
+  return fmaf(J, __bfloat162float(__ushort_as_bfloat16(d)), J);
+}
+__device__ __forceinline__ unsigned short b16_encode(float I, float rJ) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(fmaf(I, rJ, -1.0f)));
+}
 
 using f2 = float2;
 
@@ -101,7 +116,8 @@ __host__ __device__ inline size_t smem_bytes2(int dim, int M, bool has_v, int tx
 }
 
 // One tile of one problem, float intensities: arguments as process_tile.
-template <int DIM, bool VEL, int TX, int TY, int TZ>
+// B16: intensities stored as bf16 deviations (see b16_decode), Q_m in a.Q.
+template <int DIM, bool VEL, int TX, int TY, int TZ, bool B16 = false>
 __device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid, int tbx, int tby, int tbz,
                                               unsigned char *smem_raw) {
   using G = GeoT<DIM, TX, TY, TZ>;
@@ -169,12 +185,13 @@ __device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid,
 
   // ---- staging slots (see process_tile) ---------------------------------------
   int sl_box[kSlots], sl_code[kSlots], sl_g[kSlots];
-  float sl_w[kSlots][3];
+  float sl_w[kSlots][3], sl_J[kSlots];
 #pragma unroll
   for (int s = 0; s < kSlots; ++s) {
     const int k = tid + s * nthr;
     sl_box[s] = -1; sl_code[s] = 0; sl_g[s] = 0;
     sl_w[s][0] = sl_w[s][1] = sl_w[s][2] = 0.0f;
+    sl_J[s] = 0.0f;
     if (k >= G::ncross) continue;
     int b[3] = {0, 0, 0};
     if (k < G::ncell) {
@@ -217,7 +234,17 @@ __device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid,
       sl_w[s][1] = w3 * a.v[N + cc];
       sl_w[s][2] = w3 * a.v[2 * N + cc];
     }
+    if (B16) sl_J[s] = b16_mean(a.mom_in[sl_g[s]]);
   }
+  // one angle pair of a staged cell from the stored intensities
+  auto load_pair = [&](long long row, int s, bool two) -> f2 {
+    if (B16) {
+      const unsigned short *p = a.I16_in + row + sl_g[s];
+      return make_float2(b16_decode(p[0], sl_J[s]), two ? b16_decode(p[N], sl_J[s]) : 0.0f);
+    }
+    const float *p = a.I_in + row + sl_g[s];
+    return make_float2(p[0], two ? p[N] : 0.0f);
+  };
 
   // ---- slope-extension items (see process_tile) -------------------------------
   int ext_bb[kExt > 0 ? kExt : 1], ext_st[kExt > 0 ? kExt : 1], ext_si[kExt > 0 ? kExt : 1];
@@ -325,9 +352,8 @@ __device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid,
   // prefetch pair 0
   f2 pf[kSlots];
 #pragma unroll
-  for (int s = 0; s < kSlots; ++s)
-    pf[s] = sl_box[s] >= 0 ? make_float2(a.I_in[sl_g[s]], M > 1 ? a.I_in[N + sl_g[s]] : 0.0f) : dup(0.0f);
-  const float *I_next = a.I_in;
+  for (int s = 0; s < kSlots; ++s) pf[s] = sl_box[s] >= 0 ? load_pair(0, s, M > 1) : dup(0.0f);
+  long long row_next = 0;   // offset of the prefetched pair's first row
   __syncthreads();
 
   for (int k = 0; k < K; ++k) {
@@ -360,11 +386,11 @@ __device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid,
       if (s == 0) { I0 = I; q0 = It; p0 = IV; }
     }
     if (k + 1 < K) {
-      I_next += 2 * N;
+      row_next += 2 * N;
       const bool next2 = m + 3 < M;
 #pragma unroll
       for (int s = 0; s < kSlots; ++s)
-        if (sl_box[s] >= 0) pf[s] = make_float2(I_next[sl_g[s]], next2 ? I_next[N + sl_g[s]] : 0.0f);
+        if (sl_box[s] >= 0) pf[s] = load_pair(row_next, s, next2);
     }
     __syncthreads();
 
@@ -426,8 +452,9 @@ __device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid,
     const f2 qa = p_mul(to_scat ? I0 : full, rd);   // r_m / d_m
     const f2 Q = to_scat ? p_add(qa, dF) : qa;
     if (valid) {
-      a.I_out[(long long)m * N + c] = Q.x;
-      if (second) a.I_out[(long long)(m + 1) * N + c] = Q.y;
+      float *qdst = B16 ? a.Q : a.I_out;
+      qdst[(long long)m * N + c] = Q.x;
+      if (second) qdst[(long long)(m + 1) * N + c] = Q.y;
     }
     const f2 wq = p_mul(Wm, qa);
     U0.part = p_add(U0.part, wq);
@@ -554,7 +581,8 @@ __device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid,
   mE.zero();
   for (int i = 0; i < 3; ++i) mF[i].zero();
   for (int i = 0; i < 6; ++i) mP[i].zero();
-  float *out = a.I_out + c;
+  float *out = (B16 ? a.Q : a.I_out) + c;
+  const float rJ = b16_inv(s2);   // s2 = sum W I^{n+1}: the new mean intensity (bf16 storage)
 #pragma unroll 2
   for (int k = 0; k < K; ++k) {
     const f2 *t = s_tab + kTab2 * k;
@@ -572,8 +600,13 @@ __device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid,
     const f2 rs = p_fma(pe, dup(th), p_fma(rd, dup(-kS), Q));        // r'_m
     const f2 cm = p_mul(dup(cq), vn);
     const f2 I1 = p_mul(p_fma(cm, dup(-s2), p_sub(rs, dup(s1))), ra);
-    out[(long long)m * N] = I1.x;
-    if (second) out[(long long)(m + 1) * N] = I1.y;
+    if (B16) {
+      a.I16_out[(long long)m * N + c] = b16_encode(I1.x, rJ);
+      if (second) a.I16_out[(long long)(m + 1) * N + c] = b16_encode(I1.y, rJ);
+    } else {
+      out[(long long)m * N] = I1.x;
+      if (second) out[(long long)(m + 1) * N] = I1.y;
+    }
     const f2 wi = p_mul(Wm, I1);
     mE.part = p_add(mE.part, wi);
     const f2 wx = p_mul(nx, wi), wy = p_mul(ny, wi), wz = p_mul(nz, wi);
@@ -615,16 +648,16 @@ __device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid,
   a.dEgas[c] = kv * (T1 - T0) + (double)dEK;
 }
 
-template <int DIM, bool VEL, int TX, int TY, int TZ>
+template <int DIM, bool VEL, int TX, int TY, int TZ, bool B16 = false>
 __global__ void __launch_bounds__(TX * TY * TZ, 1) step_kernel2(const StepArgs<float> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  process_tile2<DIM, VEL, TX, TY, TZ>(a, threadIdx.x, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+  process_tile2<DIM, VEL, TX, TY, TZ, B16>(a, threadIdx.x, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
 }
 
-template <int DIM, bool VEL, int TX, int TY, int TZ>
+template <int DIM, bool VEL, int TX, int TY, int TZ, bool B16 = false>
 cudaError_t launch_shape2(const StepArgs<float> &a, cudaStream_t s) {
   const size_t sm = smem_bytes2(DIM, a.M, VEL, TX, TY, TZ);
-  auto kern = step_kernel2<DIM, VEL, TX, TY, TZ>;
+  auto kern = step_kernel2<DIM, VEL, TX, TY, TZ, B16>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   dim3 block(TX * TY * TZ);

@@ -97,7 +97,7 @@ def test_create_validates_before_touching_the_device():
     g = _grid()
     g.bc[0][0], g.bc[0][1] = rt.RT_BC_PERIODIC, rt.RT_BC_VACUUM
     _expect(rt.RT_E_INVALID, rt.rt_create, g, _angles(n, w), 10.0, 1.0, o)
-    o.precision = rt.RT_BF16
+    o.precision = 7
     _expect(rt.RT_E_INVALID, rt.rt_create, _grid(), _angles(n, w), 10.0, 1.0, o)
     assert "precision" in rt.rt_last_error()
 
