@@ -311,9 +311,13 @@ def run_gpu(args):
     clocks = sampler.summary()
     ctx.close()
 
-    batched = serving = small = None
+    batched = serving = small = accuracy = bf16 = None
     if world == 1 and not args.no_small:
         small = bench_small(stream)
+    if world == 1 and not args.no_accuracy:
+        accuracy = bench_accuracy(stream)
+    if world == 1 and not args.no_bf16:
+        bf16 = bench_bf16(args, stream)
     if world == 1 and not args.no_batch:
         batched = bench_batched(args, stream)
     if world == 1 and not args.no_serve:
@@ -335,6 +339,7 @@ def run_gpu(args):
                        "l2": "inputs larger than L2: %.2f GB of intensity read per step" % (N * M * rs / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
+            "accuracy_vs_oracle": accuracy, "bf16_storage": bf16,
             "small_configs": small, "batched": batched, "serving": serving,
         }
         print(json.dumps(line))
@@ -478,6 +483,72 @@ def bench_small(stream):
     return out
 
 
+def bench_accuracy(stream, n=32, steps=10):
+    """Error against the FP64 oracle of every GPU precision on a sample of
+    the timed workload: the box3d recipe at n^3 x 80 angles, `steps` steps
+    from identical (float-rounded) inputs.  Norm-relative errors of E_r,
+    |F_r| (against max E_r where the flux is round-off) and T."""
+    import oracle
+    from paper_1403_6126_gb300 import workloads as wlmod
+    wl = wlmod.rounded_to_float32(wlmod.box3d(n=n, steps=steps))
+    nn, w = oracle.angles.by_name(wl["angles"])
+    I0 = wlmod.initial_intensity(wl, len(w)).astype(np.float32).astype(np.float64)
+    dx = tuple((wl["hi"][d] - wl["lo"][d]) / wl["shape"][2 - d] for d in range(3))
+    p = oracle.Problem(wl["shape"], dx, nn, w, C=wl["C"], P=wl["P"], dim=3, bc=wl["bc"], gamma=wl["gamma"],
+                       R=wl["R"], hold_T=wl["hold_T"], estimate_v=wl["estimate_v"])
+    oracle.set_threads(os.cpu_count() or 1)
+    dt = oracle.cfl_dt(p, wl["cfl"])
+    o = oracle.run(p, dt, steps, I0, wl["T"], wl["rho"], wl["v"], wl["sa"], wl["ss"])
+    Fo = np.sqrt((o["F"] ** 2).sum(axis=0))
+    out = {"workload": "box3d recipe at %d^3 x %d angles, %d steps, FP64 oracle on the host" % (n, len(w), steps)}
+    for prec in ("fp64", "fp32", "bf16"):
+        c = _context(wl, nn, w, stream=stream.cuda_stream, precision=prec)
+        c.set_intensity(I0)
+        c.set_material(wl["rho"], wl["T"], wl["v"], wl["sa"], wl["ss"])
+        c.run(dt, steps)
+        c.sync()
+        E, F, _ = c.moments()
+        _, _, T = c.sources()
+        c.close()
+        Fg = np.sqrt((F ** 2).sum(axis=0))
+        out[prec] = {"E_r": float(np.abs(E - o["E"]).max() / np.abs(o["E"]).max()),
+                     "abs_F_r": float(np.abs(Fg - Fo).max() / max(Fo.max(), 1e-3 * np.abs(o["E"]).max())),
+                     "T": float(np.abs(T - o["T"]).max() / np.abs(o["T"]).max())}
+    return out
+
+
+def bench_bf16(args, stream):
+    """The timed workload with bf16 intensity storage (RT_BF16)."""
+    import torch
+    from paper_1403_6126_gb300 import workloads as wlmod
+    wl = wlmod.by_name(args.workload, **({"n": args.n} if args.n else {}))
+    n, w = _angles(wl["angles"])
+    M, N = len(w), int(np.prod(wl["shape"]))
+    c = _context(wl, n, w, stream=stream.cuda_stream, precision="bf16")
+    c.set_intensity(wlmod.initial_intensity(wl, M))
+    c.set_material(wl["rho"], wl["T"], wl["v"], wl["sa"], wl["ss"])
+    dt = c.cfl_dt()
+    for _ in range(3):
+        c.step(dt)
+    c.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        c.step(dt)
+    e1.record(stream)
+    c.sync()
+    ms = e0.elapsed_time(e1) / args.steps
+    c.close()
+    peak, _ = _peaks()
+    velocity = bool(np.any(wl["v"] != 0)) or wl["estimate_v"]
+    b = (algorithmic_bytes_per_cell(M, 4, velocity, not wl["hold_T"]) - 2 * M * 2) * N   # intensities at 2 bytes
+    return {"workload": "%s: %s cells x %d angles, bf16 intensities (deviation from the cell mean)"
+                        % (wl["name"], "x".join(str(x) for x in wl["shape"][::-1]), M),
+            "ms_per_step": ms, "value": N * M / (ms / 1e3), "unit": "cell-angle updates/s",
+            "algorithmic_gb_s": b / (ms / 1e3) / 1e9, "frac_of_measured_hbm": b / (ms / 1e3) / 1e9 / peak,
+            "algorithmic_bytes_per_step": b}
+
+
 def _submit_args(wl):
     import ctypes
     import paper_1403_6126_gb300 as rt
@@ -577,6 +648,8 @@ def main():
     ap.add_argument("--cpu-sample-n", type=int, default=32)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-bf16", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-n", type=int, default=512)

@@ -185,13 +185,13 @@ __device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid,
 
   // ---- staging slots (see process_tile) ---------------------------------------
   int sl_box[kSlots], sl_code[kSlots], sl_g[kSlots];
-  float sl_w[kSlots][3], sl_J[kSlots];
+  float sl_w[kSlots][3], sl_J[B16 ? kSlots : 1];   // sl_J: mean intensity of the slot's cell (bf16 storage)
 #pragma unroll
   for (int s = 0; s < kSlots; ++s) {
     const int k = tid + s * nthr;
     sl_box[s] = -1; sl_code[s] = 0; sl_g[s] = 0;
     sl_w[s][0] = sl_w[s][1] = sl_w[s][2] = 0.0f;
-    sl_J[s] = 0.0f;
+    if (B16) sl_J[B16 ? s : 0] = 0.0f;
     if (k >= G::ncross) continue;
     int b[3] = {0, 0, 0};
     if (k < G::ncell) {
@@ -234,17 +234,8 @@ __device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid,
       sl_w[s][1] = w3 * a.v[N + cc];
       sl_w[s][2] = w3 * a.v[2 * N + cc];
     }
-    if (B16) sl_J[s] = b16_mean(a.mom_in[sl_g[s]]);
+    if (B16) sl_J[B16 ? s : 0] = b16_mean(a.mom_in[sl_g[s]]);
   }
-  // one angle pair of a staged cell from the stored intensities
-  auto load_pair = [&](long long row, int s, bool two) -> f2 {
-    if (B16) {
-      const unsigned short *p = a.I16_in + row + sl_g[s];
-      return make_float2(b16_decode(p[0], sl_J[s]), two ? b16_decode(p[N], sl_J[s]) : 0.0f);
-    }
-    const float *p = a.I_in + row + sl_g[s];
-    return make_float2(p[0], two ? p[N] : 0.0f);
-  };
 
   // ---- slope-extension items (see process_tile) -------------------------------
   int ext_bb[kExt > 0 ? kExt : 1], ext_st[kExt > 0 ? kExt : 1], ext_si[kExt > 0 ? kExt : 1];
@@ -350,10 +341,19 @@ __device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid,
   f2 U1 = dup(0.0f), U2 = dup(0.0f), BQ = dup(0.0f), pre0 = dup(0.0f), pre1 = dup(0.0f), pre2 = dup(0.0f);
 
   // prefetch pair 0
+  // stored intensities of the prefetched pair: float, or bf16 deviations
+  const float *I_next = a.I_in;
+  const unsigned short *I16_next = a.I16_in;
+  auto stored = [&](int s, bool two) -> f2 {
+    if (B16) {
+      const float J = sl_J[B16 ? s : 0];
+      return make_float2(b16_decode(I16_next[sl_g[s]], J), two ? b16_decode(I16_next[N + sl_g[s]], J) : 0.0f);
+    }
+    return make_float2(I_next[sl_g[s]], two ? I_next[N + sl_g[s]] : 0.0f);
+  };
   f2 pf[kSlots];
 #pragma unroll
-  for (int s = 0; s < kSlots; ++s) pf[s] = sl_box[s] >= 0 ? load_pair(0, s, M > 1) : dup(0.0f);
-  long long row_next = 0;   // offset of the prefetched pair's first row
+  for (int s = 0; s < kSlots; ++s) pf[s] = sl_box[s] >= 0 ? stored(s, M > 1) : dup(0.0f);
   __syncthreads();
 
   for (int k = 0; k < K; ++k) {
@@ -386,11 +386,12 @@ __device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid,
       if (s == 0) { I0 = I; q0 = It; p0 = IV; }
     }
     if (k + 1 < K) {
-      row_next += 2 * N;
+      if (B16) I16_next += 2 * N;
+      else I_next += 2 * N;
       const bool next2 = m + 3 < M;
 #pragma unroll
       for (int s = 0; s < kSlots; ++s)
-        if (sl_box[s] >= 0) pf[s] = load_pair(row_next, s, next2);
+        if (sl_box[s] >= 0) pf[s] = stored(s, next2);
     }
     __syncthreads();
 
