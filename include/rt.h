@@ -354,6 +354,17 @@ rt_status rt_step_noalloc(const rt_grid *grid, const rt_angles *angles, double C
 /* Message of the last failed call on this thread ("" if none). */
 const char *rt_last_error(void);
 
+/* ---- host-side fault injection (testing hook) -----------------------------
+ * Makes the library's device allocation that follows `after` further
+ * successful ones fail once, as if the device were out of memory: the
+ * calling entry point then takes its error path (RT_E_NOMEM from rt_create,
+ * an error status from rt_batch_step or a failed server request) and frees
+ * what it had allocated.  kind RT_FAULT_NONE clears a pending fault.
+ * RT_E_INVALID for an unknown kind or after < 0.  No GPU state is touched:
+ * the failing allocation is never requested. */
+enum { RT_FAULT_NONE = 0, RT_FAULT_ALLOC = 1 };
+rt_status rt_fault_inject(int kind, int after);
+
 #ifdef __cplusplus
 }
 #endif

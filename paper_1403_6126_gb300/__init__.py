@@ -24,6 +24,7 @@ RT_E_INVALID, RT_E_NOMEM, RT_E_BUDGET, RT_E_CUDA, RT_E_NONFINITE, RT_E_TIMEOUT, 
 RT_BC_PERIODIC, RT_BC_VACUUM, RT_BC_COPY, RT_BC_INFLOW = 0, 1, 2, 3
 RT_FP64, RT_FP32, RT_BF16 = 0, 1, 2
 RT_ANGLES_LEVEL_SYMMETRIC, RT_ANGLES_GAUSS_LEGENDRE, RT_ANGLES_PAPER_S4 = 0, 1, 2
+RT_FAULT_NONE, RT_FAULT_ALLOC = 0, 1
 
 _STATUS_NAMES = {0: "RT_OK", 1: "RT_PENDING", -1: "RT_E_INVALID", -2: "RT_E_NOMEM", -3: "RT_E_BUDGET",
                  -4: "RT_E_CUDA", -5: "RT_E_NONFINITE", -6: "RT_E_TIMEOUT", -7: "RT_E_STATE"}
@@ -112,6 +113,7 @@ def lib():
             "rt_step_noalloc": (I, [ctypes.POINTER(rt_grid), ctypes.POINTER(rt_angles), D, D, ctypes.POINTER(rt_options),
                                     D, ctypes.POINTER(rt_noalloc_fields), ctypes.POINTER(I)]),
             "rt_last_error": (ctypes.c_char_p, []),
+            "rt_fault_inject": (I, [I, I]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -327,6 +329,10 @@ def rt_step_noalloc(grid, angles, Crat, Prat, opts, dt, fields, want_failures=Tr
     _check(lib().rt_step_noalloc(ctypes.byref(grid), ctypes.byref(angles), Crat, Prat, ctypes.byref(opts), dt,
                                  ctypes.byref(fields), ctypes.byref(nf) if want_failures else None), "rt_step_noalloc")
     return nf.value
+
+
+def rt_fault_inject(kind, after=0):
+    _check(lib().rt_fault_inject(kind, after), "rt_fault_inject")
 
 
 def rt_last_error():

@@ -1,6 +1,7 @@
 // C ABI runtime: contexts, device state, validation, launches and graphs.
 // The declarations and their documentation are in include/rt.h.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -24,6 +25,24 @@ rt_status fail(rt_status s, const std::string &msg) {
 }  // namespace
 
 rt_status rtg::set_error(rt_status s, const std::string &msg) { return fail(s, msg); }
+
+namespace {
+std::atomic<int> g_fail_alloc_after{-1};   // armed by rt_fault_inject
+}
+
+cudaError_t rtg::device_alloc(void **p, size_t bytes) {
+  int k = g_fail_alloc_after.load();
+  while (k >= 0) {
+    if (g_fail_alloc_after.compare_exchange_weak(k, k - 1)) {
+      if (k == 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
 
 namespace {
 
@@ -176,6 +195,16 @@ extern "C" {
 
 const char *rt_last_error(void) { return g_last_error.c_str(); }
 
+rt_status rt_fault_inject(int kind, int after) {
+  if (kind == RT_FAULT_NONE) {
+    g_fail_alloc_after.store(-1);
+    return RT_OK;
+  }
+  if (kind != RT_FAULT_ALLOC || after < 0) return fail(RT_E_INVALID, "rt_fault_inject: unknown kind or after < 0");
+  g_fail_alloc_after.store(after);
+  return RT_OK;
+}
+
 rt_status rt_options_default(rt_options *o) {
   if (!o) return fail(RT_E_INVALID, "rt_options_default: NULL");
   std::memset(o, 0, sizeof(*o));
@@ -192,6 +221,7 @@ rt_status rt_options_default(rt_options *o) {
 
 rt_status rt_create(const rt_grid *g, const rt_angles *ang, double Crat, double Prat, const rt_options *opts,
                     rt_ctx **out) {
+  rtg::Range nvtx_range("rt_create");
   if (!out) return fail(RT_E_INVALID, "rt_create: out is NULL");
   *out = nullptr;
   if (!g || !ang || !ang->n || !ang->w) return fail(RT_E_INVALID, "rt_create: NULL grid or angles");
@@ -278,7 +308,7 @@ rt_status rt_create(const rt_grid *g, const rt_angles *ang, double Crat, double 
   };
   for (auto &a : allocs) {
     if (a.bytes == 0) continue;
-    if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
+    if (rtg::device_alloc(a.p, a.bytes) != cudaSuccess) {
       cudaGetLastError();
       free_all(c);
       delete c;
@@ -310,6 +340,7 @@ rt_status rt_create(const rt_grid *g, const rt_angles *ang, double Crat, double 
 
 rt_status rt_set_material(rt_ctx *c, const double *rho, const double *T, const double *v, const double *sa,
                           const double *ss) {
+  rtg::Range nvtx_range("rt_set_material");
   if (!c || !rho || !T || !v || !sa || !ss) return fail(RT_E_INVALID, "rt_set_material: NULL argument");
   const long long N = c->N;
   if (c->stage_len < 7 * N) return fail(RT_E_STATE, "rt_set_material: staging buffer too small");
@@ -344,6 +375,7 @@ rt_status rt_set_material(rt_ctx *c, const double *rho, const double *T, const d
 }
 
 rt_status rt_set_intensity(rt_ctx *c, const double *I) {
+  rtg::Range nvtx_range("rt_set_intensity");
   if (!c) return fail(RT_E_INVALID, "rt_set_intensity: NULL context");
   const long long N = c->N;
   // bf16 storage: the float field goes to the Q scratch first; its moments
@@ -422,6 +454,7 @@ rt_status rt_set_tile(rt_ctx *c, int tx, int ty, int tz) {
 }
 
 rt_status rt_autotune(rt_ctx *c, int trial_steps, rt_tile_time *times, int cap, int *ntimes) {
+  rtg::Range nvtx_range("rt_autotune");
   if (!c) return fail(RT_E_INVALID, "rt_autotune: NULL context");
   if (trial_steps < 1) return fail(RT_E_INVALID, "rt_autotune: trial_steps < 1");
   if (cap < 0 || (cap > 0 && !times)) return fail(RT_E_INVALID, "rt_autotune: bad times buffer");
@@ -533,6 +566,7 @@ size_t rt_state_bytes(const rt_ctx *c) {
 }
 
 rt_status rt_save_state(rt_ctx *c, void *buf, size_t bytes) {
+  rtg::Range nvtx_range("rt_save_state");
   if (!c || !buf) return fail(RT_E_INVALID, "rt_save_state: NULL argument");
   if (bytes < rt_state_bytes(c)) return fail(RT_E_INVALID, "rt_save_state: buffer smaller than rt_state_bytes");
   if (!c->material_set) return fail(RT_E_STATE, "rt_save_state: call rt_set_material first");
@@ -565,6 +599,7 @@ rt_status rt_save_state(rt_ctx *c, void *buf, size_t bytes) {
 }
 
 rt_status rt_load_state(rt_ctx *c, const void *buf, size_t bytes) {
+  rtg::Range nvtx_range("rt_load_state");
   if (!c || !buf) return fail(RT_E_INVALID, "rt_load_state: NULL argument");
   if (c->batch) return fail(RT_E_STATE, "rt_load_state: the context belongs to a batch");
   if (bytes < sizeof(StateHeader)) return fail(RT_E_INVALID, "rt_load_state: buffer too short");
@@ -615,6 +650,7 @@ double rt_cfl_dt(const rt_ctx *c) {
 }
 
 rt_status rt_step(rt_ctx *c, double dt) {
+  rtg::Range nvtx_range("rt_step");
   if (!c) return fail(RT_E_INVALID, "rt_step: NULL context");
   if (!c->material_set) return fail(RT_E_STATE, "rt_step: call rt_set_material first");
   if (c->batch) return fail(RT_E_STATE, "rt_step: the context belongs to a batch; step it with rt_batch_step");
@@ -624,6 +660,7 @@ rt_status rt_step(rt_ctx *c, double dt) {
 }
 
 rt_status rt_run(rt_ctx *c, double dt, int nsteps) {
+  rtg::Range nvtx_range("rt_run");
   if (!c) return fail(RT_E_INVALID, "rt_run: NULL context");
   if (!c->material_set) return fail(RT_E_STATE, "rt_run: call rt_set_material first");
   if (c->batch) return fail(RT_E_STATE, "rt_run: the context belongs to a batch; step it with rt_batch_step");
@@ -682,6 +719,7 @@ rt_status rt_sync(rt_ctx *c) {
 }
 
 rt_status rt_moments(rt_ctx *c, double *E, double *F, double *P) {
+  rtg::Range nvtx_range("rt_moments");
   if (!c) return fail(RT_E_INVALID, "rt_moments: NULL context");
   if (!c->intensity_set) return fail(RT_E_STATE, "rt_moments: no intensity yet");
   const long long N = c->N;
@@ -695,6 +733,7 @@ rt_status rt_moments(rt_ctx *c, double *E, double *F, double *P) {
 }
 
 rt_status rt_sources(rt_ctx *c, double *dE_gas, double *dMom, double *T_new) {
+  rtg::Range nvtx_range("rt_sources");
   if (!c) return fail(RT_E_INVALID, "rt_sources: NULL context");
   const long long N = c->N;
   rt_status st;
@@ -714,6 +753,7 @@ rt_status rt_sources(rt_ctx *c, double *dE_gas, double *dMom, double *T_new) {
 }
 
 rt_status rt_get_intensity(rt_ctx *c, double *I) {
+  rtg::Range nvtx_range("rt_get_intensity");
   if (!c || !I) return fail(RT_E_INVALID, "rt_get_intensity: NULL argument");
   if (!c->intensity_set) return fail(RT_E_STATE, "rt_get_intensity: no intensity yet");
   long long total = (long long)c->M * c->N, chunk = c->stage_len;

@@ -74,6 +74,7 @@ void drop_graph(rt_batch *b) {
 // Rebuilds the work list and both descriptor arrays (current parity of each
 // problem and the flipped one) after the membership changed.
 rt_status rebuild(rt_batch *b) {
+  rtg::Range nvtx_range("rt_batch rebuild");
   drop_graph(b);
   std::vector<int> order(b->ctxs.size());
   for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
@@ -104,7 +105,8 @@ rt_status rebuild(rt_batch *b) {
   if (items.size() > b->items_cap) {
     if (b->d_items) cudaFree(b->d_items);
     b->d_items = nullptr;
-    RT_BCUDA(cudaMalloc(&b->d_items, sizeof(rtg::WorkItem) * items.size()));
+    b->items_cap = 0;   // consistent if the allocation fails
+    RT_BCUDA(rtg::device_alloc((void **)&b->d_items, sizeof(rtg::WorkItem) * items.size()));
     b->items_cap = items.size();
   }
   if (!items.empty())
@@ -120,10 +122,11 @@ rt_status rebuild(rt_batch *b) {
     }
   }
   if (b->ctxs.size() > b->desc_cap) {
+    b->desc_cap = 0;   // consistent if an allocation fails
     for (int p = 0; p < 2; ++p) {
       if (b->d_desc[p]) cudaFree(b->d_desc[p]);
       b->d_desc[p] = nullptr;
-      RT_BCUDA(cudaMalloc(&b->d_desc[p], sizeof(rtg::StepArgs<float>) * b->ctxs.size()));
+      RT_BCUDA(rtg::device_alloc((void **)&b->d_desc[p], sizeof(rtg::StepArgs<float>) * b->ctxs.size()));
     }
     b->desc_cap = b->ctxs.size();
   }
@@ -160,7 +163,7 @@ rt_status rt_batch_create(void *stream, rt_batch **out) {
   rt_batch *b = new (std::nothrow) rt_batch;
   if (!b) return rtg::set_error(RT_E_NOMEM, "rt_batch_create: host allocation");
   b->stream = (cudaStream_t)stream;
-  if (cudaMalloc(&b->d_counter, sizeof(int)) != cudaSuccess) {
+  if (rtg::device_alloc((void **)&b->d_counter, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     delete b;
     return rtg::set_error(RT_E_NOMEM, "rt_batch_create: device allocation");
@@ -196,6 +199,7 @@ rt_status rt_batch_remove(rt_batch *b, rt_ctx *c) {
 int rt_batch_size(const rt_batch *b) { return b ? (int)b->ctxs.size() : 0; }
 
 rt_status rt_batch_step(rt_batch *b, int nsteps) {
+  rtg::Range nvtx_range("rt_batch_step");
   if (!b) return rtg::set_error(RT_E_INVALID, "rt_batch_step: NULL batch");
   if (nsteps < 0) return rtg::set_error(RT_E_INVALID, "rt_batch_step: nsteps < 0");
   if (nsteps == 0 || b->ctxs.empty()) return RT_OK;
@@ -233,6 +237,7 @@ rt_status rt_batch_step(rt_batch *b, int nsteps) {
 }
 
 rt_status rt_batch_autotune(rt_batch *b, int trial_steps, double *ms, int *chosen) {
+  rtg::Range nvtx_range("rt_batch_autotune");
   if (!b) return rtg::set_error(RT_E_INVALID, "rt_batch_autotune: NULL batch");
   if (trial_steps < 1) return rtg::set_error(RT_E_INVALID, "rt_batch_autotune: trial_steps < 1");
   if (b->ctxs.empty()) {

@@ -43,7 +43,19 @@ struct rt_ctx {
   void *batch = nullptr;  // the rt_batch this context belongs to, if any
 };
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace rtg {
+// Device allocation of the library: cudaMalloc, unless rt_fault_inject has
+// armed a failure for this allocation.
+cudaError_t device_alloc(void **p, size_t bytes);
+// NVTX range over an entry point (free when no profiler is attached).
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range &) = delete;
+  Range &operator=(const Range &) = delete;
+};
 // Step arguments of context c for its current buffer parity.
 template <typename Real>
 StepArgs<Real> make_args(rt_ctx *c, double dt);

@@ -147,6 +147,7 @@ void loop(rt_server *s) {
       live = s->live;
     }
     if (live.empty()) continue;
+    rtg::Range nvtx_range("rt_server step");
     rt_status st = rt_batch_step(s->batch, 1);
     cudaError_t e = cudaStreamSynchronize(s->stream);
     s->steps += 1;
@@ -195,6 +196,7 @@ rt_status rt_server_create(size_t hbm_budget_bytes, const rt_options *opts, rt_s
 rt_status rt_submit(rt_server *s, const rt_grid *g, const rt_angles *a, double Crat, double Prat, const double *rho,
                     const double *T, const double *v, const double *sa, const double *ss, int nsteps,
                     rt_ticket *out) {
+  rtg::Range nvtx_range("rt_submit");
   if (!s || !g || !a || !a->n || !a->w || !rho || !T || !v || !sa || !ss || !out)
     return fail(RT_E_INVALID, "rt_submit: NULL argument");
   if (nsteps < 1) return fail(RT_E_INVALID, "rt_submit: nsteps < 1");

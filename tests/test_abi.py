@@ -109,3 +109,13 @@ def test_null_context_calls_are_rejected():
             fn()
         assert e.value.status == rt.RT_E_INVALID
     rt.rt_destroy(None)
+
+
+def test_fault_inject_arguments():
+    with pytest.raises(rt.RTError) as e:
+        rt.rt_fault_inject(99, 0)
+    assert e.value.status == rt.RT_E_INVALID
+    with pytest.raises(rt.RTError) as e:
+        rt.rt_fault_inject(rt.RT_FAULT_ALLOC, -1)
+    assert e.value.status == rt.RT_E_INVALID
+    rt.rt_fault_inject(rt.RT_FAULT_NONE)
