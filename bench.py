@@ -385,8 +385,9 @@ def _e2e(ctx, wl, N, M, stream, args, world):
 
 
 def bench_batched(args, stream):
-    """Config 3: many uneven problems in one persistent launch per step, CUDA
-    graph; against stepping the same contexts one launch each."""
+    """The batched workload (512 uneven 1-D and 2-D problems) in one
+    persistent launch per step under a CUDA graph, against stepping the same
+    contexts one launch each."""
     import torch
     import paper_1403_6126_gb300 as rt
     from paper_1403_6126_gb300 import workloads as wlmod
@@ -441,7 +442,7 @@ def bench_batched(args, stream):
 
 
 def bench_small(stream):
-    """Configs 0 and 1: the 1-D slab (512 cells x 8 angles, FP64, 2000
+    """The two small workloads: the 1-D slab (512 cells x 8 angles, FP64, 2000
     steps in one captured graph; launch/latency bound, so microseconds per
     step) and the 2-D shadow problem (256 x 128 cells x 80 angles, 4000
     steps, FP64 and FP32 intensities; its working set fits in L2, so the
@@ -501,6 +502,9 @@ def bench_accuracy(stream, n=32, steps=10):
     o = oracle.run(p, dt, steps, I0, wl["T"], wl["rho"], wl["v"], wl["sa"], wl["ss"])
     Fo = np.sqrt((o["F"] ** 2).sum(axis=0))
     out = {"workload": "box3d recipe at %d^3 x %d angles, %d steps, FP64 oracle on the host" % (n, len(w), steps)}
+    out["slab1d_512x8_2000_steps"] = _accuracy_case(stream, wlmod.slab1d(), 2000, ("fp64", "fp32"))
+    out["shadow2d_64x32x80_200_steps"] = _accuracy_case(stream, wlmod.shadow2d(nx=64, ny=32), 200,
+                                                        ("fp64", "fp32", "bf16"))
     for prec in ("fp64", "fp32", "bf16"):
         c = _context(wl, nn, w, stream=stream.cuda_stream, precision=prec)
         c.set_intensity(I0)
@@ -514,6 +518,36 @@ def bench_accuracy(stream, n=32, steps=10):
         out[prec] = {"E_r": float(np.abs(E - o["E"]).max() / np.abs(o["E"]).max()),
                      "abs_F_r": float(np.abs(Fg - Fo).max() / max(Fo.max(), 1e-3 * np.abs(o["E"]).max())),
                      "T": float(np.abs(T - o["T"]).max() / np.abs(o["T"]).max())}
+    return out
+
+
+def _accuracy_case(stream, wl, steps, precisions):
+    """Norm-relative errors of E_r and |F_r| of each precision against the
+    FP64 oracle after `steps` steps of a small workload."""
+    import oracle
+    from paper_1403_6126_gb300 import workloads as wlmod
+    wl = wlmod.rounded_to_float32(wl)
+    nn, w = oracle.angles.by_name(wl["angles"])
+    I0 = wlmod.initial_intensity(wl, len(w)).astype(np.float32).astype(np.float64)
+    dx = tuple((wl["hi"][d] - wl["lo"][d]) / wl["shape"][2 - d] for d in range(3))
+    inflow = {face: wlmod.inflow_values(rule, nn) for face, rule in wl["inflow"].items()}
+    p = oracle.Problem(wl["shape"], dx, nn, w, C=wl["C"], P=wl["P"], dim=wl["dim"], bc=wl["bc"], inflow=inflow,
+                       gamma=wl["gamma"], R=wl["R"], hold_T=wl["hold_T"], estimate_v=wl["estimate_v"])
+    dt = oracle.cfl_dt(p, wl["cfl"])
+    o = oracle.run(p, dt, steps, I0, wl["T"], wl["rho"], wl["v"], wl["sa"], wl["ss"])
+    Fo = np.sqrt((o["F"] ** 2).sum(axis=0))
+    out = {}
+    for prec in precisions:
+        c = _context(wl, nn, w, stream=stream.cuda_stream, precision=prec)
+        c.set_intensity(I0)
+        c.set_material(wl["rho"], wl["T"], wl["v"], wl["sa"], wl["ss"])
+        c.run(dt, steps)
+        c.sync()
+        E, F, _ = c.moments()
+        c.close()
+        Fg = np.sqrt((F ** 2).sum(axis=0))
+        out[prec] = {"E_r": float(np.abs(E - o["E"]).max() / np.abs(o["E"]).max()),
+                     "abs_F_r": float(np.abs(Fg - Fo).max() / max(Fo.max(), 1e-3 * np.abs(o["E"]).max()))}
     return out
 
 
@@ -569,7 +603,7 @@ def _submit_args(wl):
 
 
 def bench_serving(args):
-    """Config 4 (scaled): a Poisson stream of 2-D / 3-D solves
+    """The serving workload: a Poisson stream of 2-D / 3-D solves
     into the continuous-batching server under an HBM budget; solves/s and
     p50/p99 latency, against solving the same requests one at a time with
     the FP64 path."""

@@ -53,7 +53,7 @@ typedef enum {
   RT_E_BUDGET = -3,     /* request larger than the server's HBM budget       */
   RT_E_CUDA = -4,       /* a CUDA call failed                                */
   RT_E_NONFINITE = -5,  /* non-finite input, or the T^4 Newton did not converge */
-  RT_E_TIMEOUT = -6,    /* rt_poll timed out                                 */
+  RT_E_TIMEOUT = -6,    /* rt_server_wait timed out                          */
   RT_E_STATE = -7       /* call out of order (e.g. rt_step before material)  */
 } rt_status;
 
