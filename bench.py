@@ -144,6 +144,23 @@ def _dist():
     return world, rank, local
 
 
+def max_over_ranks(x, world, device="cuda"):
+    """The slowest rank's figure: replicas report whole-job rates over the
+    longest time any rank took (x unchanged when world == 1)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds_max):
+    """Units all replicas processed per second of the slowest one."""
+    return units_per_rank * world / seconds_max
+
+
 def _angles(name):
     import paper_1403_6126_gb300 as rt
     if name.startswith("s"):
@@ -280,14 +297,10 @@ def run_gpu(args):
     ctx.sync()
     total_ms = t_all0.elapsed_time(t_all1)
     launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world)
     ms_per_step = total_ms / args.steps
     units_per_step = N * M
-    value = units_per_step * args.steps * world / (total_ms / 1e3)
+    value = whole_job_rate(units_per_step * args.steps, world, total_ms / 1e3)
 
     bytes_per_launch = algorithmic_bytes_per_cell(M, rs, velocity, not wl["hold_T"]) * N
     avg_launch_s = statistics.mean(launch_ms) / 1e3
@@ -373,14 +386,10 @@ def _e2e(ctx, wl, N, M, stream, args, world):
         one()
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([el], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
+    el = max_over_ranks(el, world)
     h2d = 7 * N * 8
     d2h = (10 + 1 + 3 + 1) * N * 8
-    return {"value": N * M * k * world / el, "unit": "cell-angle updates/s", "h2d_bytes_per_step": h2d,
+    return {"value": whole_job_rate(N * M * k, world, el), "unit": "cell-angle updates/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "steps": k, "ms_per_step": 1e3 * el / k}
 
 
