@@ -304,7 +304,8 @@ rt_status rt_poll(rt_server *s, rt_ticket t, double *E, double *F, double *P, do
 rt_status rt_server_wait(rt_server *s, rt_ticket t, double timeout_s);
 /* Steps launched so far, requests queued / running, device bytes in use. */
 rt_status rt_server_stats(rt_server *s, long long *steps, int *queued, int *running, size_t *bytes_in_use);
-/* Stops the thread and frees everything, including uncollected results. */
+/* Stops the thread and frees everything, including uncollected results.
+ * Servers not destroyed by the caller are destroyed when the process exits. */
 void rt_server_destroy(rt_server *s);
 
 /* ---- one step without device allocation ------------------------------------

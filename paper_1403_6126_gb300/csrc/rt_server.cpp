@@ -13,6 +13,7 @@
 // result is in host memory.
 #include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -163,6 +164,34 @@ void loop(rt_server *s) {
 
 rt_status fail(rt_status st, const std::string &m) { return rtg::set_error(st, m); }
 
+// Servers still alive when the process exits are stopped first: their
+// threads must not run into the CUDA runtime's own teardown.  The handler
+// is registered after the runtime has initialised (rt_server_create makes a
+// CUDA call first), so it runs before the runtime's.
+std::mutex g_live_mu;
+std::vector<rt_server *> g_live;
+
+void stop_live_servers() {
+  std::vector<rt_server *> live;
+  {
+    std::lock_guard<std::mutex> lock(g_live_mu);
+    live.swap(g_live);
+  }
+  for (rt_server *s : live) rt_server_destroy(s);
+}
+
+void track(rt_server *s) {
+  static const bool registered = (std::atexit(stop_live_servers), true);
+  (void)registered;
+  std::lock_guard<std::mutex> lock(g_live_mu);
+  g_live.push_back(s);
+}
+
+void untrack(rt_server *s) {
+  std::lock_guard<std::mutex> lock(g_live_mu);
+  g_live.erase(std::remove(g_live.begin(), g_live.end(), s), g_live.end());
+}
+
 }  // namespace
 
 extern "C" {
@@ -189,6 +218,7 @@ rt_status rt_server_create(size_t hbm_budget_bytes, const rt_options *opts, rt_s
     return st;
   }
   s->th = std::thread(loop, s);
+  track(s);
   *out = s;
   return RT_OK;
 }
@@ -295,6 +325,7 @@ rt_status rt_server_stats(rt_server *s, long long *steps, int *queued, int *runn
 
 void rt_server_destroy(rt_server *s) {
   if (!s) return;
+  untrack(s);
   {
     std::lock_guard<std::mutex> lock(s->mu);
     s->stop = true;

@@ -125,3 +125,33 @@ def test_server_errors_and_timeouts():
         rt.rt_poll(server, t)                      # ticket released
     assert e.value.status == rt.RT_E_INVALID
     rt.rt_server_destroy(server)
+
+
+def test_process_exit_with_a_live_server():
+    # a program that exits with a server still running (requests in flight,
+    # no rt_server_destroy) ends cleanly: the library stops its servers
+    # before the CUDA runtime shuts down
+    import os
+    import subprocess
+    import sys
+    code = """
+import ctypes, numpy as np, oracle, paper_1403_6126_gb300 as rt
+from paper_1403_6126_gb300 import workloads as wlmod
+wl = wlmod.box3d(n=16, angles="s4", steps=0)
+wl["v"] = np.zeros_like(wl["v"])
+n, w = oracle.angles.by_name("s4")
+g = rt.rt_grid(); g.dim = 3
+for d in range(3):
+    g.n[d] = 16; g.lo[d], g.hi[d] = 0.0, 1.0; g.bc[d][0] = g.bc[d][1] = rt.RT_BC_PERIODIC
+a = rt.rt_angles(); a.m = len(w)
+a.n = n.ctypes.data_as(ctypes.POINTER(ctypes.c_double)); a.w = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+f = [np.ascontiguousarray(wl[k], dtype=np.float64).reshape(-1) for k in ("rho", "T", "v", "sa", "ss")]
+s = rt.rt_server_create(1 << 30, rt.rt_options_default())
+for _ in range(4):
+    rt.rt_submit(s, g, a, wl["C"], wl["P"], *f, 1000)
+print("leaving")
+"""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, (r.returncode, r.stderr[-2000:])
+    assert "leaving" in r.stdout
