@@ -89,6 +89,15 @@ def test_create_validates_before_touching_the_device():
     assert o.precision == rt.RT_FP32 and abs(o.cfl - 0.4) < 1e-15 and o.estimate_v == 1
     _expect(rt.RT_E_INVALID, rt.rt_create, _grid(dim=4), _angles(n, w), 10.0, 1.0, o)
     _expect(rt.RT_E_INVALID, rt.rt_create, _grid(n=(0, 1, 1)), _angles(n, w), 10.0, 1.0, o)
+    _expect(rt.RT_E_INVALID, rt.rt_create, _grid(n=(0, 4, 4), dim=3), _angles(n, w), 10.0, 1.0, o)
+    # 2^28 cells is one more than the largest grid the ABI accepts
+    _expect(rt.RT_E_INVALID, rt.rt_create, _grid(n=(1024, 1024, 256), dim=3), _angles(n, w), 10.0, 1.0, o)
+    empty = _angles(n, w)
+    empty.m = 0
+    _expect(rt.RT_E_INVALID, rt.rt_create, _grid(), empty, 10.0, 1.0, o)
+    many = np.random.default_rng(0).normal(size=(257, 3))
+    many = np.ascontiguousarray(many / np.linalg.norm(many, axis=1, keepdims=True))
+    _expect(rt.RT_E_INVALID, rt.rt_create, _grid(), _angles(many, np.full(257, 1.0 / 257)), 10.0, 1.0, o)
     _expect(rt.RT_E_INVALID, rt.rt_create, _grid(), _angles(n, w), -1.0, 1.0, o)
     _expect(rt.RT_E_INVALID, rt.rt_create, _grid(), _angles(n, w * 1.01), 10.0, 1.0, o)
     bad = n.copy()
