@@ -541,7 +541,11 @@ __device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid,
     const float beta = a.P * C * (1.0f - v2 * invC * invC) * sa;
     const float c0r = dt * (float(8.0 * kPi) * a.P * sa * (H0 - S0 * invC) - float(4.0 * kPi) * beta * J0);
     const float c4 = dt * (2.0f * a.P * sa * (H1 - S1 * invC) + beta * omJ1);
-    // Newton on delta = T - T^n in float, then one double-precision step
+    // Newton on delta = T - T^n in float, then one double-precision step.
+    // The float iteration stops at |step| <= 1e-6 T (about 8 float ulps of
+    // T): near the root the float iterate can cycle between values one or
+    // two ulps apart, and a tighter test would never be met.  The double
+    // step from within 1e-6 leaves ~1e-12 (Newton converges quadratically).
     const float T0f = (float)T0, kvf = (float)kv;
     float d = 0.0f;
     int extra = -1, it;
@@ -554,7 +558,7 @@ __device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid,
       const float step = dn - d;
       d = dn;
       if (extra == 0) break;
-      if (extra < 0 && fabsf(step) <= 2e-7f * (T0f + d)) extra = 0;
+      if (extra < 0 && fabsf(step) <= 1e-6f * (T0f + d)) extra = 0;
     }
     double dd = (double)d;
     const double T = T0 + dd, T2 = T * T;

@@ -160,6 +160,29 @@ def batched(nprob=512, seed=5, steps=200):
     return out
 
 
+def _serving_specs(nreq, seed, scale):
+    """(index, angle set, side, opacity seed) of each serving request, in
+    the order the stream draws them."""
+    rng = np.random.default_rng(seed)
+    q = 32 if scale >= 1 else 8
+    for i in range(nreq):
+        ang = str(rng.choice(["s4", "s8"]))
+        lo, hi = (64, 512) if i % 2 == 0 else (64, 192)
+        side = max(q, int(round(np.exp(rng.uniform(np.log(lo * scale), np.log(hi * scale))) / q)) * q)
+        yield i, ang, side, int(rng.integers(1 << 30))
+
+
+def _serving_build(i, ang, side, ro_seed, steps, cache):
+    make = box2d if i % 2 == 0 else box3d
+    key = (make.__name__, side)
+    if key not in cache:
+        cache[key] = make(n=side, angles="s4", seed=1000 + side, steps=steps, kmax=max(1.0, side / 8))
+    base = cache[key]
+    ro = np.random.default_rng(ro_seed)
+    N = int(np.prod(base["shape"]))
+    return dict(base, angles=ang, steps=steps, sa=10.0 ** ro.uniform(0.0, 3.0, N), ss=10.0 ** ro.uniform(0.0, 3.0, N))
+
+
 def serving(nreq=32, seed=6, steps=200, scale=1.0):
     """Requests for the serving loop: even ones 2-D (side log-uniform in
     64..512 x scale), odd ones 3-D (side log-uniform in 64..192 x scale),
@@ -170,24 +193,16 @@ def serving(nreq=32, seed=6, steps=200, scale=1.0):
     side); every request draws its own sigma_a, sigma_s (10^U(0, 3) per
     cell), so long streams stay cheap to generate.  The arrival gaps are
     drawn by the caller."""
-    rng = np.random.default_rng(seed)
-    q = 32 if scale >= 1 else 8
     cache = {}
-    out = []
-    for i in range(nreq):
-        ang = str(rng.choice(["s4", "s8"]))
-        lo, hi = (64, 512) if i % 2 == 0 else (64, 192)
-        side = max(q, int(round(np.exp(rng.uniform(np.log(lo * scale), np.log(hi * scale))) / q)) * q)
-        make = box2d if i % 2 == 0 else box3d
-        key = (make.__name__, side)
-        if key not in cache:
-            cache[key] = make(n=side, angles="s4", seed=1000 + side, steps=steps, kmax=max(1.0, side / 8))
-        base = cache[key]
-        ro = np.random.default_rng(int(rng.integers(1 << 30)))
-        N = int(np.prod(base["shape"]))
-        out.append(dict(base, angles=ang, steps=steps, sa=10.0 ** ro.uniform(0.0, 3.0, N),
-                        ss=10.0 ** ro.uniform(0.0, 3.0, N)))
-    return out
+    return [_serving_build(i, ang, side, ro, steps, cache) for i, ang, side, ro in _serving_specs(nreq, seed, scale)]
+
+
+def serving_request(index, seed=6, steps=200, scale=1.0):
+    """Request `index` of the serving stream alone (the same fields as
+    serving() gives it)."""
+    for i, ang, side, ro in _serving_specs(index + 1, seed, scale):
+        if i == index:
+            return _serving_build(i, ang, side, ro, steps, {})
 
 
 def initial_intensity(wl, M):
