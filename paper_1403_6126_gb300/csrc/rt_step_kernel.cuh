@@ -1,5 +1,7 @@
 // Fused radiation-transfer step for sm_103a (Jiang, Stone & Davis 2014,
-// arXiv:1403.6126, secs. 3-4).
+// arXiv:1403.6126, secs. 3-4): the double-precision kernel (process_tile
+// with Real = double) and the tile geometry that the float kernel of
+// rt_step_pair.cuh shares.
 //
 // One CTA owns a tile of cells, one thread per cell, and walks the angles.
 // Per angle, in four phases separated by CTA barriers:
