@@ -178,15 +178,23 @@ rt_status fetch(rt_ctx *c, const double *src, double *dst, long long n) {
   return RT_OK;
 }
 
-// Copies n doubles from the device buffer src to the caller.
-rt_status deliver(rt_ctx *c, const double *src, double *dst, long long n) {
-  if (c->opt.device_ptrs) {
-    RT_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-  } else {
-    RT_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    RT_CUDA(cudaStreamSynchronize(c->stream));
-  }
+// Queues the copy of n doubles from the device buffer src to the caller;
+// delivered() then waits once for all of a call's copies to host memory.
+rt_status deliver_async(rt_ctx *c, const double *src, double *dst, long long n) {
+  RT_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double),
+                          c->opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
   return RT_OK;
+}
+
+rt_status delivered(rt_ctx *c) {
+  if (!c->opt.device_ptrs) RT_CUDA(cudaStreamSynchronize(c->stream));
+  return RT_OK;
+}
+
+// Copies n doubles from the device buffer src to the caller (host: waits).
+rt_status deliver(rt_ctx *c, const double *src, double *dst, long long n) {
+  rt_status st = deliver_async(c, src, dst, n);
+  return st != RT_OK ? st : delivered(c);
 }
 
 }  // namespace
@@ -726,10 +734,10 @@ rt_status rt_moments(rt_ctx *c, double *E, double *F, double *P) {
   const char *mom = (const char *)c->mom[c->cur];
   rt_status st;
   if ((st = convert_out(c, mom, c->stage, 10 * N)) != RT_OK) return st;
-  if (E && (st = deliver(c, c->stage, E, N)) != RT_OK) return st;
-  if (F && (st = deliver(c, c->stage + N, F, 3 * N)) != RT_OK) return st;
-  if (P && (st = deliver(c, c->stage + 4 * N, P, 6 * N)) != RT_OK) return st;
-  return RT_OK;
+  if (E && (st = deliver_async(c, c->stage, E, N)) != RT_OK) return st;
+  if (F && (st = deliver_async(c, c->stage + N, F, 3 * N)) != RT_OK) return st;
+  if (P && (st = deliver_async(c, c->stage + 4 * N, P, 6 * N)) != RT_OK) return st;
+  return delivered(c);
 }
 
 rt_status rt_sources(rt_ctx *c, double *dE_gas, double *dMom, double *T_new) {
@@ -737,19 +745,14 @@ rt_status rt_sources(rt_ctx *c, double *dE_gas, double *dMom, double *T_new) {
   if (!c) return fail(RT_E_INVALID, "rt_sources: NULL context");
   const long long N = c->N;
   rt_status st;
-  if (dE_gas) {
-    RT_CUDA(cudaMemcpyAsync(c->stage, c->dEgas, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    if ((st = deliver(c, c->stage, dE_gas, N)) != RT_OK) return st;
-  }
+  // the energy source and T are double on the device: copied out directly
+  if (dE_gas && (st = deliver_async(c, c->dEgas, dE_gas, N)) != RT_OK) return st;
   if (dMom) {
     if ((st = convert_out(c, c->dMom, c->stage, 3 * N)) != RT_OK) return st;
-    if ((st = deliver(c, c->stage, dMom, 3 * N)) != RT_OK) return st;
+    if ((st = deliver_async(c, c->stage, dMom, 3 * N)) != RT_OK) return st;
   }
-  if (T_new) {
-    RT_CUDA(cudaMemcpyAsync(c->stage, c->T, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    if ((st = deliver(c, c->stage, T_new, N)) != RT_OK) return st;
-  }
-  return RT_OK;
+  if (T_new && (st = deliver_async(c, c->T, T_new, N)) != RT_OK) return st;
+  return delivered(c);
 }
 
 rt_status rt_get_intensity(rt_ctx *c, double *I) {
