@@ -10,7 +10,15 @@
 // dummy angle (n = 0, W = 0): it adds nothing to any angle sum and is never
 // stored.
 //
-// Two further differences from the scalar kernel:
+// Three further differences from the scalar kernel:
+//  * The implicit steps divide in increment form: (r' - s1 - c s2)/a' as
+//    r' - ((a' - 1) r' + s1 + c s2)/a' always, and r/d as r - (d - 1) r/d
+//    where dt C sa < 1, with d - 1 and a' - 1 formed as dt sigma (C - vn)
+//    directly.  In float, 1 + dt C sigma carries dt C sigma only to one ulp
+//    of 1 (6e-8), so a cell with dt C sigma = 1e-5 would see its absorption
+//    rate off by ~1e-3 relative, the same way every step, and a scattering
+//    step would not conserve sum W I to better than that ulp; in increment
+//    form the rounding of d and a' only scales the (small) change of I.
 //  * The right-hand sides Q_m of the implicit steps go to the output
 //    intensity array instead of shared memory.  Each thread writes Q_m of its
 //    cell for every angle, and after the cell solve reads them back and
@@ -332,6 +340,15 @@ __device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid,
   const float apb0 = 1.0f - a1 * v2 * invC, apb2 = -a1 * invC;
   const float rd0 = VEL ? 0.0f : fast_rcp(A0);
   const float ra0 = VEL ? 0.0f : fast_rcp(a0);
+  // d_m - 1 = dt sa (C - vn) and a'_m - 1 = dt ss (C - vn), negated, from
+  // their own products: 1 + x holds x only to one float ulp of 1, so the
+  // implicit steps divide by the rounded d_m, a'_m inside an increment (see
+  // phase 4 and the last loop).  Absorption takes the increment only while
+  // dt C sa < 1: for an opaque cell r/d is small beside r, and r - r(d-1)/d
+  // would cancel; there the direct quotient's rounding is forgotten within a
+  // step, since the cell relaxes to its emission on that time scale.
+  const float nA1C = -A1 * C, na1C = -a1 * C;
+  const bool abs_inc = A1 * C < 1.0f;
 
   // intensity-dependent sums: U_k = sum W vn^k r / d, AQ = sum Q / a,
   // BQ = sum b Q / a, pre = sum W n (I^n + Delta F)
@@ -450,7 +467,10 @@ __device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid,
       rd = p_rcp(p_fma(dup(-A1), vn, dup(A0)));
       ra = p_rcp(p_fma(dup(-a1), vn, dup(a0)));
     }
-    const f2 qa = p_mul(to_scat ? I0 : full, rd);   // r_m / d_m
+    // r_m / d_m as r_m - (d_m - 1) r_m / d_m
+    const f2 rm = to_scat ? I0 : full;
+    const f2 xdn = VEL ? p_fma(dup(A1), vn, dup(nA1C)) : dup(nA1C);   // -(d_m - 1)
+    const f2 qa = abs_inc ? p_fma(p_mul(rm, xdn), rd, rm) : p_mul(rm, rd);
     const f2 Q = to_scat ? p_add(qa, dF) : qa;
     if (valid) {
       float *qdst = B16 ? a.Q : a.I_out;
@@ -604,7 +624,9 @@ __device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid,
     const f2 pe = p_mul(dup(A1), p_mul(p_fma(dup(3.0f), vn, dup(C)), rd));
     const f2 rs = p_fma(pe, dup(th), p_fma(rd, dup(-kS), Q));        // r'_m
     const f2 cm = p_mul(dup(cq), vn);
-    const f2 I1 = p_mul(p_fma(cm, dup(-s2), p_sub(rs, dup(s1))), ra);
+    // I^{n+1} = (r' - s1 - c s2) / a' taken as r' - ((a' - 1) r' + s1 + c s2) / a'
+    const f2 xan = VEL ? p_fma(dup(a1), vn, dup(na1C)) : dup(na1C);   // -(a'_m - 1)
+    const f2 I1 = p_fma(p_fma(xan, rs, p_fma(cm, dup(-s2), dup(-s1))), ra, rs);
     if (B16) {
       a.I16_out[(long long)m * N + c] = b16_encode(I1.x, rJ);
       if (second) a.I16_out[(long long)(m + 1) * N + c] = b16_encode(I1.y, rJ);
