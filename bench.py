@@ -601,10 +601,10 @@ def bench_bf16(args, stream):
             "algorithmic_bytes_per_step": b}
 
 
-def _submit_args(wl):
+def _submit_args(wl, angles=None):
     import ctypes
     import paper_1403_6126_gb300 as rt
-    n, w = _angles(wl["angles"])
+    n, w = _angles(wl["angles"]) if angles is None else (np.ascontiguousarray(angles[0]), np.ascontiguousarray(angles[1]))
     g = rt.rt_grid()
     g.dim = wl["dim"]
     nz, ny, nx = wl["shape"]
@@ -618,6 +618,49 @@ def _submit_args(wl):
     a.w = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     fields = [np.ascontiguousarray(wl[k], dtype=np.float64).reshape(-1) for k in ("rho", "T", "v", "sa", "ss")]
     return g, a, (n, w), fields
+
+
+def _serving_accuracy(wl, opts, budget_gb):
+    """E_r and |F_r| of one request served (through the server) and solved by
+    the FP64 path alone, each against the FP64 oracle on the host; the
+    request's fields are float32-rounded so all three see the same inputs."""
+    import oracle
+    import paper_1403_6126_gb300 as rt
+    from paper_1403_6126_gb300 import workloads as wlmod
+    wl = wlmod.rounded_to_float32(wl)
+    g, a, (nn, w), f = _submit_args(wl, oracle.angles.by_name(wl["angles"]))   # the oracle's own angle set
+    N, M, steps, dim = int(np.prod(wl["shape"])), len(w), wl["steps"], wl["dim"]
+    server = rt.rt_server_create(int(budget_gb * 2 ** 30), opts)
+    try:
+        t = rt.rt_submit(server, g, a, wl["C"], wl["P"], *f, steps)
+        rt.rt_server_wait(server, t, 600.0)
+        Es, Fs = np.zeros(N), np.zeros((3, N))
+        rt.rt_poll(server, t, Es, Fs, None)
+    finally:
+        rt.rt_server_destroy(server)
+    c = _context(wl, nn, w, precision="fp64")
+    c.set_material(*f)
+    c.run(0.0, steps)
+    c.sync()
+    E64, F64, _ = c.moments()
+    c.close()
+    dx = tuple((wl["hi"][d] - wl["lo"][d]) / wl["shape"][2 - d] for d in range(3))
+    p = oracle.Problem(wl["shape"], dx, nn, w, C=wl["C"], P=wl["P"], dim=dim, bc=wl["bc"], gamma=wl["gamma"],
+                       R=wl["R"], hold_T=wl["hold_T"], estimate_v=wl["estimate_v"])
+    oracle.set_threads(os.cpu_count() or 1)
+    o = oracle.run(p, oracle.cfl_dt(p, wl["cfl"]), steps, wlmod.initial_intensity(wl, M), wl["T"], wl["rho"],
+                   wl["v"], wl["sa"], wl["ss"])
+    Fo = np.sqrt((o["F"][:dim] ** 2).sum(axis=0))
+    Emax = np.abs(o["E"]).max()
+
+    def err(E, F):
+        Fg = np.sqrt((F[:dim] ** 2).sum(axis=0))
+        return {"E_r": float(np.abs(E - o["E"]).max() / Emax),
+                "abs_F_r": float(np.abs(Fg - Fo).max() / max(Fo.max(), 1e-3 * Emax))}
+
+    return {"request": "%s %s x %d angles, %d steps" % (wl["name"], "x".join(str(s) for s in wl["shape"][::-1] if s > 1),
+                                                      M, steps),
+            "served_fp32": err(Es, Fs), "fp64_one_at_a_time": err(E64, F64)}
 
 
 def bench_serving(args):
@@ -689,6 +732,9 @@ def bench_serving(args):
         c.close()
     fp64_s = time.perf_counter() - t0
     fp64_rate = len(reqs) / (fp64_s * sum(work) / sum(work[:k]))
+    # both paths against the oracle on the smallest 2-D request of the stream
+    i2 = min((i for i, wl in enumerate(wls) if wl["dim"] == 2), key=lambda i: work[i])
+    accuracy = _serving_accuracy(wls[i2], o, args.serve_budget_gb)
     return {"workload": "%d requests: 2-D 64..512^2 and 3-D 64..192^3 (sides in steps of 32), 24/80 angles, %d steps each, box gas fields; "
                         "Poisson arrivals at 0.8 x measured capacity" % (len(reqs), args.serve_steps),
             "value": (len(reqs) - failed[1]) / makespan, "unit": "solves/s", "p50_latency_s": float(np.percentile(lat, 50)),
@@ -700,7 +746,8 @@ def bench_serving(args):
                             "p99_latency_s": float(np.percentile(over_lat, 99))},
             "fp64_one_at_a_time": {"value": fp64_rate, "unit": "solves/s", "timed_requests": k,
                                    "note": "first %d requests timed (%.1f s), scaled to the whole stream by "
-                                           "cell-angle-steps" % (k, fp64_s)}}
+                                           "cell-angle-steps" % (k, fp64_s)},
+            "accuracy_vs_oracle": accuracy}
 
 
 def main():
