@@ -119,3 +119,36 @@ def test_opaque_limit():
     for k in ("I", "E", "F", "P", "T", "dEgas", "dMom"):
         err = field_err(g, o, k, o["wl"])
         assert err <= 1e4 * 2.2e-16 * 10, (k, err)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_crossing_beams(precision):
+    # Sec. 5.4 as an initial-value problem (see test_oracle_transport): two
+    # beams on the 45-degree S2 angles cross in a periodic, source-free box;
+    # 60 steps take them through each other.
+    from test_oracle_transport import _beams_problem, _run_free
+    from _helpers import gpu_context
+    p, n, a, b, IA, IB = _beams_problem()
+    N = p.N
+    wl = dict(shape=p.shape, dim=2, lo=(0.0, 0.0, 0.0), hi=(1.0, 4.0, 1.0), bc=p.bc, C=1.0, P=1.0, cfl=0.4,
+              gamma=5.0 / 3.0, R=1.0, hold_T=True, estimate_v=False, inflow={})
+    ctx = gpu_context(wl, n, p.w, precision)
+    ctx.set_intensity(IA + IB)
+    ctx.set_material(np.ones(N), np.ones(N), np.zeros((3, N)), np.zeros(N), np.zeros(N))
+    dt = oracle.cfl_dt(p, 0.4)
+    assert abs(ctx.cfl_dt() - dt) <= 1e-15 * dt
+    for _ in range(60):
+        ctx.step(dt)
+    ctx.sync()
+    E, F, _ = ctx.moments()
+    I = ctx.intensity()
+    ctx.close()
+    o = _run_free(p, IA + IB, dt, 60)
+    Emax = np.abs(o["E"]).max()
+    if precision == "fp64":
+        assert np.abs(I - o["I"]).max() <= FP64_TOL * np.abs(o["I"]).max()
+        assert np.abs(E - o["E"]).max() <= FP64_TOL * Emax
+        assert np.abs(F - o["F"]).max() <= FP64_TOL * Emax
+    else:
+        assert np.abs(E - o["E"]).max() <= MIXED_TOL * Emax
+        assert np.abs(flux_magnitude(F) - flux_magnitude(o["F"])).max() <= MIXED_TOL * Emax

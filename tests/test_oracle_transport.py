@@ -116,3 +116,66 @@ def test_alpha_limits():
         assert abs(a * (10 * 0.1 * s) - 1.0) < 1e-12
     # tau = 1 exactly: sqrt(1 - e^-1)
     assert abs(oracle.alpha(0.1, 1.0) - np.sqrt(1 - np.exp(-1.0))) < 1e-15
+
+
+def _beams_problem():
+    """Sec. 5.4 crossing beams, as an initial-value problem: a periodic-in-x,
+    vacuum-in-y box of 32 x 128 square cells, sigma = 0, S2 angles (every
+    direction at 45 degrees to the x and y axes in the x-y plane).  Beam A is
+    a 4 x 4-cell blob of I = 1 on the two angles with n_x > 0, n_y > 0, beam
+    B one on the two angles with n_x < 0, n_y > 0, 12 cells to its right."""
+    n, w = angles.level_symmetric(2)
+    nx, ny = 32, 128
+    p = oracle.Problem((1, ny, nx), (1.0 / nx, 4.0 / ny, 1.0), n, w, C=1.0, P=1.0, dim=2,
+                       bc=((oracle.PERIODIC, oracle.PERIODIC), (oracle.VACUUM, oracle.VACUUM),
+                           (oracle.PERIODIC, oracle.PERIODIC)), hold_T=True)
+    a = np.where((n[:, 0] > 0) & (n[:, 1] > 0))[0]
+    b = np.where((n[:, 0] < 0) & (n[:, 1] > 0))[0]
+    IA, IB = np.zeros((p.M, ny, nx)), np.zeros((p.M, ny, nx))
+    IA[a, 8:12, 8:12] = 1.0
+    IB[b, 8:12, 20:24] = 1.0
+    return p, n, a, b, IA.reshape(p.M, -1), IB.reshape(p.M, -1)
+
+
+def _run_free(p, I, dt, steps):
+    N = p.N
+    out = None
+    for _ in range(steps):
+        out = oracle.step(p, dt, I, np.ones(N), np.ones(N), np.zeros((3, N)), _zeros(N), _zeros(N))
+        I = out["I"]
+    return out
+
+
+def test_crossing_beams_pass_through_each_other():
+    # Sec. 5.4: with the intensity split by angle, two beams that cross do
+    # not interact (an angle-moment closure would merge them where they
+    # cross): after they have crossed, each angle holds exactly what it holds
+    # when its beam travels alone, and E_r is the sum.  Each angle's sum over
+    # cells is conserved (sigma = 0, the blobs stay off the vacuum faces), and
+    # each blob's centroid moves at C n.
+    p, n, a, b, IA, IB = _beams_problem()
+    dt = oracle.cfl_dt(p, 0.4)
+    steps = 60                     # relative x speed 0.46 cells/step: they meet near step 26
+    both = _run_free(p, IA + IB, dt, steps)
+    onlyA = _run_free(p, IA, dt, steps)
+    onlyB = _run_free(p, IB, dt, steps)
+    np.testing.assert_array_equal(both["I"][a], onlyA["I"][a])
+    np.testing.assert_array_equal(both["I"][b], onlyB["I"][b])
+    assert np.abs(both["I"][a]).max() > 0.1 and np.abs(onlyA["I"][b]).max() == 0.0
+    np.testing.assert_allclose(both["E"], onlyA["E"] + onlyB["E"], rtol=0, atol=1e-15 * both["E"].max())
+    ny, nx = p.shape[1], p.shape[2]
+    x = (np.arange(nx) + 0.5) / nx
+    y = (np.arange(ny) + 0.5) * 4.0 / ny
+    t = steps * dt
+    for m in np.concatenate([a, b]):
+        I0 = (IA + IB)[m].reshape(ny, nx)
+        I1 = both["I"][m].reshape(ny, nx)
+        assert abs(I1.sum() / I0.sum() - 1.0) < 1e-13
+        # x: offsets from the expected centre wrapped into (-0.5, 0.5] (periodic)
+        wx0, wx1 = I0.sum(axis=0), I1.sum(axis=0)
+        x_expect = (wx0 * x).sum() / wx0.sum() + p.C * n[m, 0] * t
+        dxw = (x - x_expect + 0.5) % 1.0 - 0.5
+        assert abs((wx1 * dxw).sum() / wx1.sum()) < 0.05 / nx, m
+        wy0, wy1 = I0.sum(axis=1), I1.sum(axis=1)
+        y_expect = (wy0 * y).sum() / wy0.sum() + p.C * n[m, 1] * t
+        assert abs((wy1 * y).sum() / wy1.sum() - y_expect) < 0.05 * 4.0 / ny, m
