@@ -254,8 +254,8 @@ rt_status rt_batch_create(void *stream, rt_batch **out);
 rt_status rt_batch_add(rt_batch *b, rt_ctx *ctx);
 rt_status rt_batch_remove(rt_batch *b, rt_ctx *ctx);
 int rt_batch_size(const rt_batch *b);
-/* nsteps steps of every member, captured in one CUDA graph (a counter reset
- * and one persistent launch per step) when the stream is not NULL.
+/* nsteps steps of every member, captured in one CUDA graph (one persistent
+ * launch per step) when the stream is not NULL.
  * Stream-ordered.  RT_E_INVALID if the largest angle set does not fit. */
 rt_status rt_batch_step(rt_batch *b, int nsteps);
 /* Tile-set autotuner of the persistent kernel.  Three variants are

@@ -3,11 +3,12 @@
 // A batch holds contexts created with rt_create (float intensities).  For a
 // step, a device work list names every (problem, tile) pair; a grid of
 // persistent CTAs (as many as fit on the GPU at the shared-memory size the
-// largest angle set needs) pulls items through an atomic counter and runs the
-// same per-tile code as the single-problem kernel, so each problem's result
-// is bitwise the one it gets alone.  Items are ordered by decreasing angle
-// count so the long tiles start first.  Steps are captured in a CUDA graph (a
-// counter reset and a kernel per step) and replayed.  Three tile sets are
+// largest angle set needs) takes items b, b + grid, b + 2 grid, ... and runs
+// the same per-tile code as the single-problem kernel, so each problem's
+// result is bitwise the one it gets alone.  Items are ordered by decreasing
+// angle count, so the long tiles start first and the interleave gives every
+// CTA a like share.  Steps are captured in a CUDA graph (one kernel per step)
+// and replayed.  Three tile sets are
 // compiled (rt_batch_k*.cu); rt_batch_autotune times them on the batch's own
 // members and keeps the fastest.
 #include <algorithm>
@@ -48,7 +49,6 @@ struct rt_batch {
   size_t smem = 0;
   rtg::WorkItem *d_items = nullptr;
   rtg::StepArgs<float> *d_desc[2] = {nullptr, nullptr};
-  int *d_counter = nullptr;
   size_t items_cap = 0, desc_cap = 0;
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0, graph_phase = -1;
@@ -145,11 +145,10 @@ rt_status rebuild(rt_batch *b) {
   return RT_OK;
 }
 
-// Queues one step: counter reset and one persistent launch.
+// Queues one step: one persistent launch.
 rt_status enqueue_step(rt_batch *b, int parity) {
-  RT_BCUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream));
   RT_BCUDA(rtg::batch_variant(b->variant)
-                .launch(b->vel, b->grid, b->smem, b->d_desc[parity], b->d_items, b->nitems, b->d_counter, b->stream));
+                .launch(b->vel, b->grid, b->smem, b->d_desc[parity], b->d_items, b->nitems, b->stream));
   return RT_OK;
 }
 
@@ -163,11 +162,6 @@ rt_status rt_batch_create(void *stream, rt_batch **out) {
   rt_batch *b = new (std::nothrow) rt_batch;
   if (!b) return rtg::set_error(RT_E_NOMEM, "rt_batch_create: host allocation");
   b->stream = (cudaStream_t)stream;
-  if (rtg::device_alloc((void **)&b->d_counter, sizeof(int)) != cudaSuccess) {
-    cudaGetLastError();
-    delete b;
-    return rtg::set_error(RT_E_NOMEM, "rt_batch_create: device allocation");
-  }
   *out = b;
   return RT_OK;
 }
@@ -312,7 +306,6 @@ void rt_batch_destroy(rt_batch *b) {
   if (b->d_items) cudaFree(b->d_items);
   for (int p = 0; p < 2; ++p)
     if (b->d_desc[p]) cudaFree(b->d_desc[p]);
-  if (b->d_counter) cudaFree(b->d_counter);
   delete b;
 }
 

@@ -1,6 +1,6 @@
-// Persistent multi-problem step kernel (see rt_batch.cu): CTAs pull
-// (problem, tile) work items through an atomic counter and run the same
-// per-tile code as the single-problem float kernel.  One compiled variant per
+// Persistent multi-problem step kernel (see rt_batch.cu): CTAs walk the
+// (problem, tile) work list in a fixed interleave and run the same per-tile
+// code as the single-problem float kernel.  One compiled variant per
 // tile set; all shapes of a set have the same thread count (one per cell).
 #pragma once
 
@@ -18,7 +18,7 @@ struct BatchVariant {
   TileShape t1, t2, t3;   // tiles of 1-D, 2-D and 3-D members
   cudaError_t (*prepare)(bool vel, size_t smem, int *blocks_per_sm);
   cudaError_t (*launch)(bool vel, int grid, size_t smem, const StepArgs<float> *descs, const WorkItem *items,
-                        int nitems, int *counter, cudaStream_t s);
+                        int nitems, cudaStream_t s);
 };
 
 constexpr int kBatchVariants = 3;
@@ -27,30 +27,31 @@ const BatchVariant &batch_variant(int i);
 
 template <bool VEL, int NT, int X2, int Y2, int X3, int Y3, int Z3>
 __global__ void __launch_bounds__(NT, 512 / NT)
-    batch_kernel(const StepArgs<float> *__restrict__ descs, const WorkItem *__restrict__ items, int nitems,
-                 int *counter) {
+    batch_kernel(const StepArgs<float> *__restrict__ descs, const WorkItem *__restrict__ items, int nitems) {
   static_assert(X2 * Y2 == NT && X3 * Y3 * Z3 == NT, "every tile shape has one thread per cell");
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ StepArgs<float> desc;
-  __shared__ int s_item;
   const int tid = threadIdx.x;
-  for (;;) {
-    if (tid == 0) s_item = atomicAdd(counter, 1);
-    __syncthreads();
-    const int it = s_item;
-    if (it >= nitems) break;
+  // CTA b takes items b, b + grid, b + 2 grid, ...: the list is sorted by
+  // decreasing cost, so every CTA gets a like share, and no claim (atomic,
+  // barrier, broadcast) stands between one tile and the next
+  int cur = -1;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const WorkItem w = items[it];
-    const int *src = reinterpret_cast<const int *>(descs + w.prob);
-    int *dst = reinterpret_cast<int *>(&desc);
-    for (int i = tid; i < (int)(sizeof(StepArgs<float>) / sizeof(int)); i += NT) dst[i] = src[i];
-    __syncthreads();
+    if (w.prob != cur) {   // the descriptor is copied only when the problem changes
+      __syncthreads();     // every thread is done with the previous one
+      const int *src = reinterpret_cast<const int *>(descs + w.prob);
+      int *dst = reinterpret_cast<int *>(&desc);
+      for (int i = tid; i < (int)(sizeof(StepArgs<float>) / sizeof(int)); i += NT) dst[i] = src[i];
+      __syncthreads();
+      cur = w.prob;
+    }
     if (desc.dim == 3)
       stepk::process_tile2<3, VEL, X3, Y3, Z3>(desc, tid, w.tbx, w.tby, w.tbz, smem);
     else if (desc.dim == 2)
       stepk::process_tile2<2, VEL, X2, Y2, 1>(desc, tid, w.tbx, w.tby, 0, smem);
     else
       stepk::process_tile2<1, VEL, NT, 1, 1>(desc, tid, w.tbx, 0, 0, smem);
-    __syncthreads();   // every thread has read s_item and desc
   }
 }
 
@@ -63,9 +64,9 @@ struct BatchImpl {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, NT, smem);
   }
   static cudaError_t launch(bool vel, int grid, size_t smem, const StepArgs<float> *descs, const WorkItem *items,
-                            int nitems, int *counter, cudaStream_t s) {
+                            int nitems, cudaStream_t s) {
     auto kern = vel ? batch_kernel<true, NT, X2, Y2, X3, Y3, Z3> : batch_kernel<false, NT, X2, Y2, X3, Y3, Z3>;
-    kern<<<grid, NT, smem, s>>>(descs, items, nitems, counter);
+    kern<<<grid, NT, smem, s>>>(descs, items, nitems);
     return cudaGetLastError();
   }
   static BatchVariant describe() {
