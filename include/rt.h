@@ -212,6 +212,23 @@ rt_status rt_moments(rt_ctx *ctx, double *E, double *F, double *P);
  * dMom = Delta(rho v) (3N), T_new = T^{n+1} (N).  NULL skips a field. */
 rt_status rt_sources(rt_ctx *ctx, double *dE_gas, double *dMom, double *T_new);
 
+/* One step of the loop a gas code runs around the radiation (sec. 4.1: the
+ * MHD update between steps is the caller's): rt_set_material(rho, T, v,
+ * sigma_a, sigma_s), rt_step(dt), rt_sources(dE_gas, dMom, T_new) in one
+ * call, with the same arguments, results and errors (bitwise the same
+ * outputs and state).  For a 3-D context with host arrays the grid is cut
+ * into z-slabs of whole tiles: the fields of a slab (and its two-plane
+ * halo) cross to the device while the previous slab steps, and the sources
+ * of a slab cross back while the next one steps.  Other contexts (1-D, 2-D,
+ * device_ptrs, bf16 storage, the first call) run the three calls in turn.
+ * T_new may be T (the next step's temperature); no other output may
+ * overlap an input.  Waits for the transfers.  On RT_E_NONFINITE /
+ * RT_E_INVALID from the fields the intensity is unchanged and the gas
+ * fields must be set again (RT_E_STATE until then). */
+rt_status rt_step_coupled(rt_ctx *ctx, double dt, const double *rho, const double *T, const double *v,
+                          const double *sigma_a, const double *sigma_s, double *dE_gas, double *dMom,
+                          double *T_new);
+
 /* Copies the current intensity out (M*N values, angle-major). */
 rt_status rt_get_intensity(rt_ctx *ctx, double *I);
 

@@ -94,6 +94,7 @@ def lib():
             "rt_sync": (I, [V]),
             "rt_moments": (I, [V, V, V, V]),
             "rt_sources": (I, [V, V, V, V]),
+            "rt_step_coupled": (I, [V, D, V, V, V, V, V, V, V, V]),
             "rt_get_intensity": (I, [V, V]),
             "rt_destroy": (None, [V]),
             "rt_batch_create": (I, [V, ctypes.POINTER(V)]),
@@ -238,6 +239,11 @@ def rt_moments(ctx, E, F, P):
 
 def rt_sources(ctx, dE_gas, dMom, T_new):
     _check(lib().rt_sources(ctx, _ptr(dE_gas), _ptr(dMom), _ptr(T_new)), "rt_sources")
+
+
+def rt_step_coupled(ctx, dt, rho, T, v, sigma_a, sigma_s, dE_gas, dMom, T_new):
+    _check(lib().rt_step_coupled(ctx, float(dt), _ptr(rho), _ptr(T), _ptr(v), _ptr(sigma_a), _ptr(sigma_s),
+                                 _ptr(dE_gas), _ptr(dMom), _ptr(T_new)), "rt_step_coupled")
 
 
 def rt_get_intensity(ctx, I):
@@ -437,6 +443,18 @@ class Context:
         dE, dM, T = np.zeros(N), np.zeros((3, N)), np.zeros(N)
         rt_sources(self.ctx, dE, dM, T)
         return dE, dM, T
+
+    def step_coupled(self, dt, rho, T, v, sigma_a, sigma_s, dE_gas=None, dMom=None, T_new=None):
+        """rt_step_coupled: the fields in, one step, the sources out (into the
+        given float64 arrays, or new ones); returns (dE_gas, dMom, T_new)."""
+        N = self.N
+        fields = [self._host(rho, N), self._host(T, N), self._host(v, 3 * N), self._host(sigma_a, N),
+                  self._host(sigma_s, N)]
+        dE_gas = np.zeros(N) if dE_gas is None else dE_gas
+        dMom = np.zeros((3, N)) if dMom is None else dMom
+        T_new = np.zeros(N) if T_new is None else T_new
+        rt_step_coupled(self.ctx, dt, *fields, dE_gas, dMom, T_new)
+        return dE_gas, dMom, T_new
 
     def intensity(self):
         I = np.zeros((self.M, self.N))

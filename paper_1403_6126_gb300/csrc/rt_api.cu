@@ -63,6 +63,16 @@ namespace {
 
 void free_all(rt_ctx *c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (cudaStream_t s : {c->xs_in, c->xs_out}) {
+    if (!s) continue;
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+  if (c->ev_start) cudaEventDestroy(c->ev_start);
+  for (int k = 0; k < rt_ctx::kSlabs; ++k) {
+    if (c->ev_in[k]) cudaEventDestroy(c->ev_in[k]);
+    if (c->ev_done[k]) cudaEventDestroy(c->ev_done[k]);
+  }
   void *ptrs[] = {c->I[0], c->I[1], c->mom[0], c->mom[1], c->rho, c->sa, c->ss, c->v,
                   c->T, c->dEgas, c->dMom, c->ang, c->inflow, c->flags, c->stage, c->qscr};
   for (void *p : ptrs)
@@ -117,6 +127,8 @@ rtg::StepArgs<Real> rtg::make_args(rt_ctx *c, double dt) {
   a.dEgas = c->dEgas;
   a.dMom = (Real *)c->dMom;
   a.status = c->flags;
+  a.tz_begin = 0;
+  a.tz_count = 0;
   return a;
 }
 
@@ -148,6 +160,25 @@ rt_status launch_step(rt_ctx *c, double dt) {
 rt_status convert_in(rt_ctx *c, const double *src, void *dst, long long n) {
   cudaError_t e = c->fp64 ? rtg::launch_convert_in<double>(src, (double *)dst, n, c->stream)
                           : rtg::launch_convert_in<float>(src, (float *)dst, n, c->stream);
+  return e == cudaSuccess ? RT_OK : cuda_fail(e, "convert");
+}
+
+// Scan (and with convert, conversion into the context's arrays) of the gas
+// fields staged in c->stage, cells [c0, c1); flag bits go to c->flags[1].
+rt_status fields_in(rt_ctx *c, long long c0, long long c1, bool convert) {
+  cudaError_t e = c->fp64 ? rtg::launch_fields_in<double>(c->stage, c->N, c0, c1 - c0, convert, (double *)c->rho,
+                                                          (double *)c->sa, (double *)c->ss, (double *)c->v, c->T,
+                                                          c->flags + 1, c->stream)
+                          : rtg::launch_fields_in<float>(c->stage, c->N, c0, c1 - c0, convert, (float *)c->rho,
+                                                         (float *)c->sa, (float *)c->ss, (float *)c->v, c->T,
+                                                         c->flags + 1, c->stream);
+  return e == cudaSuccess ? RT_OK : cuda_fail(e, "fields");
+}
+
+// Delta(rho v) of cells [c0, c1), three components, into dst (double, 3N).
+rt_status dmom_out(rt_ctx *c, double *dst, long long c0, long long c1) {
+  cudaError_t e = c->fp64 ? rtg::launch_dmom_out<double>((const double *)c->dMom, dst, c->N, c0, c1 - c0, c->stream)
+                          : rtg::launch_dmom_out<float>((const float *)c->dMom, dst, c->N, c0, c1 - c0, c->stream);
   return e == cudaSuccess ? RT_OK : cuda_fail(e, "convert");
 }
 
@@ -195,6 +226,73 @@ rt_status delivered(rt_ctx *c) {
 rt_status deliver(rt_ctx *c, const double *src, double *dst, long long n) {
   rt_status st = deliver_async(c, src, dst, n);
   return st != RT_OK ? st : delivered(c);
+}
+
+}  // namespace
+
+namespace {
+
+// Copy streams and events of rt_step_coupled, made on first use (kept in the
+// context as they are made, so free_all releases a partial set too).
+rt_status coupled_init(rt_ctx *c) {
+  if (c->xs_in && c->xs_out && c->ev_done[rt_ctx::kSlabs - 1]) return RT_OK;
+  if (!c->xs_in) RT_CUDA(cudaStreamCreateWithFlags(&c->xs_in, cudaStreamNonBlocking));
+  if (!c->xs_out) RT_CUDA(cudaStreamCreateWithFlags(&c->xs_out, cudaStreamNonBlocking));
+  if (!c->ev_start) RT_CUDA(cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming));
+  for (int k = 0; k < rt_ctx::kSlabs; ++k) {
+    if (!c->ev_in[k]) RT_CUDA(cudaEventCreateWithFlags(&c->ev_in[k], cudaEventDisableTiming));
+    if (!c->ev_done[k]) RT_CUDA(cudaEventCreateWithFlags(&c->ev_done[k], cudaEventDisableTiming));
+  }
+  return RT_OK;
+}
+
+// Fields of the cells [c0, c1) to the staging buffer (copy stream), in the
+// layout rt_set_material uses: rho, T, v (3 components), sigma_a, sigma_s.
+rt_status coupled_in(rt_ctx *c, const double *const f[5], long long c0, long long c1) {
+  const long long N = c->N, n = c1 - c0;
+  const size_t b = n * sizeof(double);
+  const double *src[7] = {f[0], f[1], f[2], f[2] + N, f[2] + 2 * N, f[3], f[4]};
+  for (int k = 0; k < 7; ++k)
+    RT_CUDA(cudaMemcpyAsync(c->stage + k * N + c0, src[k] + c0, b, cudaMemcpyHostToDevice, c->xs_in));
+  return RT_OK;
+}
+
+// Sources of the cells [c0, c1) back to the caller: Delta(rho v) converted
+// on the context stream into the staging buffer's last 3N doubles, then all
+// three fields copied on the outgoing stream once ev (recorded after the
+// conversion) has fired.
+rt_status coupled_out(rt_ctx *c, long long c0, long long c1, cudaEvent_t ev, double *dE_gas, double *dMom,
+                      double *T_new) {
+  const long long N = c->N, n = c1 - c0;
+  double *s_mom = c->stage + 7 * N;
+  rt_status st;
+  if (dMom && (st = dmom_out(c, s_mom, c0, c1)) != RT_OK) return st;
+  RT_CUDA(cudaEventRecord(ev, c->stream));
+  RT_CUDA(cudaStreamWaitEvent(c->xs_out, ev, 0));
+  const size_t b = n * sizeof(double);
+  if (dE_gas) RT_CUDA(cudaMemcpyAsync(dE_gas + c0, c->dEgas + c0, b, cudaMemcpyDeviceToHost, c->xs_out));
+  if (dMom)
+    for (int i = 0; i < 3; ++i)
+      RT_CUDA(cudaMemcpyAsync(dMom + i * N + c0, s_mom + i * N + c0, b, cudaMemcpyDeviceToHost, c->xs_out));
+  if (T_new) RT_CUDA(cudaMemcpyAsync(T_new + c0, c->T + c0, b, cudaMemcpyDeviceToHost, c->xs_out));
+  return RT_OK;
+}
+
+// The step's kernel over tile layers [l0, l1) along z (all layers: l1 = 0).
+rt_status coupled_launch(rt_ctx *c, double dt, bool vel, int l0, int l1) {
+  cudaError_t e;
+  if (c->fp64) {
+    rtg::StepArgs<double> a = rtg::make_args<double>(c, dt);
+    a.tz_begin = l0;
+    a.tz_count = l1 - l0;
+    e = rtg::launch_step<double>(a, c->dim, vel, c->tile, c->stream);
+  } else {
+    rtg::StepArgs<float> a = rtg::make_args<float>(c, dt);
+    a.tz_begin = l0;
+    a.tz_count = l1 - l0;
+    e = rtg::launch_step<float>(a, c->dim, vel, c->tile, c->stream);
+  }
+  return e == cudaSuccess ? RT_OK : cuda_fail(e, "step kernel launch");
 }
 
 }  // namespace
@@ -362,20 +460,12 @@ rt_status rt_set_material(rt_ctx *c, const double *rho, const double *T, const d
   if ((st = fetch(c, ss, s_ss, N)) != RT_OK) return st;
   // scan: bit 0 = a value out of range or non-finite, bit 1 = some v != 0
   RT_CUDA(cudaMemsetAsync(c->flags + 1, 0, sizeof(int), c->stream));
-  RT_CUDA(rtg::launch_check(s_rho, N, 0.0, 1, 0, c->flags + 1, c->stream));
-  RT_CUDA(rtg::launch_check(s_T, N, 0.0, 1, 0, c->flags + 1, c->stream));
-  RT_CUDA(rtg::launch_check(s_sa, N, 0.0, 0, 0, c->flags + 1, c->stream));
-  RT_CUDA(rtg::launch_check(s_ss, N, 0.0, 0, 0, c->flags + 1, c->stream));
-  RT_CUDA(rtg::launch_check(s_v, 3 * N, -INFINITY, 0, 2, c->flags + 1, c->stream));
+  if ((st = fields_in(c, 0, N, false)) != RT_OK) return st;
   int flag = 0;
   RT_CUDA(cudaMemcpyAsync(&flag, c->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   RT_CUDA(cudaStreamSynchronize(c->stream));
   if (flag & 1) return fail(RT_E_NONFINITE, "rt_set_material: need finite rho > 0, T > 0, sigma >= 0, v");
-  if ((st = convert_in(c, s_rho, c->rho, N)) != RT_OK) return st;
-  if ((st = convert_in(c, s_sa, c->sa, N)) != RT_OK) return st;
-  if ((st = convert_in(c, s_ss, c->ss, N)) != RT_OK) return st;
-  if ((st = convert_in(c, s_v, c->v, 3 * N)) != RT_OK) return st;
-  RT_CUDA(cudaMemcpyAsync(c->T, s_T, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  if ((st = fields_in(c, 0, N, true)) != RT_OK) return st;
   c->has_v = (flag & 2) != 0;
   c->material_set = true;
   if (!c->intensity_set) return rt_set_intensity(c, nullptr);
@@ -748,11 +838,101 @@ rt_status rt_sources(rt_ctx *c, double *dE_gas, double *dMom, double *T_new) {
   // the energy source and T are double on the device: copied out directly
   if (dE_gas && (st = deliver_async(c, c->dEgas, dE_gas, N)) != RT_OK) return st;
   if (dMom) {
-    if ((st = convert_out(c, c->dMom, c->stage, 3 * N)) != RT_OK) return st;
+    if ((st = dmom_out(c, c->stage, 0, N)) != RT_OK) return st;
     if ((st = deliver_async(c, c->stage, dMom, 3 * N)) != RT_OK) return st;
   }
   if (T_new && (st = deliver_async(c, c->T, T_new, N)) != RT_OK) return st;
   return delivered(c);
+}
+
+rt_status rt_step_coupled(rt_ctx *c, double dt, const double *rho, const double *T, const double *v,
+                          const double *sa, const double *ss, double *dE_gas, double *dMom, double *T_new) {
+  rtg::Range nvtx_range("rt_step_coupled");
+  if (!c) return fail(RT_E_INVALID, "rt_step_coupled: NULL context");
+  if (!rho || !T || !v || !sa || !ss) return fail(RT_E_INVALID, "rt_step_coupled: NULL field");
+  if (c->batch) return fail(RT_E_STATE, "rt_step_coupled: the context belongs to a batch");
+  const int nz = c->n[2], TZ = std::max(1, c->tile.tz), layers = (nz + TZ - 1) / TZ;
+  if (c->dim != 3 || c->opt.device_ptrs || c->bf16 || !c->material_set || !c->intensity_set || layers < 2 ||
+      c->stage_len < 10 * c->N) {
+    // the three calls in turn
+    rt_status st = rt_set_material(c, rho, T, v, sa, ss);
+    if (st == RT_E_NONFINITE) c->material_set = false;
+    if (st == RT_OK) st = rt_step(c, dt);
+    if (st == RT_OK) st = rt_sources(c, dE_gas, dMom, T_new);
+    return st;
+  }
+  if (!(dt > 0)) dt = rt_cfl_dt(c);
+  if (!std::isfinite(dt)) return fail(RT_E_INVALID, "rt_step_coupled: dt not finite");
+  rt_status st = coupled_init(c);
+  if (st != RT_OK) return st;
+  const long long Nxy = (long long)c->n[0] * c->n[1];
+  const int S = std::min(rt_ctx::kSlabs, layers);
+  int L[rt_ctx::kSlabs + 1], e[rt_ctx::kSlabs];   // slab s: tile layers [L[s], L[s+1]), planes up to e[s]
+  // Thin first and last slabs: nothing overlaps the first slab's fields
+  // going over or the last slab's sources coming back.
+  const int thin = S >= 3 ? std::max(1, layers / 16) : 0;
+  L[0] = 0;
+  L[S] = layers;
+  if (thin) {
+    L[1] = thin;
+    L[S - 1] = layers - thin;
+    for (int s = 2; s < S - 1; ++s) L[s] = thin + (int)((long long)(layers - 2 * thin) * (s - 1) / (S - 2));
+  } else {
+    for (int s = 1; s < S; ++s) L[s] = (int)((long long)layers * s / S);
+  }
+  for (int s = 0; s < S; ++s) e[s] = std::min(L[s + 1] * TZ, nz);
+  // A slab reads the fields of two planes beyond its own on each side.  The
+  // planes go over in order, each once: slab s needs those below
+  // min(top, e[s] + 2), and the top planes [top, nz) go first, for slab 0's
+  // periodic wrap.
+  const int top = std::min(nz, std::max(nz - 2, e[0] + 2));
+  const double *f[5] = {rho, T, v, sa, ss};
+  // the staging buffer and the outputs are free once the context's stream
+  // reaches this point
+  RT_CUDA(cudaEventRecord(c->ev_start, c->stream));
+  RT_CUDA(cudaStreamWaitEvent(c->xs_in, c->ev_start, 0));
+  RT_CUDA(cudaStreamWaitEvent(c->xs_out, c->ev_start, 0));
+  // the Newton-failure count of earlier steps, restored if the fields fail
+  // (cells stepped with bad fields must not count against the next rt_sync)
+  int failures = 0;
+  RT_CUDA(cudaMemcpyAsync(&failures, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  RT_CUDA(cudaMemsetAsync(c->flags + 1, 0, sizeof(int), c->stream));
+  const bool vel = rtg::velocity_on(c);   // kernel of the previous fields; checked below
+  int sent = 0;
+  for (int s = 0; s < S; ++s) {
+    const int upto = std::min(top, e[s] + 2);
+    if (s == 0 && top < nz && (st = coupled_in(c, f, top * Nxy, nz * Nxy)) != RT_OK) return st;
+    if (upto > sent && (st = coupled_in(c, f, sent * Nxy, upto * Nxy)) != RT_OK) return st;
+    RT_CUDA(cudaEventRecord(c->ev_in[s], c->xs_in));
+    RT_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in[s], 0));
+    if (s == 0 && top < nz && (st = fields_in(c, top * Nxy, nz * Nxy, true)) != RT_OK) return st;
+    if (upto > sent && (st = fields_in(c, sent * Nxy, upto * Nxy, true)) != RT_OK) return st;
+    sent = std::max(sent, upto);
+    if ((st = coupled_launch(c, dt, vel, L[s], L[s + 1])) != RT_OK) return st;
+    const long long c0 = (long long)L[s] * TZ * Nxy, c1 = (long long)e[s] * Nxy;
+    if ((st = coupled_out(c, c0, c1, c->ev_done[s], dE_gas, dMom, T_new)) != RT_OK) return st;
+  }
+  int flag = 0;
+  RT_CUDA(cudaMemcpyAsync(&flag, c->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  RT_CUDA(cudaStreamSynchronize(c->stream));
+  RT_CUDA(cudaStreamSynchronize(c->xs_out));
+  if (flag & 1) {
+    // T was stepped in place and the fields are partly new: neither is usable
+    c->material_set = false;
+    RT_CUDA(cudaMemcpy(c->flags, &failures, sizeof(int), cudaMemcpyHostToDevice));
+    return fail(RT_E_NONFINITE, "rt_step_coupled: need finite rho > 0, T > 0, sigma >= 0, v");
+  }
+  c->has_v = (flag & 2) != 0;
+  if (rtg::velocity_on(c) != vel) {
+    // the fields switched the velocity terms on or off: step again from the
+    // staged T with the other kernel
+    RT_CUDA(cudaMemcpyAsync(c->T, c->stage + c->N, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    if ((st = coupled_launch(c, dt, !vel, 0, 0)) != RT_OK) return st;
+    c->cur = 1 - c->cur;
+    return rt_sources(c, dE_gas, dMom, T_new);
+  }
+  c->cur = 1 - c->cur;
+  return RT_OK;
 }
 
 rt_status rt_get_intensity(rt_ctx *c, double *I) {

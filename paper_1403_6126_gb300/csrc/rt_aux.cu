@@ -98,10 +98,81 @@ __global__ void check_kernel(const double *__restrict__ x, long long n, double l
     if (!isfinite(v) || (strict ? !(v > lo) : !(v >= lo))) bits |= 1;
     if (v != 0.0) bits |= nzbit;
   }
-  if (bits) atomicOr(flag, bits);
+  // one atomic per block: an atomic per thread on the one flag word would
+  // serialize (nearly every thread sets the nonzero bit of a velocity field)
+  const int bad = __syncthreads_or(bits & 1), nonzero = __syncthreads_or(bits & nzbit);
+  if (threadIdx.x == 0 && (bad || nonzero)) atomicOr(flag, (bad ? 1 : 0) | (nonzero ? nzbit : 0));
+}
+
+// Gas fields staged as doubles (stage: rho, T, v_x, v_y, v_z, sigma_a,
+// sigma_s, N each), cells [c0, c0 + n): bit 0 of *flag for a value out of
+// range (rho, T > 0; sigma >= 0; all finite), bit 1 for a nonzero velocity;
+// with CONVERT also the context's arrays (Real, T in double).
+template <typename Real, bool CONVERT>
+__global__ void fields_in_kernel(const double *__restrict__ stage, long long N, long long c0, long long n,
+                                 Real *__restrict__ rho, Real *__restrict__ sa, Real *__restrict__ ss,
+                                 Real *__restrict__ v, double *__restrict__ T, int *flag) {
+  int bits = 0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const long long i = c0 + k;
+    const double r = stage[i], t = stage[N + i], vx = stage[2 * N + i], vy = stage[3 * N + i],
+                 vz = stage[4 * N + i], a = stage[5 * N + i], s = stage[6 * N + i];
+    if (!(isfinite(r) && r > 0.0 && isfinite(t) && t > 0.0 && isfinite(a) && a >= 0.0 && isfinite(s) &&
+          s >= 0.0 && isfinite(vx) && isfinite(vy) && isfinite(vz)))
+      bits |= 1;
+    if (vx != 0.0 || vy != 0.0 || vz != 0.0) bits |= 2;
+    if (CONVERT) {
+      rho[i] = (Real)r;
+      sa[i] = (Real)a;
+      ss[i] = (Real)s;
+      v[i] = (Real)vx;
+      v[N + i] = (Real)vy;
+      v[2 * N + i] = (Real)vz;
+      T[i] = t;
+    }
+  }
+  const int bad = __syncthreads_or(bits & 1), nonzero = __syncthreads_or(bits & 2);
+  if (threadIdx.x == 0 && (bad || nonzero)) atomicOr(flag, (bad ? 1 : 0) | (nonzero ? 2 : 0));
+}
+
+// The three components of Delta(rho v) of cells [c0, c0 + n) to double.
+template <typename Real>
+__global__ void dmom_out_kernel(const Real *__restrict__ dMom, double *__restrict__ dst, long long N, long long c0,
+                                long long n) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const long long i = c0 + k;
+    dst[i] = (double)dMom[i];
+    dst[N + i] = (double)dMom[N + i];
+    dst[2 * N + i] = (double)dMom[2 * N + i];
+  }
 }
 
 }  // namespace
+
+template <typename Real>
+cudaError_t launch_fields_in(const double *stage, long long N, long long c0, long long n, bool convert, Real *rho,
+                             Real *sa, Real *ss, Real *v, double *T, int *flag, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (convert)
+    fields_in_kernel<Real, true><<<grid_for(n, 256), 256, 0, s>>>(stage, N, c0, n, rho, sa, ss, v, T, flag);
+  else
+    fields_in_kernel<Real, false><<<grid_for(n, 256), 256, 0, s>>>(stage, N, c0, n, rho, sa, ss, v, T, flag);
+  return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_dmom_out(const Real *dMom, double *dst, long long N, long long c0, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  dmom_out_kernel<Real><<<grid_for(n, 256), 256, 0, s>>>(dMom, dst, N, c0, n);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_fields_in<float>(const double *, long long, long long, long long, bool, float *, float *,
+                                             float *, float *, double *, int *, cudaStream_t);
+template cudaError_t launch_fields_in<double>(const double *, long long, long long, long long, bool, double *,
+                                              double *, double *, double *, double *, int *, cudaStream_t);
+template cudaError_t launch_dmom_out<float>(const float *, double *, long long, long long, long long, cudaStream_t);
+template cudaError_t launch_dmom_out<double>(const double *, double *, long long, long long, long long, cudaStream_t);
 
 template <typename Real>
 cudaError_t launch_convert_in(const double *src, Real *dst, long long n, cudaStream_t s) {

@@ -45,6 +45,10 @@ struct StepArgs {
   const unsigned short *I16_in;
   unsigned short *I16_out;
   float *Q;
+  // The launch covers tile layers [tz_begin, tz_begin + tz_count) along z
+  // (tz_count = 0: every layer).  Tiles are independent within a step, so a
+  // grid stepped in z-slabs gives bitwise the whole-grid result.
+  int tz_begin, tz_count;
 };
 
 struct TileShape {
@@ -95,5 +99,15 @@ cudaError_t launch_decode_b16(const unsigned short *in, const float *E, double *
 // Scans n doubles: ORs bit 0 into *flag for a non-finite value or one below
 // `lo` (or equal to it when strict), and ORs `nzbit` for a nonzero value.
 cudaError_t launch_check(const double *x, long long n, double lo, int strict, int nzbit, int *flag, cudaStream_t s);
+// Scan of the gas fields staged as doubles (stage: rho, T, v_x, v_y, v_z,
+// sigma_a, sigma_s, N each) over cells [c0, c0 + n) into *flag (bit 0: a
+// value out of range, bit 1: some v != 0); with convert also the copy into
+// the context's arrays (rho, sigma_a, sigma_s, v in Real; T in double).
+template <typename Real>
+cudaError_t launch_fields_in(const double *stage, long long N, long long c0, long long n, bool convert, Real *rho,
+                             Real *sa, Real *ss, Real *v, double *T, int *flag, cudaStream_t s);
+// Delta(rho v) of cells [c0, c0 + n), all three components, to double.
+template <typename Real>
+cudaError_t launch_dmom_out(const Real *dMom, double *dst, long long N, long long c0, long long n, cudaStream_t s);
 
 }  // namespace rtg
