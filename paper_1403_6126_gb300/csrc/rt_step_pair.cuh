@@ -608,13 +608,17 @@ __device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid,
   for (int i = 0; i < 6; ++i) mP[i].zero();
   float *out = (B16 ? a.Q : a.I_out) + c;
   const float rJ = b16_inv(s2);   // s2 = sum W I^{n+1}: the new mean intensity (bf16 storage)
+  // Q of the next pair is loaded before this pair's I^{n+1} is stored over
+  // its own Q (different addresses), so the L2 latency overlaps a pair's work
+  f2 Qn = make_float2(out[0], M > 1 ? out[N] : 0.0f);
 #pragma unroll 2
   for (int k = 0; k < K; ++k) {
     const f2 *t = s_tab + kTab2 * k;
     const f2 nx = t[0], ny = t[1], nz = t[2], Wm = t[3];
     const int m = 2 * k;
     const bool second = m + 1 < M;
-    const f2 Q = make_float2(out[(long long)m * N], second ? out[(long long)(m + 1) * N] : 0.0f);
+    const f2 Q = Qn;
+    if (k + 1 < K) Qn = make_float2(out[(long long)(m + 2) * N], m + 3 < M ? out[(long long)(m + 3) * N] : 0.0f);
     f2 vn = dup(0.0f), rd = dup(rd0), ra = dup(ra0);
     if (VEL) {
       vn = p_fma(nx, dup(vt[0]), p_fma(ny, dup(vt[1]), p_mul(nz, dup(vt[2]))));
