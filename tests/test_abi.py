@@ -113,7 +113,8 @@ def test_create_validates_before_touching_the_device():
 
 def test_null_context_calls_are_rejected():
     for fn in (lambda: rt.rt_step(None, 0.1), lambda: rt.rt_sync(None), lambda: rt.rt_run(None, 0.1, 2),
-               lambda: rt.rt_set_intensity(None, None)):
+               lambda: rt.rt_set_intensity(None, None),
+               lambda: rt.rt_step_coupled(None, 0.1, *([np.ones(4)] * 5), None, None, None)):
         with pytest.raises(rt.RTError) as e:
             fn()
         assert e.value.status == rt.RT_E_INVALID
