@@ -216,11 +216,12 @@ rt_status rt_sources(rt_ctx *ctx, double *dE_gas, double *dMom, double *T_new);
  * MHD update between steps is the caller's): rt_set_material(rho, T, v,
  * sigma_a, sigma_s), rt_step(dt), rt_sources(dE_gas, dMom, T_new) in one
  * call, with the same arguments, results and errors (bitwise the same
- * outputs and state).  For a 3-D context with host arrays the grid is cut
- * into z-slabs of whole tiles: the fields of a slab (and its two-plane
- * halo) cross to the device while the previous slab steps, and the sources
- * of a slab cross back while the next one steps.  Other contexts (1-D, 2-D,
- * device_ptrs, bf16 storage, the first call) run the three calls in turn.
+ * outputs and state).  With host arrays the grid is cut into slabs of
+ * whole tiles along its outermost active axis (z in 3-D, y in 2-D, x in
+ * 1-D): the fields of a slab (and its two-plane halo) cross to the device
+ * while the previous slab steps, and the sources of a slab cross back while
+ * the next one steps.  Other contexts (device_ptrs, bf16 storage, grids of
+ * one tile layer, the first call) run the three calls in turn.
  * T_new may be T (the next step's temperature); no other output may
  * overlap an input.  Waits for the transfers.  On RT_E_NONFINITE /
  * RT_E_INVALID from the fields the intensity is unchanged and the gas

@@ -127,8 +127,8 @@ rtg::StepArgs<Real> rtg::make_args(rt_ctx *c, double dt) {
   a.dEgas = c->dEgas;
   a.dMom = (Real *)c->dMom;
   a.status = c->flags;
-  a.tz_begin = 0;
-  a.tz_count = 0;
+  a.outer_begin = 0;
+  a.outer_count = 0;
   return a;
 }
 
@@ -283,13 +283,13 @@ rt_status coupled_launch(rt_ctx *c, double dt, bool vel, int l0, int l1) {
   cudaError_t e;
   if (c->fp64) {
     rtg::StepArgs<double> a = rtg::make_args<double>(c, dt);
-    a.tz_begin = l0;
-    a.tz_count = l1 - l0;
+    a.outer_begin = l0;
+    a.outer_count = l1 - l0;
     e = rtg::launch_step<double>(a, c->dim, vel, c->tile, c->stream);
   } else {
     rtg::StepArgs<float> a = rtg::make_args<float>(c, dt);
-    a.tz_begin = l0;
-    a.tz_count = l1 - l0;
+    a.outer_begin = l0;
+    a.outer_count = l1 - l0;
     e = rtg::launch_step<float>(a, c->dim, vel, c->tile, c->stream);
   }
   return e == cudaSuccess ? RT_OK : cuda_fail(e, "step kernel launch");
@@ -851,8 +851,13 @@ rt_status rt_step_coupled(rt_ctx *c, double dt, const double *rho, const double 
   if (!c) return fail(RT_E_INVALID, "rt_step_coupled: NULL context");
   if (!rho || !T || !v || !sa || !ss) return fail(RT_E_INVALID, "rt_step_coupled: NULL field");
   if (c->batch) return fail(RT_E_STATE, "rt_step_coupled: the context belongs to a batch");
-  const int nz = c->n[2], TZ = std::max(1, c->tile.tz), layers = (nz + TZ - 1) / TZ;
-  if (c->dim != 3 || c->opt.device_ptrs || c->bf16 || !c->material_set || !c->intensity_set || layers < 2 ||
+  // slabs along the outermost active axis (z in 3-D, y in 2-D, x in 1-D);
+  // a "plane" is the set of cells with one coordinate along it
+  const int d_out = std::max(0, c->dim - 1);
+  const int nz = c->n[d_out];
+  const int TZ = std::max(1, d_out == 2 ? c->tile.tz : d_out == 1 ? c->tile.ty : c->tile.tx);
+  const int layers = (nz + TZ - 1) / TZ;
+  if (c->opt.device_ptrs || c->bf16 || !c->material_set || !c->intensity_set || layers < 2 ||
       c->stage_len < 10 * c->N) {
     // the three calls in turn
     rt_status st = rt_set_material(c, rho, T, v, sa, ss);
@@ -865,7 +870,8 @@ rt_status rt_step_coupled(rt_ctx *c, double dt, const double *rho, const double 
   if (!std::isfinite(dt)) return fail(RT_E_INVALID, "rt_step_coupled: dt not finite");
   rt_status st = coupled_init(c);
   if (st != RT_OK) return st;
-  const long long Nxy = (long long)c->n[0] * c->n[1];
+  long long Nxy = 1;   // cells per plane
+  for (int d = 0; d < d_out; ++d) Nxy *= c->n[d];
   const int S = std::min(rt_ctx::kSlabs, layers);
   int L[rt_ctx::kSlabs + 1], e[rt_ctx::kSlabs];   // slab s: tile layers [L[s], L[s+1]), planes up to e[s]
   // Thin first and last slabs: nothing overlaps the first slab's fields

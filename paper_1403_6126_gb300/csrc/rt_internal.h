@@ -45,10 +45,11 @@ struct StepArgs {
   const unsigned short *I16_in;
   unsigned short *I16_out;
   float *Q;
-  // The launch covers tile layers [tz_begin, tz_begin + tz_count) along z
-  // (tz_count = 0: every layer).  Tiles are independent within a step, so a
-  // grid stepped in z-slabs gives bitwise the whole-grid result.
-  int tz_begin, tz_count;
+  // The launch covers tile layers [outer_begin, outer_begin + outer_count)
+  // along the outermost active axis (z in 3-D, y in 2-D, x in 1-D;
+  // outer_count = 0: every layer).  Tiles are independent within a step, so
+  // a grid stepped in slabs gives bitwise the whole-grid result.
+  int outer_begin, outer_count;
 };
 
 struct TileShape {

@@ -190,8 +190,8 @@ extern "C" rt_status rt_step_noalloc(const rt_grid *g, const rt_angles *ang, dou
   a.I16_in = nullptr;
   a.I16_out = nullptr;
   a.Q = nullptr;
-  a.tz_begin = 0;
-  a.tz_count = 0;
+  a.outer_begin = 0;
+  a.outer_count = 0;
   e = g->dim == 1   ? rtg::launch_noalloc<1, 512, 1, 1>(a, counter, s)
       : g->dim == 2 ? rtg::launch_noalloc<2, 32, 16, 1>(a, counter, s)
                     : rtg::launch_noalloc<3, 16, 8, 4>(a, counter, s);

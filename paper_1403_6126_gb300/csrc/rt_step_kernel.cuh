@@ -752,7 +752,9 @@ __device__ __forceinline__ void process_tile(const StepArgs<Real> &a, int tid, i
 template <typename Real, int DIM, bool VEL, int TX, int TY, int TZ>
 __global__ void __launch_bounds__(TX * TY * TZ) step_kernel(const StepArgs<Real> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  process_tile<Real, DIM, VEL, TX, TY, TZ>(a, threadIdx.x, blockIdx.x, blockIdx.y, a.tz_begin + blockIdx.z, smem_raw);
+  const int o = a.outer_begin;
+  process_tile<Real, DIM, VEL, TX, TY, TZ>(a, threadIdx.x, blockIdx.x + (DIM == 1 ? o : 0),
+                                           blockIdx.y + (DIM == 2 ? o : 0), blockIdx.z + (DIM == 3 ? o : 0), smem_raw);
 }
 
 template <typename Real, int DIM, bool VEL, int TX, int TY, int TZ>
@@ -762,7 +764,8 @@ cudaError_t launch_shape(const StepArgs<Real> &a, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   dim3 block(TX * TY * TZ);
-  dim3 grid((a.n[0] + TX - 1) / TX, (a.n[1] + TY - 1) / TY, a.tz_count > 0 ? a.tz_count : (a.n[2] + TZ - 1) / TZ);
+  dim3 grid((a.n[0] + TX - 1) / TX, (a.n[1] + TY - 1) / TY, (a.n[2] + TZ - 1) / TZ);
+  if (a.outer_count > 0) (DIM == 3 ? grid.z : DIM == 2 ? grid.y : grid.x) = a.outer_count;
   kern<<<grid, block, sm, s>>>(a);
   return cudaGetLastError();
 }

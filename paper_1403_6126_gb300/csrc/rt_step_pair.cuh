@@ -682,7 +682,9 @@ __device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid,
 template <int DIM, bool VEL, int TX, int TY, int TZ, bool B16 = false>
 __global__ void __launch_bounds__(TX * TY * TZ, 1) step_kernel2(const StepArgs<float> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  process_tile2<DIM, VEL, TX, TY, TZ, B16>(a, threadIdx.x, blockIdx.x, blockIdx.y, a.tz_begin + blockIdx.z, smem_raw);
+  const int o = a.outer_begin;
+  process_tile2<DIM, VEL, TX, TY, TZ, B16>(a, threadIdx.x, blockIdx.x + (DIM == 1 ? o : 0),
+                                           blockIdx.y + (DIM == 2 ? o : 0), blockIdx.z + (DIM == 3 ? o : 0), smem_raw);
 }
 
 template <int DIM, bool VEL, int TX, int TY, int TZ, bool B16 = false>
@@ -692,7 +694,8 @@ cudaError_t launch_shape2(const StepArgs<float> &a, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   dim3 block(TX * TY * TZ);
-  dim3 grid((a.n[0] + TX - 1) / TX, (a.n[1] + TY - 1) / TY, a.tz_count > 0 ? a.tz_count : (a.n[2] + TZ - 1) / TZ);
+  dim3 grid((a.n[0] + TX - 1) / TX, (a.n[1] + TY - 1) / TY, (a.n[2] + TZ - 1) / TZ);
+  if (a.outer_count > 0) (DIM == 3 ? grid.z : DIM == 2 ? grid.y : grid.x) = a.outer_count;
   kern<<<grid, block, sm, s>>>(a);
   return cudaGetLastError();
 }

@@ -1,6 +1,6 @@
 """rt_step_coupled: the gas-coupling loop (fields in, one step, sources out)
-in one call, with the transfers of one z-slab overlapping the step of the
-next.  Every output and the state afterwards are bitwise those of
+in one call, with the transfers of one slab of the grid overlapping the
+step of the next.  Every output and the state afterwards are bitwise those of
 rt_set_material + rt_step + rt_sources."""
 import numpy as np
 import pytest
@@ -116,9 +116,23 @@ def test_coupled_first_call_and_small_grids_fall_back():
     a.close(); b.close()
 
 
-def test_coupled_2d_falls_back():
-    wl = wlmod.box2d(n=48, angles="s4", steps=0)
-    _assert_same(*_run_pair(wl, "fp32", 2))
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_coupled_2d_slabs_along_y(precision):
+    # 2-D: slabs of tile rows along y (periodic, so slab 0 reads the top rows)
+    wl = wlmod.box2d(n=80, angles="s4", steps=0)
+    _assert_same(*_run_pair(wl, precision, 3))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_coupled_1d_slabs_along_x(precision):
+    # 1-D: slabs of tiles along x, open ends (copy below, vacuum above)
+    wl = wlmod.slab1d(n=3000, M=16, steps=0)
+    wl["hold_T"] = False
+
+    def fields(wl, k, T):
+        return [wl["rho"] * (1.0 + 0.01 * k), T, wl["v"], wl["sa"], wl["ss"]]
+
+    _assert_same(*_run_pair(wl, precision, 3, fields))
 
 
 def test_coupled_bad_field_leaves_intensity():
