@@ -120,12 +120,27 @@ __global__ void moments_kernel_f(const float *__restrict__ I, const float *__res
   }
 }
 
+// Range tests on the IEEE-754 bit pattern u of a double, in integer
+// arithmetic (FP64 compares run at GB300's low FP64 rate): the finite
+// values are the patterns with |u| below that of +infinity; the positive
+// ones are 0 < u below +infinity; the non-negative ones add -0.
+constexpr unsigned long long kInfBits = 0x7FF0000000000000ull, kAbsMask = 0x7FFFFFFFFFFFFFFFull,
+                             kNegZero = 0x8000000000000000ull;
+__device__ __forceinline__ unsigned long long bits_of(double x) { return (unsigned long long)__double_as_longlong(x); }
+__device__ __forceinline__ bool finite_bits(unsigned long long u) { return (u & kAbsMask) < kInfBits; }
+__device__ __forceinline__ bool positive_bits(unsigned long long u) { return u - 1ull < kInfBits - 1ull; }
+__device__ __forceinline__ bool nonneg_bits(unsigned long long u) { return u < kInfBits || u == kNegZero; }
+
 __global__ void check_kernel(const double *__restrict__ x, long long n, double lo, int strict, int nzbit, int *flag) {
   int bits = 0;
+  const bool zero_lo = lo == 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double v = x[i];
-    if (!isfinite(v) || (strict ? !(v > lo) : !(v >= lo))) bits |= 1;
-    if (v != 0.0) bits |= nzbit;
+    const double v = x[i];
+    const unsigned long long u = bits_of(v);
+    const bool ok = zero_lo ? (strict ? positive_bits(u) : nonneg_bits(u))
+                            : (finite_bits(u) && (strict ? v > lo : v >= lo));
+    if (!ok) bits |= 1;
+    if ((u & kAbsMask) != 0) bits |= nzbit;
   }
   // one atomic per block: an atomic per thread on the one flag word would
   // serialize (nearly every thread sets the nonzero bit of a velocity field)
@@ -146,10 +161,11 @@ __global__ void fields_in_kernel(const double *__restrict__ stage, long long N, 
     const long long i = c0 + k;
     const double r = stage[i], t = stage[N + i], vx = stage[2 * N + i], vy = stage[3 * N + i],
                  vz = stage[4 * N + i], a = stage[5 * N + i], s = stage[6 * N + i];
-    if (!(isfinite(r) && r > 0.0 && isfinite(t) && t > 0.0 && isfinite(a) && a >= 0.0 && isfinite(s) &&
-          s >= 0.0 && isfinite(vx) && isfinite(vy) && isfinite(vz)))
+    const unsigned long long ux = bits_of(vx), uy = bits_of(vy), uz = bits_of(vz);
+    if (!(positive_bits(bits_of(r)) && positive_bits(bits_of(t)) && nonneg_bits(bits_of(a)) &&
+          nonneg_bits(bits_of(s)) && finite_bits(ux) && finite_bits(uy) && finite_bits(uz)))
       bits |= 1;
-    if (vx != 0.0 || vy != 0.0 || vz != 0.0) bits |= 2;
+    if (((ux | uy | uz) & kAbsMask) != 0) bits |= 2;
     if (CONVERT) {
       rho[i] = (Real)r;
       sa[i] = (Real)a;
