@@ -334,6 +334,7 @@ def run_gpu(args):
         small = bench_small(stream)
     if world == 1 and not args.no_accuracy:
         accuracy = bench_accuracy(stream)
+        accuracy["box3d_128_500_steps"] = bench_accuracy_box500(stream)
     if world == 1 and not args.no_bf16:
         bf16 = bench_bf16(args, stream)
     if world == 1 and not args.no_batch:
@@ -508,6 +509,65 @@ def bench_small(stream):
                     "working_set_mb": bpc / 1e6, "tile": "x".join(str(v) for v in c.tile()), "autotune": tuned,
                     "note": "working set fits in L2 (126 MB): a bandwidth fraction here is an L2 figure"}
         c.close()
+    return out
+
+
+def _stated_sample(name):
+    """The oracle's stored values after a workload's full step count
+    (tests/golden/stated_<name>.txt, written by make_stated_steps.py from the
+    oracle alone): (dt, steps, scales, cells, E, F[3, k]), or None."""
+    path = os.path.join(ROOT, "tests", "golden", "stated_%s.txt" % name)
+    if not os.path.exists(path):
+        return None
+    scal, rows = {}, []
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            parts = line.split()
+            if len(parts) == 2:
+                scal[parts[0]] = float(parts[1])
+            else:
+                rows.append([float(x) for x in parts])
+    a = np.array(rows)
+    return scal["dt"], int(scal["steps"]), scal, a[:, 0].astype(np.int64), a[:, 1], a[:, 2:5].T
+
+
+def bench_accuracy_box500(stream):
+    """The timed workload (box3d 128^3 x 80, float32-rounded inputs) after its
+    full 500 steps in FP64 and float: E_r and |F_r| at the oracle's stored
+    sample of cells, and float against FP64 over the whole grid."""
+    from paper_1403_6126_gb300 import workloads as wlmod
+    ref = _stated_sample("box3d")
+    if ref is None:
+        return None
+    dt, steps, scal, cells, Eo, Fo = ref
+    wl = wlmod.rounded_to_float32(wlmod.box3d(n=128))
+    n, w = _angles(wl["angles"])
+    I0 = wlmod.initial_intensity(wl, len(w)).astype(np.float32).astype(np.float64)
+    Fo_abs = np.sqrt((Fo ** 2).sum(axis=0))
+    F_scale = max(scal["F_max"], 1e-3 * scal["E_max"])
+    out = {"workload": "box3d 128^3 x 80, 500 steps, float32-rounded inputs; sample: %d cells of the oracle's "
+                       "stored values (tests/golden/stated_box3d.txt)" % len(cells)}
+    full = {}
+    for prec in ("fp64", "fp32"):
+        c = _context(wl, n, w, stream=stream.cuda_stream, precision=prec)
+        c.set_intensity(I0)
+        c.set_material(wl["rho"], wl["T"], wl["v"], wl["sa"], wl["ss"])
+        c.run(dt, steps)
+        c.sync()
+        E, F, _ = c.moments()
+        c.close()
+        Fa = np.sqrt((F ** 2).sum(axis=0))
+        full[prec] = (E, Fa)
+        out[prec] = {"E_r": float(np.abs(E[cells] - Eo).max() / scal["E_max"]),
+                     "abs_F_r": float(np.abs(Fa[cells] - Fo_abs).max() / F_scale),
+                     "sum_E_r": float(abs(E.sum() - scal["E_sum"]) / scal["E_sum"])}
+    (E64, F64), (E32, F32) = full["fp64"], full["fp32"]
+    out["fp32_vs_fp64_whole_grid"] = {
+        "E_r": float(np.abs(E32 - E64).max() / np.abs(E64).max()),
+        "abs_F_r": float(np.abs(F32 - F64).max() / max(F64.max(), 1e-3 * np.abs(E64).max())),
+        "cells_E_over_1e-5": int((np.abs(E32 - E64) > 1e-5 * np.abs(E64).max()).sum())}
     return out
 
 
