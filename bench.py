@@ -219,6 +219,27 @@ def cpu_baseline(wl_name, steps, warmup, sample_n=None):
                 seconds=el)
 
 
+def arm_config(args, world):
+    """The workload's description on the JSON line, the same for both arms:
+    grid, angles, precision, whether T and the velocity terms are live, the
+    CFL time step (cfl * min dx / Crat, sec. 4.1) and the L2 note."""
+    from paper_1403_6126_gb300 import workloads as wlmod
+    wl = wlmod.by_name(args.workload, **({"n": args.n} if args.workload == "box3d" and args.n else {}))
+    name = wl["angles"]
+    M = int(name[2:]) if name.startswith("gl") else int(name[1:]) * (int(name[1:]) + 2)
+    N = int(np.prod(wl["shape"]))
+    dims = [wl["shape"][2 - d] for d in range(wl["dim"])]
+    dt = wl["cfl"] * min((wl["hi"][d] - wl["lo"][d]) / dims[d] for d in range(wl["dim"])) / wl["C"]
+    velocity = bool(np.any(wl["v"] != 0)) or wl["estimate_v"]
+    rs = 8 if wl["precision"] == "fp64" else 4
+    return {"workload": "%s: %s cells x %d angles (%s), %s intensities, T live=%s, velocity=%s"
+                        % (wl["name"], "x".join(str(s) for s in wl["shape"][::-1]), M, wl["angles"],
+                           wl["precision"], not wl["hold_T"], velocity),
+            "cells": N, "angles": M, "dt": dt,
+            "l2": "inputs larger than L2: %.2f GB of intensity read per step" % (N * M * rs / 1e9),
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -229,7 +250,7 @@ def run_reference(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * res["seconds"] / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "sample": res["sample"]},
+        "config": arm_config(args, world),
         "cpu_baseline": {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")},
         "e2e": {"value": res["value"], "unit": res["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -347,16 +368,13 @@ def run_gpu(args):
         cpu = cpu_baseline(args.workload, 2, 1, sample_n=max(args.cpu_sample_n, 48))
         cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
     if rank == 0:
+        config = arm_config(args, world)
+        assert config["cells"] == N and config["angles"] == M and abs(config["dt"] - dt) <= 1e-15 * dt
         line = {
             "metric": "cell-angle updates/s", "value": value, "unit": "cell-angle updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if rs == 4 else "f64", "data": "synthetic",
-            "config": {"workload": "%s: %s cells x %d angles (%s), %s intensities, T live=%s, velocity=%s"
-                                   % (wl["name"], "x".join(str(s) for s in wl["shape"][::-1]), M, wl["angles"],
-                                      wl["precision"], not wl["hold_T"], velocity),
-                       "cells": N, "angles": M, "dt": dt,
-                       "l2": "inputs larger than L2: %.2f GB of intensity read per step" % (N * M * rs / 1e9),
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": config,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
             "accuracy_vs_oracle": accuracy, "bf16_storage": bf16,
             "small_configs": small, "batched": batched, "serving": serving,
