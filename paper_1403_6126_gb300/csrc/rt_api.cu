@@ -63,13 +63,14 @@ namespace {
 
 void free_all(rt_ctx *c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
-  for (cudaStream_t s : {c->xs_in, c->xs_out}) {
+  for (cudaStream_t s : {c->xs_in, c->xs_cv, c->xs_out}) {
     if (!s) continue;
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
   }
   if (c->ev_start) cudaEventDestroy(c->ev_start);
   for (int k = 0; k < rt_ctx::kSlabs; ++k) {
+    if (c->ev_copied[k]) cudaEventDestroy(c->ev_copied[k]);
     if (c->ev_in[k]) cudaEventDestroy(c->ev_in[k]);
     if (c->ev_done[k]) cudaEventDestroy(c->ev_done[k]);
   }
@@ -165,20 +166,20 @@ rt_status convert_in(rt_ctx *c, const double *src, void *dst, long long n) {
 
 // Scan (and with convert, conversion into the context's arrays) of the gas
 // fields staged in c->stage, cells [c0, c1); flag bits go to c->flags[1].
-rt_status fields_in(rt_ctx *c, long long c0, long long c1, bool convert) {
+rt_status fields_in(rt_ctx *c, long long c0, long long c1, bool convert, cudaStream_t s) {
   cudaError_t e = c->fp64 ? rtg::launch_fields_in<double>(c->stage, c->N, c0, c1 - c0, convert, (double *)c->rho,
                                                           (double *)c->sa, (double *)c->ss, (double *)c->v, c->T,
-                                                          c->flags + 1, c->stream)
+                                                          c->flags + 1, s)
                           : rtg::launch_fields_in<float>(c->stage, c->N, c0, c1 - c0, convert, (float *)c->rho,
                                                          (float *)c->sa, (float *)c->ss, (float *)c->v, c->T,
-                                                         c->flags + 1, c->stream);
+                                                         c->flags + 1, s);
   return e == cudaSuccess ? RT_OK : cuda_fail(e, "fields");
 }
 
 // Delta(rho v) of cells [c0, c1), three components, into dst (double, 3N).
-rt_status dmom_out(rt_ctx *c, double *dst, long long c0, long long c1) {
-  cudaError_t e = c->fp64 ? rtg::launch_dmom_out<double>((const double *)c->dMom, dst, c->N, c0, c1 - c0, c->stream)
-                          : rtg::launch_dmom_out<float>((const float *)c->dMom, dst, c->N, c0, c1 - c0, c->stream);
+rt_status dmom_out(rt_ctx *c, double *dst, long long c0, long long c1, cudaStream_t s) {
+  cudaError_t e = c->fp64 ? rtg::launch_dmom_out<double>((const double *)c->dMom, dst, c->N, c0, c1 - c0, s)
+                          : rtg::launch_dmom_out<float>((const float *)c->dMom, dst, c->N, c0, c1 - c0, s);
   return e == cudaSuccess ? RT_OK : cuda_fail(e, "convert");
 }
 
@@ -235,11 +236,13 @@ namespace {
 // Copy streams and events of rt_step_coupled, made on first use (kept in the
 // context as they are made, so free_all releases a partial set too).
 rt_status coupled_init(rt_ctx *c) {
-  if (c->xs_in && c->xs_out && c->ev_done[rt_ctx::kSlabs - 1]) return RT_OK;
+  if (c->xs_in && c->xs_out && c->xs_cv && c->ev_done[rt_ctx::kSlabs - 1]) return RT_OK;
   if (!c->xs_in) RT_CUDA(cudaStreamCreateWithFlags(&c->xs_in, cudaStreamNonBlocking));
   if (!c->xs_out) RT_CUDA(cudaStreamCreateWithFlags(&c->xs_out, cudaStreamNonBlocking));
+  if (!c->xs_cv) RT_CUDA(cudaStreamCreateWithFlags(&c->xs_cv, cudaStreamNonBlocking));
   if (!c->ev_start) RT_CUDA(cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming));
   for (int k = 0; k < rt_ctx::kSlabs; ++k) {
+    if (!c->ev_copied[k]) RT_CUDA(cudaEventCreateWithFlags(&c->ev_copied[k], cudaEventDisableTiming));
     if (!c->ev_in[k]) RT_CUDA(cudaEventCreateWithFlags(&c->ev_in[k], cudaEventDisableTiming));
     if (!c->ev_done[k]) RT_CUDA(cudaEventCreateWithFlags(&c->ev_done[k], cudaEventDisableTiming));
   }
@@ -258,15 +261,16 @@ rt_status coupled_in(rt_ctx *c, const double *const f[5], long long c0, long lon
 }
 
 // Sources of the cells [c0, c1) back to the caller: Delta(rho v) converted
-// on the context stream into the staging buffer's last 3N doubles, then all
-// three fields copied on the outgoing stream once ev (recorded after the
-// conversion) has fired.
+// on the context stream (right after the slab: on another stream the
+// conversion would wait for SMs until the next slab's tail) into the
+// staging buffer's last 3N doubles, then all three fields copied on the
+// outgoing stream once ev (recorded after the conversion) has fired.
 rt_status coupled_out(rt_ctx *c, long long c0, long long c1, cudaEvent_t ev, double *dE_gas, double *dMom,
                       double *T_new) {
   const long long N = c->N, n = c1 - c0;
   double *s_mom = c->stage + 7 * N;
   rt_status st;
-  if (dMom && (st = dmom_out(c, s_mom, c0, c1)) != RT_OK) return st;
+  if (dMom && (st = dmom_out(c, s_mom, c0, c1, c->stream)) != RT_OK) return st;
   RT_CUDA(cudaEventRecord(ev, c->stream));
   RT_CUDA(cudaStreamWaitEvent(c->xs_out, ev, 0));
   const size_t b = n * sizeof(double);
@@ -460,12 +464,12 @@ rt_status rt_set_material(rt_ctx *c, const double *rho, const double *T, const d
   if ((st = fetch(c, ss, s_ss, N)) != RT_OK) return st;
   // scan: bit 0 = a value out of range or non-finite, bit 1 = some v != 0
   RT_CUDA(cudaMemsetAsync(c->flags + 1, 0, sizeof(int), c->stream));
-  if ((st = fields_in(c, 0, N, false)) != RT_OK) return st;
+  if ((st = fields_in(c, 0, N, false, c->stream)) != RT_OK) return st;
   int flag = 0;
   RT_CUDA(cudaMemcpyAsync(&flag, c->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   RT_CUDA(cudaStreamSynchronize(c->stream));
   if (flag & 1) return fail(RT_E_NONFINITE, "rt_set_material: need finite rho > 0, T > 0, sigma >= 0, v");
-  if ((st = fields_in(c, 0, N, true)) != RT_OK) return st;
+  if ((st = fields_in(c, 0, N, true, c->stream)) != RT_OK) return st;
   c->has_v = (flag & 2) != 0;
   c->material_set = true;
   if (!c->intensity_set) return rt_set_intensity(c, nullptr);
@@ -838,7 +842,7 @@ rt_status rt_sources(rt_ctx *c, double *dE_gas, double *dMom, double *T_new) {
   // the energy source and T are double on the device: copied out directly
   if (dE_gas && (st = deliver_async(c, c->dEgas, dE_gas, N)) != RT_OK) return st;
   if (dMom) {
-    if ((st = dmom_out(c, c->stage, 0, N)) != RT_OK) return st;
+    if ((st = dmom_out(c, c->stage, 0, N, c->stream)) != RT_OK) return st;
     if ((st = deliver_async(c, c->stage, dMom, 3 * N)) != RT_OK) return st;
   }
   if (T_new && (st = deliver_async(c, c->T, T_new, N)) != RT_OK) return st;
@@ -893,26 +897,31 @@ rt_status rt_step_coupled(rt_ctx *c, double dt, const double *rho, const double 
   // periodic wrap.
   const int top = std::min(nz, std::max(nz - 2, e[0] + 2));
   const double *f[5] = {rho, T, v, sa, ss};
-  // the staging buffer and the outputs are free once the context's stream
-  // reaches this point
-  RT_CUDA(cudaEventRecord(c->ev_start, c->stream));
-  RT_CUDA(cudaStreamWaitEvent(c->xs_in, c->ev_start, 0));
-  RT_CUDA(cudaStreamWaitEvent(c->xs_out, c->ev_start, 0));
   // the Newton-failure count of earlier steps, restored if the fields fail
   // (cells stepped with bad fields must not count against the next rt_sync)
   int failures = 0;
   RT_CUDA(cudaMemcpyAsync(&failures, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   RT_CUDA(cudaMemsetAsync(c->flags + 1, 0, sizeof(int), c->stream));
+  // the staging buffer, the outputs and the scan flag are free once the
+  // context's stream reaches this point
+  RT_CUDA(cudaEventRecord(c->ev_start, c->stream));
+  RT_CUDA(cudaStreamWaitEvent(c->xs_in, c->ev_start, 0));
+  RT_CUDA(cudaStreamWaitEvent(c->xs_cv, c->ev_start, 0));
+  RT_CUDA(cudaStreamWaitEvent(c->xs_out, c->ev_start, 0));
   const bool vel = rtg::velocity_on(c);   // kernel of the previous fields; checked below
   int sent = 0;
   for (int s = 0; s < S; ++s) {
     const int upto = std::min(top, e[s] + 2);
     if (s == 0 && top < nz && (st = coupled_in(c, f, top * Nxy, nz * Nxy)) != RT_OK) return st;
     if (upto > sent && (st = coupled_in(c, f, sent * Nxy, upto * Nxy)) != RT_OK) return st;
-    RT_CUDA(cudaEventRecord(c->ev_in[s], c->xs_in));
+    // scan and convert on their own stream as the planes arrive, so that a
+    // chunk's conversion can run in the tail of the previous slab
+    RT_CUDA(cudaEventRecord(c->ev_copied[s], c->xs_in));
+    RT_CUDA(cudaStreamWaitEvent(c->xs_cv, c->ev_copied[s], 0));
+    if (s == 0 && top < nz && (st = fields_in(c, top * Nxy, nz * Nxy, true, c->xs_cv)) != RT_OK) return st;
+    if (upto > sent && (st = fields_in(c, sent * Nxy, upto * Nxy, true, c->xs_cv)) != RT_OK) return st;
+    RT_CUDA(cudaEventRecord(c->ev_in[s], c->xs_cv));
     RT_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in[s], 0));
-    if (s == 0 && top < nz && (st = fields_in(c, top * Nxy, nz * Nxy, true)) != RT_OK) return st;
-    if (upto > sent && (st = fields_in(c, sent * Nxy, upto * Nxy, true)) != RT_OK) return st;
     sent = std::max(sent, upto);
     if ((st = coupled_launch(c, dt, vel, L[s], L[s + 1])) != RT_OK) return st;
     const long long c0 = (long long)L[s] * TZ * Nxy, c1 = (long long)e[s] * Nxy;

@@ -41,11 +41,12 @@ struct rt_ctx {
   int graph_steps = 0, graph_cur = -1;
   bool graph_vel = false;
   void *batch = nullptr;  // the rt_batch this context belongs to, if any
-  // rt_step_coupled: copy streams (fields in, sources out) and the events
-  // that order them against the slab launches, made on first use
+  // rt_step_coupled: copy streams (fields in, sources out), a stream for the
+  // field conversions, and the events that order them against the slab
+  // launches, made on first use
   static constexpr int kSlabs = 4;
-  cudaStream_t xs_in = nullptr, xs_out = nullptr;
-  cudaEvent_t ev_start = nullptr, ev_in[kSlabs] = {}, ev_done[kSlabs] = {};
+  cudaStream_t xs_in = nullptr, xs_out = nullptr, xs_cv = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_copied[kSlabs] = {}, ev_in[kSlabs] = {}, ev_done[kSlabs] = {};
 };
 
 #include <nvtx3/nvToolsExt.h>
