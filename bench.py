@@ -355,7 +355,6 @@ def run_gpu(args):
         small = bench_small(stream)
     if world == 1 and not args.no_accuracy:
         accuracy = bench_accuracy(stream)
-        accuracy["box3d_128_500_steps"] = bench_accuracy_box500(stream)
     if world == 1 and not args.no_bf16:
         bf16 = bench_bf16(args, stream)
     if world == 1 and not args.no_batch:
@@ -551,24 +550,44 @@ def _stated_sample(name):
     return scal["dt"], int(scal["steps"]), scal, a[:, 0].astype(np.int64), a[:, 1], a[:, 2:5].T
 
 
-def bench_accuracy_box500(stream):
-    """The timed workload (box3d 128^3 x 80, float32-rounded inputs) after its
-    full 500 steps in FP64 and float: E_r and |F_r| at the oracle's stored
-    sample of cells, and float against FP64 over the whole grid."""
+def _stated_workload(name):
+    """The inputs the stored oracle values were computed from (float32-rounded
+    fields; see tests/golden/make_stated_steps.py)."""
     from paper_1403_6126_gb300 import workloads as wlmod
-    ref = _stated_sample("box3d")
+    if name == "serving_req8":
+        base = wlmod.serving_request(8)
+    else:
+        base = wlmod.by_name(name, **({"n": 128} if name == "box3d" else {}))
+    return wlmod.rounded_to_float32(base)
+
+
+def _stated_errors(E, F, ref, dim):
+    """E_r, |F_r| (active axes) at the stored cells and sum E_r, against the
+    oracle's stored values."""
+    _, _, scal, cells, Eo, Fo = ref
+    Fo_abs = np.sqrt((Fo[:dim] ** 2).sum(axis=0))
+    Fg = np.sqrt((F[:dim, cells] ** 2).sum(axis=0))
+    return {"E_r": float(np.abs(E[cells] - Eo).max() / scal["E_max"]),
+            "abs_F_r": float(np.abs(Fg - Fo_abs).max() / max(scal["F_max"], 1e-3 * scal["E_max"])),
+            "sum_E_r": float(abs(E.sum() - scal["E_sum"]) / scal["E_sum"])}
+
+
+def _stated_case(stream, name, precisions):
+    """One workload after its full step count in each precision, against the
+    oracle's stored sample; float against FP64 over the whole grid too."""
+    from paper_1403_6126_gb300 import workloads as wlmod
+    ref = _stated_sample(name)
     if ref is None:
         return None
-    dt, steps, scal, cells, Eo, Fo = ref
-    wl = wlmod.rounded_to_float32(wlmod.box3d(n=128))
+    dt, steps = ref[0], ref[1]
+    wl = _stated_workload(name)
     n, w = _angles(wl["angles"])
     I0 = wlmod.initial_intensity(wl, len(w)).astype(np.float32).astype(np.float64)
-    Fo_abs = np.sqrt((Fo ** 2).sum(axis=0))
-    F_scale = max(scal["F_max"], 1e-3 * scal["E_max"])
-    out = {"workload": "box3d 128^3 x 80, 500 steps, float32-rounded inputs; sample: %d cells of the oracle's "
-                       "stored values (tests/golden/stated_box3d.txt)" % len(cells)}
+    dim = wl["dim"]
+    out = {"workload": "%s %s x %d angles, %d steps; %d stored cells" % (
+        name, "x".join(str(s) for s in wl["shape"][::-1] if s > 1), len(w), steps, len(ref[3]))}
     full = {}
-    for prec in ("fp64", "fp32"):
+    for prec in precisions:
         c = _context(wl, n, w, stream=stream.cuda_stream, precision=prec)
         c.set_intensity(I0)
         c.set_material(wl["rho"], wl["T"], wl["v"], wl["sa"], wl["ss"])
@@ -576,86 +595,25 @@ def bench_accuracy_box500(stream):
         c.sync()
         E, F, _ = c.moments()
         c.close()
-        Fa = np.sqrt((F ** 2).sum(axis=0))
-        full[prec] = (E, Fa)
-        out[prec] = {"E_r": float(np.abs(E[cells] - Eo).max() / scal["E_max"]),
-                     "abs_F_r": float(np.abs(Fa[cells] - Fo_abs).max() / F_scale),
-                     "sum_E_r": float(abs(E.sum() - scal["E_sum"]) / scal["E_sum"])}
-    (E64, F64), (E32, F32) = full["fp64"], full["fp32"]
-    out["fp32_vs_fp64_whole_grid"] = {
-        "E_r": float(np.abs(E32 - E64).max() / np.abs(E64).max()),
-        "abs_F_r": float(np.abs(F32 - F64).max() / max(F64.max(), 1e-3 * np.abs(E64).max())),
-        "cells_E_over_1e-5": int((np.abs(E32 - E64) > 1e-5 * np.abs(E64).max()).sum())}
+        full[prec] = (E, np.sqrt((F[:dim] ** 2).sum(axis=0)))
+        out[prec] = _stated_errors(E, F, ref, dim)
+    if "fp64" in full and "fp32" in full:
+        (E64, F64), (E32, F32) = full["fp64"], full["fp32"]
+        out["fp32_vs_fp64_whole_grid"] = {
+            "E_r": float(np.abs(E32 - E64).max() / np.abs(E64).max()),
+            "abs_F_r": float(np.abs(F32 - F64).max() / max(F64.max(), 1e-3 * np.abs(E64).max())),
+            "cells_E_over_1e-5": int((np.abs(E32 - E64) > 1e-5 * np.abs(E64).max()).sum())}
     return out
 
 
-def bench_accuracy(stream, n=32, steps=10):
-    """Error against the FP64 oracle of every GPU precision on a sample of
-    the timed workload: the box3d recipe at n^3 x 80 angles, `steps` steps
-    from identical (float-rounded) inputs.  Norm-relative errors of E_r,
-    |F_r| (against max E_r where the flux is round-off) and T."""
-    import oracle
-    from paper_1403_6126_gb300 import workloads as wlmod
-    wl = wlmod.rounded_to_float32(wlmod.box3d(n=n, steps=steps))
-    nn, w = oracle.angles.by_name(wl["angles"])
-    I0 = wlmod.initial_intensity(wl, len(w)).astype(np.float32).astype(np.float64)
-    dx = tuple((wl["hi"][d] - wl["lo"][d]) / wl["shape"][2 - d] for d in range(3))
-    p = oracle.Problem(wl["shape"], dx, nn, w, C=wl["C"], P=wl["P"], dim=3, bc=wl["bc"], gamma=wl["gamma"],
-                       R=wl["R"], hold_T=wl["hold_T"], estimate_v=wl["estimate_v"])
-    oracle.set_threads(os.cpu_count() or 1)
-    dt = oracle.cfl_dt(p, wl["cfl"])
-    o = oracle.run(p, dt, steps, I0, wl["T"], wl["rho"], wl["v"], wl["sa"], wl["ss"])
-    dim = wl["dim"]   # |F_r| over the active axes (a slab set carries a by-product F_y)
-    Fo = np.sqrt((o["F"][:dim] ** 2).sum(axis=0))
-    out = {"workload": "box3d recipe at %d^3 x %d angles, %d steps, FP64 oracle on the host" % (n, len(w), steps)}
-    out["slab1d_512x8_2000_steps"] = _accuracy_case(stream, wlmod.slab1d(), 2000, ("fp64", "fp32"))
-    out["shadow2d_64x32x80_200_steps"] = _accuracy_case(stream, wlmod.shadow2d(nx=64, ny=32), 200,
-                                                        ("fp64", "fp32", "bf16"))
-    for prec in ("fp64", "fp32", "bf16"):
-        c = _context(wl, nn, w, stream=stream.cuda_stream, precision=prec)
-        c.set_intensity(I0)
-        c.set_material(wl["rho"], wl["T"], wl["v"], wl["sa"], wl["ss"])
-        c.run(dt, steps)
-        c.sync()
-        E, F, _ = c.moments()
-        _, _, T = c.sources()
-        c.close()
-        Fg = np.sqrt((F[:dim] ** 2).sum(axis=0))
-        out[prec] = {"E_r": float(np.abs(E - o["E"]).max() / np.abs(o["E"]).max()),
-                     "abs_F_r": float(np.abs(Fg - Fo).max() / max(Fo.max(), 1e-3 * np.abs(o["E"]).max())),
-                     "T": float(np.abs(T - o["T"]).max() / np.abs(o["T"]).max())}
-    return out
-
-
-def _accuracy_case(stream, wl, steps, precisions):
-    """Norm-relative errors of E_r and |F_r| of each precision against the
-    FP64 oracle after `steps` steps of a small workload."""
-    import oracle
-    from paper_1403_6126_gb300 import workloads as wlmod
-    wl = wlmod.rounded_to_float32(wl)
-    nn, w = oracle.angles.by_name(wl["angles"])
-    I0 = wlmod.initial_intensity(wl, len(w)).astype(np.float32).astype(np.float64)
-    dx = tuple((wl["hi"][d] - wl["lo"][d]) / wl["shape"][2 - d] for d in range(3))
-    inflow = {face: wlmod.inflow_values(rule, nn) for face, rule in wl["inflow"].items()}
-    p = oracle.Problem(wl["shape"], dx, nn, w, C=wl["C"], P=wl["P"], dim=wl["dim"], bc=wl["bc"], inflow=inflow,
-                       gamma=wl["gamma"], R=wl["R"], hold_T=wl["hold_T"], estimate_v=wl["estimate_v"])
-    dt = oracle.cfl_dt(p, wl["cfl"])
-    o = oracle.run(p, dt, steps, I0, wl["T"], wl["rho"], wl["v"], wl["sa"], wl["ss"])
-    dim = wl["dim"]   # |F_r| over the active axes (a slab set carries a by-product F_y)
-    Fo = np.sqrt((o["F"][:dim] ** 2).sum(axis=0))
-    out = {}
-    for prec in precisions:
-        c = _context(wl, nn, w, stream=stream.cuda_stream, precision=prec)
-        c.set_intensity(I0)
-        c.set_material(wl["rho"], wl["T"], wl["v"], wl["sa"], wl["ss"])
-        c.run(dt, steps)
-        c.sync()
-        E, F, _ = c.moments()
-        c.close()
-        Fg = np.sqrt((F[:dim] ** 2).sum(axis=0))
-        out[prec] = {"E_r": float(np.abs(E - o["E"]).max() / np.abs(o["E"]).max()),
-                     "abs_F_r": float(np.abs(Fg - Fo).max() / max(Fo.max(), 1e-3 * np.abs(o["E"]).max()))}
-    return out
+def bench_accuracy(stream):
+    """The error of every GPU precision against the FP64 oracle after the full
+    step count of each workload, at the oracle's stored sample of cells
+    (tests/golden/stated_*.txt: written by tests/golden/make_stated_steps.py
+    from the oracle alone; nothing here runs the oracle)."""
+    return {"slab1d_512x8_2000_steps": _stated_case(stream, "slab1d", ("fp64", "fp32")),
+            "shadow2d_256x128x80_4000_steps": _stated_case(stream, "shadow2d", ("fp64", "fp32", "bf16")),
+            "box3d_128x80_500_steps": _stated_case(stream, "box3d", ("fp64", "fp32", "bf16"))}
 
 
 def bench_bf16(args, stream):
@@ -709,16 +667,19 @@ def _submit_args(wl, angles=None):
     return g, a, (n, w), fields
 
 
-def _serving_accuracy(wl, opts, budget_gb):
-    """E_r and |F_r| of one request served (through the server) and solved by
-    the FP64 path alone, each against the FP64 oracle on the host; the
-    request's fields are float32-rounded so all three see the same inputs."""
-    import oracle
+def _serving_accuracy(opts, budget_gb):
+    """Request 8 of the serving stream (96^2 box2d, 24 angles, 200 steps,
+    float32-rounded fields) served through the server (float) and solved
+    alone by the FP64 path, each against the oracle's stored sample
+    (tests/golden/stated_serving_req8.txt)."""
     import paper_1403_6126_gb300 as rt
-    from paper_1403_6126_gb300 import workloads as wlmod
-    wl = wlmod.rounded_to_float32(wl)
-    g, a, (nn, w), f = _submit_args(wl, oracle.angles.by_name(wl["angles"]))   # the oracle's own angle set
-    N, M, steps, dim = int(np.prod(wl["shape"])), len(w), wl["steps"], wl["dim"]
+    ref = _stated_sample("serving_req8")
+    if ref is None:
+        return None
+    dt, steps = ref[0], ref[1]
+    wl = _stated_workload("serving_req8")
+    g, a, (nn, w), f = _submit_args(wl)
+    N, dim = int(np.prod(wl["shape"])), wl["dim"]
     server = rt.rt_server_create(int(budget_gb * 2 ** 30), opts)
     try:
         t = rt.rt_submit(server, g, a, wl["C"], wl["P"], *f, steps)
@@ -729,27 +690,13 @@ def _serving_accuracy(wl, opts, budget_gb):
         rt.rt_server_destroy(server)
     c = _context(wl, nn, w, precision="fp64")
     c.set_material(*f)
-    c.run(0.0, steps)
+    c.run(dt, steps)
     c.sync()
     E64, F64, _ = c.moments()
     c.close()
-    dx = tuple((wl["hi"][d] - wl["lo"][d]) / wl["shape"][2 - d] for d in range(3))
-    p = oracle.Problem(wl["shape"], dx, nn, w, C=wl["C"], P=wl["P"], dim=dim, bc=wl["bc"], gamma=wl["gamma"],
-                       R=wl["R"], hold_T=wl["hold_T"], estimate_v=wl["estimate_v"])
-    oracle.set_threads(os.cpu_count() or 1)
-    o = oracle.run(p, oracle.cfl_dt(p, wl["cfl"]), steps, wlmod.initial_intensity(wl, M), wl["T"], wl["rho"],
-                   wl["v"], wl["sa"], wl["ss"])
-    Fo = np.sqrt((o["F"][:dim] ** 2).sum(axis=0))
-    Emax = np.abs(o["E"]).max()
-
-    def err(E, F):
-        Fg = np.sqrt((F[:dim] ** 2).sum(axis=0))
-        return {"E_r": float(np.abs(E - o["E"]).max() / Emax),
-                "abs_F_r": float(np.abs(Fg - Fo).max() / max(Fo.max(), 1e-3 * Emax))}
-
-    return {"request": "%s %s x %d angles, %d steps" % (wl["name"], "x".join(str(s) for s in wl["shape"][::-1] if s > 1),
-                                                      M, steps),
-            "served_fp32": err(Es, Fs), "fp64_one_at_a_time": err(E64, F64)}
+    return {"request": "serving request 8: %s x %d angles, %d steps; %d stored cells"
+                       % ("x".join(str(s) for s in wl["shape"][::-1] if s > 1), len(w), steps, len(ref[3])),
+            "served_fp32": _stated_errors(Es, Fs, ref, dim), "fp64_one_at_a_time": _stated_errors(E64, F64, ref, dim)}
 
 
 def bench_serving(args):
@@ -821,9 +768,8 @@ def bench_serving(args):
         c.close()
     fp64_s = time.perf_counter() - t0
     fp64_rate = len(reqs) / (fp64_s * sum(work) / sum(work[:k]))
-    # both paths against the oracle on the smallest 2-D request of the stream
-    i2 = min((i for i, wl in enumerate(wls) if wl["dim"] == 2), key=lambda i: work[i])
-    accuracy = _serving_accuracy(wls[i2], o, args.serve_budget_gb)
+    # both paths against the oracle's stored values for one request
+    accuracy = _serving_accuracy(o, args.serve_budget_gb)
     return {"workload": "%d requests: 2-D 64..512^2 and 3-D 64..192^3 (sides in steps of 32), 24/80 angles, %d steps each, box gas fields; "
                         "Poisson arrivals at 0.8 x measured capacity" % (len(reqs), args.serve_steps),
             "value": (len(reqs) - failed[1]) / makespan, "unit": "solves/s", "p50_latency_s": float(np.percentile(lat, 50)),

@@ -1,7 +1,8 @@
 """Writes the FP64 oracle's E_r and F_r after the full step count of each
 single-problem workload (the 1-D slab: 2000 steps, the 2-D shadow problem:
-4000 steps, the 3-D box: 500 steps), at full size, for
-tests/test_gpu_stated_steps.py.
+4000 steps, the 3-D box: 500 steps), at full size, and of request 8 of the
+serving stream (a 96^2 box2d problem with 24 angles, 200 steps), for
+tests/test_gpu_stated_steps.py and the accuracy report of bench.py.
 
 Only the CPU oracle (oracle/) computes anything here; the inputs come from
 the seeded generators of paper_1403_6126_gb300.workloads, rounded to float32
@@ -11,7 +12,7 @@ scales max E_r, max |F_r| (over the active axes) and sum E_r, and E_r, F_r
 at a seeded sample of cells (every cell of the slab) plus the cells of
 largest and smallest E_r and of largest |F_r|.
 
-usage: python tests/golden/make_stated_steps.py [slab1d] [shadow2d] [box3d]
+usage: python tests/golden/make_stated_steps.py [slab1d] [shadow2d] [box3d] [serving_req8]
 (the box takes a few CPU-hours on eight cores; the others minutes)
 """
 import os
@@ -32,13 +33,16 @@ CASES = {
     "slab1d": (dict(), 2000, None),
     "shadow2d": (dict(), 4000, 600),
     "box3d": (dict(n=128), 500, 600),
+    "serving_req8": (dict(index=8), 200, 600),
 }
 
 
 def inputs(name):
     """The float32-rounded workload, its angle set, I0 and the oracle problem."""
     kw, steps, _ = CASES[name]
-    wl = wlmod.rounded_to_float32(wlmod.by_name(name, **kw))
+    base = wlmod.serving_request(**kw) if name.startswith("serving") else wlmod.by_name(name, **kw)
+    assert base.get("steps", steps) == steps
+    wl = wlmod.rounded_to_float32(base)
     n, w = oracle.angles.by_name(wl["angles"])
     I0 = wlmod.initial_intensity(wl, len(w)).astype(np.float32).astype(np.float64)
     dx = tuple((wl["hi"][d] - wl["lo"][d]) / wl["shape"][2 - d] for d in range(3))

@@ -1,9 +1,10 @@
 """Each single-problem workload at full size after its full step count (the
-1-D slab 2000 steps, the 2-D shadow problem 4000, the 3-D box 500) against
-the FP64 oracle's values stored by tests/golden/make_stated_steps.py: the
-FP64 path within 1e-12, the float path within 1e-5 on E_r and |F_r| (over
-the active axes, at the stored sample of cells, relative to the whole-grid
-maxima), and the total radiation energy within the same bounds."""
+1-D slab 2000 steps, the 2-D shadow problem 4000, the 3-D box 500) and
+request 8 of the serving stream (200 steps) against the FP64 oracle's
+values stored by tests/golden/make_stated_steps.py: the FP64 path within
+1e-12, the float path within 1e-5 on E_r and |F_r| (over the active axes,
+at the stored sample of cells, relative to the whole-grid maxima), and the
+total radiation energy within the same bounds."""
 import os
 import sys
 
@@ -48,7 +49,7 @@ def stated_errors(name, precision):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("name", ["slab1d", "shadow2d", "box3d"])
+@pytest.mark.parametrize("name", ["slab1d", "shadow2d", "box3d", "serving_req8"])
 def test_full_step_count_matches_oracle(name, precision):
     err = stated_errors(name, precision)
     tol = TOL_FLOAT_SLAB if (name, precision) == ("slab1d", "fp32") else TOL[precision]
