@@ -688,7 +688,11 @@ def _serving_accuracy(opts, budget_gb):
         rt.rt_poll(server, t, Es, Fs, None)
     finally:
         rt.rt_server_destroy(server)
+    # the oracle (like the float server) started from the float32-rounded
+    # equilibrium 1/(4 pi): the FP64 path gets the same start
+    from paper_1403_6126_gb300 import workloads as wlmod
     c = _context(wl, nn, w, precision="fp64")
+    c.set_intensity(wlmod.initial_intensity(wl, len(w)).astype(np.float32).astype(np.float64))
     c.set_material(*f)
     c.run(dt, steps)
     c.sync()
