@@ -1,0 +1,45 @@
+"""Host-side logic of bench.py (no GPU): the workload description both arms
+print, and the reading and scoring of the oracle's stored samples."""
+import os
+import sys
+import types
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_arm_config_describes_the_timed_box():
+    cfg = bench.arm_config(types.SimpleNamespace(workload="box3d", n=0), 1)
+    assert cfg["cells"] == 128 ** 3 and cfg["angles"] == 80
+    # sec. 4.1 Step 1: dt = CFL min dx / Crat with CFL 0.4, dx = 1/128, Crat = 100
+    assert abs(cfg["dt"] - 0.4 / 128 / 100) <= 1e-18
+    assert "128x128x128" in cfg["workload"] and cfg["parallelism"] == "single GPU"
+    assert bench.arm_config(types.SimpleNamespace(workload="box3d", n=0), 4)["parallelism"] == "replicas"
+
+
+def test_arm_config_other_workloads():
+    slab = bench.arm_config(types.SimpleNamespace(workload="slab1d", n=0), 1)
+    assert slab["cells"] == 512 and slab["angles"] == 8
+    shadow = bench.arm_config(types.SimpleNamespace(workload="shadow2d", n=0), 1)
+    assert shadow["cells"] == 256 * 128 and shadow["angles"] == 80
+
+
+def test_stated_samples_read_and_score():
+    for name in ("slab1d", "shadow2d", "box3d", "serving_req8"):
+        ref = bench._stated_sample(name)
+        assert ref is not None, name
+        dt, steps, scal, cells, Eo, Fo = ref
+        wl = bench._stated_workload(name)
+        N = int(np.prod(wl["shape"]))
+        assert steps > 0 and dt > 0 and cells.max() < N and Fo.shape == (3, len(cells))
+        assert scal["E_max"] >= np.abs(Eo).max() and scal["E_sum"] > 0
+        E, F = np.zeros(N), np.zeros((3, N))
+        E[cells], F[:, cells] = Eo, Fo
+        err = bench._stated_errors(E, F, ref, wl["dim"])
+        assert err["E_r"] == 0.0 and err["abs_F_r"] == 0.0
+        E[cells[0]] += 1e-6 * scal["E_max"]
+        assert abs(bench._stated_errors(E, F, ref, wl["dim"])["E_r"] - 1e-6) < 1e-12
