@@ -424,7 +424,7 @@ def _e2e(ctx, wl, N, M, stream, args, world):
     return {"value": whole_job_rate(N * M * k, world, el), "unit": "cell-angle updates/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "steps": k, "ms_per_step": 1e3 * el / k,
             "transfers": "rt_step_coupled: rho, T, v, sigma_a, sigma_s in, dE_gas, dMom, T_new out, pinned doubles, "
-                         "every step, overlapped with the step in z-slabs",
+                         "every step, overlapped with the step slab by slab",
             "three_calls": {"value": whole_job_rate(N * M * k3, world, el3), "ms_per_step": 1e3 * el3 / k3,
                             "calls": "rt_set_material, rt_step, rt_sources"}}
 
