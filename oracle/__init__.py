@@ -43,6 +43,7 @@ class _Problem(ctypes.Structure):
         ("M", ctypes.c_int), ("mu", ctypes.POINTER(ctypes.c_double)), ("w", ctypes.POINTER(ctypes.c_double)),
         ("C", ctypes.c_double), ("P", ctypes.c_double), ("gamma", ctypes.c_double), ("R", ctypes.c_double),
         ("hold_T", ctypes.c_int), ("estimate_v", ctypes.c_int), ("dense", ctypes.c_int),
+        ("alpha_one", ctypes.c_int),
     ]
 
 
@@ -92,7 +93,7 @@ class Problem:
     """
 
     def __init__(self, shape, dx, n, w, C, P, dim=None, bc=None, inflow=None, gamma=5.0 / 3.0, R=1.0,
-                 hold_T=False, estimate_v=False, dense=False):
+                 hold_T=False, estimate_v=False, dense=False, alpha_one=False):
         nz, ny, nx = shape
         self.shape = (nz, ny, nx)
         self.dim = dim if dim is not None else (3 if nz > 1 else (2 if ny > 1 else 1))
@@ -120,6 +121,9 @@ class Problem:
         s.mu, s.w = _ptr(self.n_ang), _ptr(self.w)
         s.C, s.P, s.gamma, s.R = self.C, self.P, self.gamma, self.R
         s.hold_T, s.estimate_v, s.dense = int(self.hold_T), int(self.estimate_v), int(self.dense)
+        # alpha_one: alpha = 1 on every face (the plain upwinding the paper
+        # improves on in sec. 4.2), a control for the tests only
+        s.alpha_one = int(alpha_one)
 
     @property
     def N(self):

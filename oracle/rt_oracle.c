@@ -58,6 +58,8 @@ typedef struct {
   int hold_T;              /* 1: gas temperature held fixed                    */
   int estimate_v;          /* 1: Step 3 velocity estimate on                   */
   int dense;               /* 1: brute-force dense solvers                     */
+  int alpha_one;           /* 1: alpha = 1 on every face (the plain Stone &
+                              Mihalas upwinding; a control for the tests)     */
 } orc_problem;
 
 static long ncells(const orc_problem *p) { return (long)p->n[0] * p->n[1] * p->n[2]; }
@@ -203,7 +205,7 @@ static void transport_all(const orc_problem *p, const double *I, const double *J
           double iv = 3.0 * (nm[0] * vc[0] + nm[1] * vc[1] + nm[2] * vc[2]) * J[cell];
           IV[q] = iv;
           It[q] = intensity_at(p, I, m, c, d, j) - iv / p->C;
-          al[q] = orc_alpha(p->dx[d], sigt[cell]);
+          al[q] = p->alpha_one ? 1.0 : orc_alpha(p->dx[d], sigt[cell]);
           vd[q] = vc[d];
         }
         /* face f lies between cells f-1 and f (padded f+1 and f+2) */
