@@ -1,7 +1,9 @@
 """FP64 CPU oracle for the radiation-transfer step (arXiv:1403.6126, secs. 3-4).
 
-TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
-the CPU-baseline leg of ``bench.py`` may import this package.  It shares no
+TEST INFRASTRUCTURE ONLY.  Only ``tests/`` (and the script there that
+stores oracle values, ``tests/golden/make_stated_steps.py``),
+``__graft_entry__.smoke()`` and the CPU-baseline / reference leg of
+``bench.py`` may import this package.  It shares no
 code with the GPU library (``paper_1403_6126_gb300``) and never imports it.
 
 The arithmetic lives in ``rt_oracle.c`` (plain serial-per-cell C, double
