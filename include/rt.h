@@ -335,8 +335,8 @@ void rt_server_destroy(rt_server *s);
  * (float intensities and cell data, double temperature and energy source,
  * the layouts of the conventions above); the function calls no cudaMalloc,
  * cudaFree or other allocating routine.  The little scratch the persistent
- * step kernel needs (tile counter, Newton-failure word, angle and inflow
- * tables) is a fixed device array of 10496 bytes that every GPU loading the
+ * step kernel needs (Newton-failure word, angle and inflow tables) is a
+ * fixed device array of 10496 bytes that every GPU loading the
  * library holds until the process exits; it limits the angle set to 256
  * angles (RT_E_INVALID above that).
  *

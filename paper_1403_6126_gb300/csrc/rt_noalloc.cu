@@ -5,14 +5,14 @@
 // only touch buffers handed to them, and stream-capture or real-time paths
 // where an allocation could block or fail.  rt_step_noalloc serves them: the
 // caller passes every field as a device pointer, and the little scratch the
-// persistent step kernel needs (its tile counter, the Newton-failure word,
-// the angle table and the inflow table) lives in a fixed file-scope device
+// persistent step kernel needs (the Newton-failure word, the angle table and
+// the inflow table) lives in a fixed file-scope device
 // array, reserved once per GPU when the library is loaded and kept until the
 // process exits.  Its size, kNoallocScratchBytes below, bounds the angle
 // count to kNoallocMaxAngles.
 //
 // The array is shared by every call: each call rewrites the tables and
-// clears the two counters before its kernel runs, so nothing carries over
+// clears the failure word before its kernel runs, so nothing carries over
 // from the previous call, but two calls that overlap on the GPU (different
 // streams without ordering between them) race on it.
 #include <cmath>
@@ -29,30 +29,24 @@ namespace {
 
 constexpr int kNoallocMaxAngles = 256;
 constexpr int kNoallocThreads = 512;
-// counter (4 B) + failure word (4 B), padded to 256; angle table [M][4];
-// inflow table [6][M]
+// a reserved word (4 B) + failure word (4 B), padded to 256; angle table
+// [M][4]; inflow table [6][M]
 constexpr size_t kNoallocTableOffset = 256;
 constexpr size_t kNoallocScratchBytes = kNoallocTableOffset + sizeof(float) * 10 * kNoallocMaxAngles;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-// Persistent tiles of one problem: CTAs take tile numbers from the counter
-// at the start of the scratch array.
+// Persistent tiles of one problem: CTA b takes tiles b, b + grid, b + 2 grid,
+// ... (the tiles cost alike, so no claim has to stand between one tile and
+// the next).
 template <int DIM, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(TX * TY * TZ, 1) noalloc_kernel(const StepArgs<float> a, int *counter) {
+__global__ void __launch_bounds__(TX * TY * TZ, 1) noalloc_kernel(const StepArgs<float> a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_item;
   const int ntx = (a.n[0] + TX - 1) / TX, nty = (a.n[1] + TY - 1) / TY, ntz = (a.n[2] + TZ - 1) / TZ;
   const int ntiles = ntx * nty * ntz;
-  for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
-    __syncthreads();
-    const int it = s_item;
-    if (it >= ntiles) break;
+  for (int it = blockIdx.x; it < ntiles; it += gridDim.x)
     stepk::process_tile2<DIM, true, TX, TY, TZ>(a, threadIdx.x, it % ntx, (it / ntx) % nty, it / (ntx * nty),
                                                      smem);
-    __syncthreads();
-  }
 }
 
 // Device address of the scratch array, looked up once per device.
@@ -80,7 +74,7 @@ rt_status scratch_for_current_device(unsigned char **out) {
 }
 
 template <int DIM, int TX, int TY, int TZ>
-cudaError_t launch_noalloc(const StepArgs<float> &a, int *counter, cudaStream_t s) {
+cudaError_t launch_noalloc(const StepArgs<float> &a, cudaStream_t s) {
   const size_t sm = stepk::smem_bytes2(DIM, a.M, true, TX, TY, TZ);
   auto kern = noalloc_kernel<DIM, TX, TY, TZ>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -91,7 +85,7 @@ cudaError_t launch_noalloc(const StepArgs<float> &a, int *counter, cudaStream_t 
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   const long long ntiles = (long long)((a.n[0] + TX - 1) / TX) * ((a.n[1] + TY - 1) / TY) * ((a.n[2] + TZ - 1) / TZ);
   const int grid = (int)std::max(1LL, std::min(ntiles, (long long)sms * std::max(1, per_sm)));
-  kern<<<grid, TX * TY * TZ, sm, s>>>(a, counter);
+  kern<<<grid, TX * TY * TZ, sm, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -159,7 +153,7 @@ extern "C" rt_status rt_step_noalloc(const rt_grid *g, const rt_angles *ang, dou
   for (int i = 0; i < 6 * M; ++i) host_tab[4 * M + i] = f->inflow ? (float)f->inflow[i] : 0.0f;
   cudaStream_t s = (cudaStream_t)opts->stream;
   cudaError_t e = cudaMemcpyAsync(tab, host_tab, sizeof(float) * 10 * M, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, 2 * sizeof(int), s);   // tile counter, failure word
+  if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, 2 * sizeof(int), s);   // reserved word, failure word
   if (e != cudaSuccess) return set_error(RT_E_CUDA, std::string("rt_step_noalloc: scratch set-up: ") + cudaGetErrorString(e));
 
   a.M = M;
@@ -192,9 +186,9 @@ extern "C" rt_status rt_step_noalloc(const rt_grid *g, const rt_angles *ang, dou
   a.Q = nullptr;
   a.outer_begin = 0;
   a.outer_count = 0;
-  e = g->dim == 1   ? rtg::launch_noalloc<1, 512, 1, 1>(a, counter, s)
-      : g->dim == 2 ? rtg::launch_noalloc<2, 32, 16, 1>(a, counter, s)
-                    : rtg::launch_noalloc<3, 16, 8, 4>(a, counter, s);
+  e = g->dim == 1   ? rtg::launch_noalloc<1, 512, 1, 1>(a, s)
+      : g->dim == 2 ? rtg::launch_noalloc<2, 32, 16, 1>(a, s)
+                    : rtg::launch_noalloc<3, 16, 8, 4>(a, s);
   if (e != cudaSuccess) return set_error(RT_E_CUDA, std::string("rt_step_noalloc: launch: ") + cudaGetErrorString(e));
   if (newton_failures) {
     e = cudaMemcpyAsync(newton_failures, counter + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
