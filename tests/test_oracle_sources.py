@@ -211,6 +211,54 @@ def test_velocity_estimate_limits():
     np.testing.assert_allclose(vt, lim, rtol=1e-11)
 
 
+def _momentum_exchange_exact(rho, v, F, K, st, C, P, t):
+    """Exact solution at time t of the sec. 4.5 ODE pair with E_r and P_dd
+    held (K = E + P_dd per axis):
+        rho dv/dt = P st (F - v K / C),   dF/dt = -C st (F - v K / C).
+    The total rho v + (P/C) F is conserved, and g = F - v K / C obeys
+    dg/dt = -lam g with lam = st (C + P K / (rho C)), so
+    v(t) = v + (P st / rho) g0 (1 - exp(-lam t)) / lam."""
+    g0 = F - v * K / C
+    lam = st * (C + P * K / (rho * C))
+    return v + (P * st / rho) * g0 * (-np.expm1(-lam * t)) / lam
+
+
+def test_velocity_estimate_is_a_half_step_of_the_momentum_exchange():
+    # sec. 4.5: v~ estimates the velocity at n + 1/2 from the ODE pair of
+    # photon-gas momentum exchange (E_r, P_r held).  Two checks against the
+    # ODE itself rather than against the implicit formula:
+    #  (a) as dt -> 0, (v~ - v^n) / dt tends to 1/2 of the ODE's rate
+    #      dv/dt = (P st / rho) (F - v (E + P_dd) / C): v~ advances half a step;
+    #  (b) v~ agrees with the exact solution at t = dt/2 to second order in
+    #      dt (the error falls by ~4x when dt halves), as a one-step implicit
+    #      estimate of the half-step velocity must.
+    # Taking the full step dt in place of dt/2 fails (a) by a factor 2 and
+    # (b) at first order.
+    n, w = angles.level_symmetric(2)
+    C, P, rho, st = 10.0, 50.0, 2.0, 3.0
+    p = oracle.Problem((1, 1, 1), 1.0, n, w, C=C, P=P)
+    v = np.array([0.3, -0.2, 0.1])
+    F = np.array([0.5, 0.1, -0.3])
+    E = 1.2
+    Pd = np.array([0.4, 0.3, 0.5])
+    K = E + Pd
+    rate = (P * st / rho) * (F - v * K / C)
+    dt = 1e-7
+    slope = (oracle.vtilde(p, rho, v, st, E, F, Pd, dt) - v) / dt
+    np.testing.assert_allclose(slope, 0.5 * rate, rtol=1e-5)
+    errs = []
+    for dt in (2e-3, 1e-3, 5e-4):
+        vt = oracle.vtilde(p, rho, v, st, E, F, Pd, dt)
+        errs.append(np.abs(vt - _momentum_exchange_exact(rho, v, F, K, st, C, P, 0.5 * dt)).max())
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 3.5 < e1 / e2 < 4.5, errs
+    # with the exchange fast against the step (lam dt >> 1) both reach the
+    # exchange equilibrium g = 0, the implicit estimate to O(1 / (lam dt))
+    vt = oracle.vtilde(p, rho, v, 1e6, E, F, Pd, 1.0)
+    vinf = _momentum_exchange_exact(rho, v, F, K, 1e6, C, P, 0.5)
+    np.testing.assert_allclose(vt, vinf, rtol=1e-5)
+
+
 def test_quadrature_of_isotropic_field():
     # sec. 3: for isotropic I, E_r = 4 pi I, F_r = 0, P_r = E_r / 3 * identity.
     for name in ("s2", "s4", "s6", "s8"):
