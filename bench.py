@@ -31,22 +31,24 @@ sys.path.insert(0, ROOT)
 
 PROFILE = os.path.join(ROOT, "profiles", "step_kernel_box3d.md")
 # sources of the float step kernel (the pair kernel and the tile geometry it shares)
-KERNEL_SRCS = [os.path.join(ROOT, "paper_1403_6126_gb300", "csrc", f) for f in ("rt_step_pair.cuh", "rt_step_kernel.cuh")]
+KERNEL_SRCS = [os.path.join(ROOT, "paper_1403_6126_gb300", "csrc", f)
+               for f in ("rt_step_quad.cuh", "rt_step_pair.cuh", "rt_step_kernel.cuh")]
 NOMINAL_HBM_GBS = 8000.0
 
 
 def algorithmic_bytes_per_cell(M, rs, velocity, live_T):
     """Bytes one fused step must move per cell: read and write I (M values of
-    rs bytes); read rho, sigma_a, sigma_s, v and T; read E (for IV = 3 n.v J)
-    and F, P_xx..P_zz (for the velocity estimate) when velocity terms are on;
-    write T, E, F, P (10 moments), the gas energy source (double) and the
-    momentum source (3)."""
+    rs bytes); read rho, sigma_a, sigma_s, v (rs bytes each) and T (double);
+    read E (for IV = 3 n.v J) and F, P_xx..P_zz (for the velocity estimate),
+    double, when velocity terms are on; write T, E, F, P (10 moments), the
+    gas energy source and the momentum source (3), all double.  At 80 angles
+    and float intensities that is 848 bytes per cell."""
     b = 2 * M * rs                 # I^n in, I^{n+1} out
     b += 3 * rs + 3 * rs           # rho, sigma_a, sigma_s, v
     b += 8 + (8 if live_T else 0)  # T in (double), T out when it evolves
     if velocity:
-        b += 7 * rs                # E, F, P_dd of step n
-    b += 10 * rs + 8 + 3 * rs      # moments, dE_gas, dMom
+        b += 7 * 8                 # E, F, P_dd of step n
+    b += 10 * 8 + 8 + 3 * 8        # moments, dE_gas, dMom
     return b
 
 
@@ -337,7 +339,7 @@ def run_gpu(args):
                 "traffic": traffic, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
                 "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
-                "kernel": ("step_kernel2<%d,%s,%d,%d,%d>" % ((wl["dim"], "true" if velocity else "false") + tile)
+                "kernel": ("step_kernel_q<%d,%s,%d,%d,%d>" % ((wl["dim"], "true" if velocity else "false") + tile)
                            if rs == 4 else "step_kernel<double,%d,%s,%d,%d,%d>"
                            % ((wl["dim"], "true" if velocity else "false") + tile)),
                 "tile": "%dx%dx%d" % tile, "autotune": tuned}

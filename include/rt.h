@@ -105,7 +105,17 @@ typedef struct {
 
 /* Options.  Defaults (rt_options_default): RT_FP32, cfl 0.4 (Step 1 of
  * sec. 4.1), gamma 5/3, r_ideal 1, hold_T 0, estimate_v 1, device_ptrs 0,
- * stream NULL (the legacy default stream). */
+ * stream NULL (the legacy default stream), newton_max_it 60, newton_rtol
+ * 1e-13.
+ *
+ * The Newton iteration on the gas temperature (Step 4, sec. 4.3: the paper
+ * solves eq. absorptionmatrix by Newton-Raphson and notes that it converges
+ * in a few iterations) starts from T^n and stops once a step changes T by
+ * at most newton_rtol * T, after one more step; a cell that needs more than
+ * newton_max_it steps, or whose iterate leaves T > 0, counts as a failure
+ * (rt_sync then returns RT_E_NONFINITE).  newton_max_it in 1..1000,
+ * newton_rtol in [1e-15, 1e-3] (RT_E_INVALID otherwise).  The FP64 CPU
+ * reference of this library uses the defaults. */
 typedef struct {
   int precision;
   double cfl;        /* dt = cfl * min dx / Crat when rt_step gets dt <= 0      */
@@ -115,6 +125,8 @@ typedef struct {
   int estimate_v;    /* 1: use the sec. 4.5 half-step velocity in Steps 4-5   */
   int device_ptrs;   /* 1: array arguments are device pointers               */
   void *stream;      /* cudaStream_t the context launches on                  */
+  int newton_max_it; /* iteration cap of the T^4 Newton solve                 */
+  double newton_rtol;/* its stopping tolerance on |dT| / T                     */
 } rt_options;
 
 /* Fills *o with the defaults above.  RT_E_INVALID if o is NULL. */
@@ -331,39 +343,51 @@ void rt_server_destroy(rt_server *s);
  * allocate device memory -- code running inside another framework's memory
  * pool or under a fixed memory budget, plugins allowed to touch only the
  * buffers handed to them, and latency-critical paths where an allocation
- * could block or fail.  The caller passes every field as a device pointer
- * (float intensities and cell data, double temperature and energy source,
- * the layouts of the conventions above); the function calls no cudaMalloc,
- * cudaFree or other allocating routine.  The little scratch the persistent
- * step kernel needs (Newton-failure word, angle and inflow tables) is a
- * fixed device array of 10496 bytes that every GPU loading the
- * library holds until the process exits; it limits the angle set to 256
- * angles (RT_E_INVALID above that).
+ * could block or fail.  The caller passes every field as a device pointer;
+ * the function calls no cudaMalloc, cudaFree or other allocating routine.
+ * The angle and inflow tables travel in the kernel's launch parameters,
+ * which limits the angle set to 256 angles (RT_E_INVALID above that).  The
+ * one scratch word the step kernel needs (the count of cells whose T^4
+ * Newton did not converge) is a fixed 256-byte device array that every GPU
+ * loading the library holds until the process exits.
  *
  * The first call on a device looks up that array's device address (once per
  * device, with the device current); make that first call before any stream
- * capture.  Every call rewrites the tables and clears the counters before its
- * kernel runs, but all calls share the one array: calls that overlap on the
- * GPU (unordered streams) race.
+ * capture.  Every call clears the failure word before its kernel runs, but
+ * all calls share the one array: calls that overlap on the GPU (unordered
+ * streams) race.
  *
  * The step is the same as rt_step with RT_FP32 and the velocity terms on
  * (grid, angles, Crat, Prat, opts->hold_T / estimate_v / gamma / r_ideal /
- * stream as for rt_create; opts->precision must be RT_FP32; dt > 0).
- * I_out, mom_out, dE_gas, dMom receive the new state; T is updated in place.
- * mom_in must hold E_r, F_r, P_r of I_in (10 components, as rt_moments).
+ * newton_max_it / newton_rtol / stream as for rt_create; opts->precision must
+ * be RT_FP32; dt > 0), and gives bitwise what rt_step gives.  Layouts:
+ *  - I_in, I_out: the float step's storage layout, ceil(M/4) planes of four
+ *    angles each: angle m of cell c is at float index
+ *    (m / 4) * 4N + 4c + (m % 4); the entries of angles M .. 4 ceil(M/4) - 1
+ *    are padding (zero on input; the step writes zeros there);
+ *  - rho, sigma_a, sigma_s (N floats), v (3N floats, component-major);
+ *  - T (N doubles), updated in place;
+ *  - mom_in, mom_out: E_r, F_r, P_r as 10N doubles in the order of
+ *    rt_moments; mom_in must hold the moments of I_in;
+ *  - dE_gas (N doubles), dMom (3N doubles): the step's gas sources.
+ * I_in and I_out, and mom_in and mom_out, must be different buffers
+ * (RT_E_INVALID when they are the same pointer): neighbouring cells read
+ * the step-n values while others write the new ones.  Other overlaps
+ * between the buffers are not detected and give undefined results.
  * inflow: host array [3][2][M] of incoming intensities for RT_BC_INFLOW
  * faces, or NULL.  If newton_failures is not NULL the call waits for the
- * stream and stores the number of cells whose T^4 Newton did not converge;
- * otherwise it returns once the work is queued. */
+ * stream and stores the number of cells whose T^4 Newton did not converge
+ * (RT_E_INVALID on a stream that is being captured); otherwise it returns
+ * once the work is queued. */
 typedef struct {
   const float *I_in;
   float *I_out;
   const float *rho, *sigma_a, *sigma_s, *v;
   double *T;
-  const float *mom_in;
-  float *mom_out;
+  const double *mom_in;
+  double *mom_out;
   double *dE_gas;
-  float *dMom;
+  double *dMom;
   const double *inflow;
 } rt_noalloc_fields;
 

@@ -42,7 +42,8 @@ class rt_angles(ctypes.Structure):
 class rt_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("cfl", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("r_ideal", ctypes.c_double), ("hold_T", ctypes.c_int), ("estimate_v", ctypes.c_int),
-                ("device_ptrs", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("device_ptrs", ctypes.c_int), ("stream", ctypes.c_void_p), ("newton_max_it", ctypes.c_int),
+                ("newton_rtol", ctypes.c_double)]
 
 
 class rt_noalloc_fields(ctypes.Structure):

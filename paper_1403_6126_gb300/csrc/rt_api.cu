@@ -26,6 +26,14 @@ rt_status fail(rt_status s, const std::string &msg) {
 
 rt_status rtg::set_error(rt_status s, const std::string &msg) { return fail(s, msg); }
 
+rt_status rtg::check_newton_options(const rt_options &o, const char *where) {
+  if (o.newton_max_it < 1 || o.newton_max_it > 1000)
+    return fail(RT_E_INVALID, std::string(where) + ": newton_max_it must be in 1..1000");
+  if (!(o.newton_rtol >= 1e-15 && o.newton_rtol <= 1e-3))
+    return fail(RT_E_INVALID, std::string(where) + ": newton_rtol must be in [1e-15, 1e-3]");
+  return RT_OK;
+}
+
 namespace {
 std::atomic<int> g_fail_alloc_after{-1};   // armed by rt_fault_inject
 }
@@ -103,6 +111,8 @@ rtg::StepArgs<Real> rtg::make_args(rt_ctx *c, double dt) {
   a.kv_per_rho = c->opt.r_ideal / (c->opt.gamma - 1.0);
   a.hold_T = c->opt.hold_T;
   a.estimate_v = c->opt.estimate_v;
+  a.newton_max_it = c->opt.newton_max_it;
+  a.newton_rtol = c->opt.newton_rtol;
   a.ang = (const Real *)c->ang;
   a.inflow = (const Real *)c->inflow;
   a.I_in = (const Real *)c->I[c->cur];
@@ -123,10 +133,10 @@ rtg::StepArgs<Real> rtg::make_args(rt_ctx *c, double dt) {
   a.v = (const Real *)c->v;
   a.T_in = c->T;
   a.T_out = c->T;
-  a.mom_in = (const Real *)c->mom[c->cur];
-  a.mom_out = (Real *)c->mom[1 - c->cur];
+  a.mom_in = c->mom[c->cur];
+  a.mom_out = c->mom[1 - c->cur];
   a.dEgas = c->dEgas;
-  a.dMom = (Real *)c->dMom;
+  a.dMom = c->dMom;
   a.status = c->flags;
   a.outer_begin = 0;
   a.outer_count = 0;
@@ -135,8 +145,18 @@ rtg::StepArgs<Real> rtg::make_args(rt_ctx *c, double dt) {
 
 size_t rtg::context_bytes(long long N, int M, bool fp64) {
   const size_t rs = fp64 ? 8 : 4, Nz = (size_t)N, Mz = (size_t)M;
+  const size_t Ms = fp64 ? Mz : 4 * (size_t)((M + 3) / 4);   // stored angles (float: quad padding)
   const size_t stage = sizeof(double) * std::max<size_t>(10 * Nz, 8 * Mz);
-  return rs * (2 * Mz * Nz + 2 * 10 * Nz + 6 * Nz + 3 * Nz + 10 * Mz) + 16 * Nz + 2 * sizeof(int) + stage;
+  return rs * (2 * Ms * Nz + 6 * Nz + 10 * Mz) + 8 * (2 * 10 * Nz + 3 * Nz) + 16 * Nz + 2 * sizeof(int) + stage;
+}
+
+cudaError_t rtg::launch_ctx_step(rt_ctx *c, const StepArgs<double> &a, bool vel, TileShape t) {
+  return launch_step<double>(a, c->dim, vel, t, c->stream);
+}
+
+cudaError_t rtg::launch_ctx_step(rt_ctx *c, const StepArgs<float> &a, bool vel, TileShape t) {
+  if (c->bf16) return launch_step<float>(a, c->dim, vel, t, c->stream);
+  return launch_step_quad(a, c->host_angf.data(), c->host_inflowf.data(), c->dim, vel, t, c->stream);
 }
 
 template rtg::StepArgs<float> rtg::make_args<float>(rt_ctx *, double);
@@ -150,9 +170,9 @@ rt_status launch_step(rt_ctx *c, double dt) {
   cudaError_t e;
   bool vel = rtg::velocity_on(c);
   if (c->fp64)
-    e = rtg::launch_step<double>(rtg::make_args<double>(c, dt), c->dim, vel, c->tile, c->stream);
+    e = rtg::launch_ctx_step(c, rtg::make_args<double>(c, dt), vel, c->tile);
   else
-    e = rtg::launch_step<float>(rtg::make_args<float>(c, dt), c->dim, vel, c->tile, c->stream);
+    e = rtg::launch_ctx_step(c, rtg::make_args<float>(c, dt), vel, c->tile);
   if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
   c->cur = 1 - c->cur;
   return RT_OK;
@@ -176,13 +196,6 @@ rt_status fields_in(rt_ctx *c, long long c0, long long c1, bool convert, cudaStr
   return e == cudaSuccess ? RT_OK : cuda_fail(e, "fields");
 }
 
-// Delta(rho v) of cells [c0, c1), three components, into dst (double, 3N).
-rt_status dmom_out(rt_ctx *c, double *dst, long long c0, long long c1, cudaStream_t s) {
-  cudaError_t e = c->fp64 ? rtg::launch_dmom_out<double>((const double *)c->dMom, dst, c->N, c0, c1 - c0, s)
-                          : rtg::launch_dmom_out<float>((const float *)c->dMom, dst, c->N, c0, c1 - c0, s);
-  return e == cudaSuccess ? RT_OK : cuda_fail(e, "convert");
-}
-
 rt_status convert_out(rt_ctx *c, const void *src, double *dst, long long n) {
   cudaError_t e = c->fp64 ? rtg::launch_convert_out<double>((const double *)src, dst, n, c->stream)
                           : rtg::launch_convert_out<float>((const float *)src, dst, n, c->stream);
@@ -194,9 +207,9 @@ rt_status convert_out(rt_ctx *c, const void *src, double *dst, long long n) {
 rt_status recompute_moments(rt_ctx *c) {
   const void *I = c->bf16 ? (const void *)c->qscr : c->I[c->cur];
   cudaError_t e = c->fp64 ? rtg::launch_moments<double>((const double *)I, (const double *)c->ang, c->M,
-                                                        c->N, (double *)c->mom[c->cur], c->stream)
+                                                        c->N, false, c->mom[c->cur], c->stream)
                           : rtg::launch_moments<float>((const float *)I, (const float *)c->ang, c->M,
-                                                       c->N, (float *)c->mom[c->cur], c->stream);
+                                                       c->N, c->quad, c->mom[c->cur], c->stream);
   return e == cudaSuccess ? RT_OK : cuda_fail(e, "moments");
 }
 
@@ -260,17 +273,13 @@ rt_status coupled_in(rt_ctx *c, const double *const f[5], long long c0, long lon
   return RT_OK;
 }
 
-// Sources of the cells [c0, c1) back to the caller: Delta(rho v) converted
-// on the context stream (right after the slab: on another stream the
-// conversion would wait for SMs until the next slab's tail) into the
-// staging buffer's last 3N doubles, then all three fields copied on the
-// outgoing stream once ev (recorded after the conversion) has fired.
+// Sources of the cells [c0, c1) back to the caller (all three double on the
+// device), copied on the outgoing stream once ev (recorded after the slab's
+// kernel) has fired.
 rt_status coupled_out(rt_ctx *c, long long c0, long long c1, cudaEvent_t ev, double *dE_gas, double *dMom,
                       double *T_new) {
   const long long N = c->N, n = c1 - c0;
-  double *s_mom = c->stage + 7 * N;
-  rt_status st;
-  if (dMom && (st = dmom_out(c, s_mom, c0, c1, c->stream)) != RT_OK) return st;
+  const double *s_mom = c->dMom;
   RT_CUDA(cudaEventRecord(ev, c->stream));
   RT_CUDA(cudaStreamWaitEvent(c->xs_out, ev, 0));
   const size_t b = n * sizeof(double);
@@ -289,12 +298,12 @@ rt_status coupled_launch(rt_ctx *c, double dt, bool vel, int l0, int l1) {
     rtg::StepArgs<double> a = rtg::make_args<double>(c, dt);
     a.outer_begin = l0;
     a.outer_count = l1 - l0;
-    e = rtg::launch_step<double>(a, c->dim, vel, c->tile, c->stream);
+    e = rtg::launch_ctx_step(c, a, vel, c->tile);
   } else {
     rtg::StepArgs<float> a = rtg::make_args<float>(c, dt);
     a.outer_begin = l0;
     a.outer_count = l1 - l0;
-    e = rtg::launch_step<float>(a, c->dim, vel, c->tile, c->stream);
+    e = rtg::launch_ctx_step(c, a, vel, c->tile);
   }
   return e == cudaSuccess ? RT_OK : cuda_fail(e, "step kernel launch");
 }
@@ -326,6 +335,8 @@ rt_status rt_options_default(rt_options *o) {
   o->estimate_v = 1;
   o->device_ptrs = 0;
   o->stream = nullptr;
+  o->newton_max_it = 60;
+  o->newton_rtol = 1e-13;
   return RT_OK;
 }
 
@@ -372,6 +383,7 @@ rt_status rt_create(const rt_grid *g, const rt_angles *ang, double Crat, double 
     return fail(RT_E_INVALID, "rt_create: precision must be RT_FP64, RT_FP32 or RT_BF16");
   if (!(o.cfl > 0) || !(o.gamma > 1.0) || !(o.r_ideal > 0))
     return fail(RT_E_INVALID, "rt_create: need cfl > 0, gamma > 1, r_ideal > 0");
+  if (rt_status st = rtg::check_newton_options(o, "rt_create"); st != RT_OK) return st;
 
   rt_ctx *c = new (std::nothrow) rt_ctx;
   if (!c) return fail(RT_E_NOMEM, "rt_create: host allocation");
@@ -390,13 +402,22 @@ rt_status rt_create(const rt_grid *g, const rt_angles *ang, double Crat, double 
   c->stream = (cudaStream_t)o.stream;
   c->fp64 = o.precision == RT_FP64;
   c->bf16 = o.precision == RT_BF16;
+  c->quad = o.precision == RT_FP32;
   c->rs = c->fp64 ? 8 : 4;
   c->rsI = c->bf16 ? 2 : c->rs;
+  c->I_bytes = c->rsI * (size_t)N * (c->quad ? 4 * (size_t)((M + 3) / 4) : (size_t)M);
   c->host_n.assign(ang->n, ang->n + 3 * M);
   c->host_w.assign(ang->w, ang->w + M);
   c->host_inflow.assign(6 * (size_t)M, 0.0);
+  c->host_angf.resize(4 * (size_t)M);
+  for (int m = 0; m < M; ++m) {
+    for (int d = 0; d < 3; ++d) c->host_angf[4 * m + d] = (float)ang->n[3 * m + d];
+    c->host_angf[4 * m + 3] = (float)ang->w[m];
+  }
+  c->host_inflowf.assign(6 * (size_t)M, 0.0f);
   bool ok = c->fp64 ? rtg::choose_tile<double>(c->dim, M, true, &c->tile)
-                    : rtg::choose_tile<float>(c->dim, M, true, &c->tile);
+            : c->bf16 ? rtg::choose_tile_b16(c->dim, M, &c->tile)
+                      : rtg::choose_tile<float>(c->dim, M, true, &c->tile);
   if (!ok) {
     delete c;
     return fail(RT_E_INVALID, "rt_create: too many angles for one CTA's shared memory");
@@ -408,10 +429,10 @@ rt_status rt_create(const rt_grid *g, const rt_angles *ang, double Crat, double 
     void **p;
     size_t bytes;
   } allocs[] = {
-      {&c->I[0], c->rsI * Mz * Nz},  {&c->I[1], c->rsI * Mz * Nz},  {&c->mom[0], rs * 10 * Nz},
-      {&c->mom[1], rs * 10 * Nz}, {&c->rho, rs * Nz},               {&c->sa, rs * Nz},
+      {&c->I[0], c->I_bytes},        {&c->I[1], c->I_bytes},        {(void **)&c->mom[0], 8 * 10 * Nz},
+      {(void **)&c->mom[1], 8 * 10 * Nz}, {&c->rho, rs * Nz},       {&c->sa, rs * Nz},
       {&c->ss, rs * Nz},         {&c->v, rs * 3 * Nz},             {(void **)&c->T, 8 * Nz},
-      {(void **)&c->dEgas, 8 * Nz}, {&c->dMom, rs * 3 * Nz},       {&c->ang, rs * 4 * Mz},
+      {(void **)&c->dEgas, 8 * Nz}, {(void **)&c->dMom, 8 * 3 * Nz}, {&c->ang, rs * 4 * Mz},
       {&c->inflow, rs * 6 * Mz}, {(void **)&c->flags, 2 * sizeof(int)},
       {(void **)&c->stage, sizeof(double) * (size_t)c->stage_len},
       {(void **)&c->qscr, c->bf16 ? sizeof(float) * Mz * Nz : 0},
@@ -437,7 +458,7 @@ rt_status rt_create(const rt_grid *g, const rt_angles *ang, double Crat, double 
   if (e == cudaSuccess && st == RT_OK) e = cudaMemsetAsync(c->inflow, 0, rs * 6 * M, c->stream);
   if (e == cudaSuccess && st == RT_OK) e = cudaMemsetAsync(c->flags, 0, 2 * sizeof(int), c->stream);
   if (e == cudaSuccess && st == RT_OK) e = cudaMemsetAsync(c->dEgas, 0, 8 * N, c->stream);
-  if (e == cudaSuccess && st == RT_OK) e = cudaMemsetAsync(c->dMom, 0, rs * 3 * N, c->stream);
+  if (e == cudaSuccess && st == RT_OK) e = cudaMemsetAsync(c->dMom, 0, 8 * 3 * N, c->stream);
   if (e == cudaSuccess && st == RT_OK) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess || st != RT_OK) {
     free_all(c);
@@ -486,8 +507,8 @@ rt_status rt_set_intensity(rt_ctx *c, const double *I) {
   const size_t rsd = c->bf16 ? sizeof(float) : c->rs;
   if (!I) {
     if (!c->material_set) return fail(RT_E_STATE, "rt_set_intensity(NULL) needs rt_set_material first");
-    cudaError_t e = c->fp64 ? rtg::launch_isotropic<double>(c->T, (double *)dst, c->M, N, c->stream)
-                            : rtg::launch_isotropic<float>(c->T, (float *)dst, c->M, N, c->stream);
+    cudaError_t e = c->fp64 ? rtg::launch_isotropic<double>(c->T, (double *)dst, c->M, N, false, c->stream)
+                            : rtg::launch_isotropic<float>(c->T, (float *)dst, c->M, N, c->quad, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "isotropic");
   } else {
     // check everything first (finite, >= 0), then convert chunk by chunk
@@ -503,19 +524,23 @@ rt_status rt_set_intensity(rt_ctx *c, const double *I) {
     RT_CUDA(cudaMemcpyAsync(&flag, c->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     RT_CUDA(cudaStreamSynchronize(c->stream));
     if (flag & 1) return fail(RT_E_NONFINITE, "rt_set_intensity: need finite I >= 0");
+    if (c->quad) RT_CUDA(cudaMemsetAsync(dst, 0, c->I_bytes, c->stream));   // the padding angles
     for (long long off = 0; off < (long long)c->M * N; off += chunk) {
       long long n = std::min(chunk, (long long)c->M * N - off);
       rt_status st = fetch(c, I + off, c->stage, n);
       if (st != RT_OK) return st;
-      st = convert_in(c, c->stage, (char *)dst + off * rsd, n);
-      if (st != RT_OK) return st;
+      if (c->quad) {
+        RT_CUDA(rtg::launch_quad_in(c->stage, (float *)dst, off, n, N, c->stream));
+      } else {
+        st = convert_in(c, c->stage, (char *)dst + off * rsd, n);
+        if (st != RT_OK) return st;
+      }
     }
   }
   rt_status st = recompute_moments(c);
   if (st != RT_OK) return st;
   if (c->bf16)
-    RT_CUDA(rtg::launch_encode_b16(c->qscr, (const float *)c->mom[c->cur], (unsigned short *)c->I[c->cur], c->M, N,
-                                   c->stream));
+    RT_CUDA(rtg::launch_encode_b16(c->qscr, c->mom[c->cur], (unsigned short *)c->I[c->cur], c->M, N, c->stream));
   c->intensity_set = true;
   return RT_OK;
 }
@@ -526,6 +551,7 @@ rt_status rt_set_inflow(rt_ctx *c, int axis, int side, const double *I_ghost) {
   for (int m = 0; m < c->M; ++m)
     if (!std::isfinite(I_ghost[m]) || I_ghost[m] < 0) return fail(RT_E_NONFINITE, "rt_set_inflow: need finite I >= 0");
   std::copy(I_ghost, I_ghost + c->M, c->host_inflow.begin() + (size_t)(axis * 2 + side) * c->M);
+  for (int m = 0; m < c->M; ++m) c->host_inflowf[(size_t)(axis * 2 + side) * c->M + m] = (float)I_ghost[m];
   RT_CUDA(cudaMemcpyAsync(c->stage, c->host_inflow.data(), 6 * c->M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   rt_status st = convert_in(c, c->stage, c->inflow, 6 * c->M);
   if (st != RT_OK) return st;
@@ -537,13 +563,17 @@ rt_status rt_set_tile(rt_ctx *c, int tx, int ty, int tz) {
   if (!c) return fail(RT_E_INVALID, "rt_set_tile: NULL context");
   rtg::TileShape t{tx, ty, tz};
   if (tx == 0 && ty == 0 && tz == 0) {
-    bool ok = c->fp64 ? rtg::choose_tile<double>(c->dim, c->M, true, &t) : rtg::choose_tile<float>(c->dim, c->M, true, &t);
+    bool ok = c->fp64 ? rtg::choose_tile<double>(c->dim, c->M, true, &t)
+              : c->bf16 ? rtg::choose_tile_b16(c->dim, c->M, &t)
+                        : rtg::choose_tile<float>(c->dim, c->M, true, &t);
     if (!ok) return fail(RT_E_INVALID, "rt_set_tile: no default tile fits");
   } else {
-    bool ok = c->fp64 ? rtg::tile_ok<double>(c->dim, c->M, true, t) : rtg::tile_ok<float>(c->dim, c->M, true, t);
-    if (ok && c->bf16) {
+    bool ok;
+    if (c->bf16) {
       rtg::TileShape d;
-      ok = rtg::choose_tile<float>(c->dim, c->M, true, &d) && d.tx == t.tx && d.ty == t.ty && d.tz == t.tz;
+      ok = rtg::choose_tile_b16(c->dim, c->M, &d) && d.tx == t.tx && d.ty == t.ty && d.tz == t.tz;
+    } else {
+      ok = c->fp64 ? rtg::tile_ok<double>(c->dim, c->M, true, t) : rtg::tile_ok<float>(c->dim, c->M, true, t);
     }
     if (!ok) return fail(RT_E_INVALID, "rt_set_tile: shape exceeds the thread, shared-memory or staging limits");
   }
@@ -566,7 +596,7 @@ rt_status rt_autotune(rt_ctx *c, int trial_steps, rt_tile_time *times, int cap, 
   rtg::TileShape cand[16];
   int nc = c->fp64 ? rtg::tile_candidates<double>(c->dim, c->M, true, cand)
                    : rtg::tile_candidates<float>(c->dim, c->M, true, cand);
-  if (c->bf16) nc = rtg::choose_tile<float>(c->dim, c->M, true, &cand[0]) ? 1 : 0;   // one compiled tile
+  if (c->bf16) nc = rtg::choose_tile_b16(c->dim, c->M, &cand[0]) ? 1 : 0;   // one compiled tile
   if (nc == 0) return fail(RT_E_INVALID, "rt_autotune: no compiled tile fits");
   // The trial steps read I[cur] and write only I[1 - cur], mom[1 - cur]
   // (scratch until the next real step), T in place and the step sources:
@@ -577,7 +607,7 @@ rt_status rt_autotune(rt_ctx *c, int trial_steps, rt_tile_time *times, int cap, 
   RT_CUDA(cudaMemcpyAsync(&flag0, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   RT_CUDA(cudaMemcpyAsync(save_T, c->T, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   RT_CUDA(cudaMemcpyAsync(save_dE, c->dEgas, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-  RT_CUDA(cudaMemcpyAsync(save_dM, c->dMom, 3 * N * c->rs, cudaMemcpyDeviceToDevice, c->stream));
+  RT_CUDA(cudaMemcpyAsync(save_dM, c->dMom, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   const double dt = rt_cfl_dt(c);
   cudaEvent_t e0, e1;
   RT_CUDA(cudaEventCreate(&e0));
@@ -595,8 +625,8 @@ rt_status rt_autotune(rt_ctx *c, int trial_steps, rt_tile_time *times, int cap, 
     for (int k = 0; k <= trial_steps && e == cudaSuccess; ++k) {
       if (k == 1) e = cudaEventRecord(e0, c->stream);
       if (e == cudaSuccess)
-        e = c->fp64 ? rtg::launch_step<double>(rtg::make_args<double>(c, dt), c->dim, vel, cand[i], c->stream)
-                    : rtg::launch_step<float>(rtg::make_args<float>(c, dt), c->dim, vel, cand[i], c->stream);
+        e = c->fp64 ? rtg::launch_ctx_step(c, rtg::make_args<double>(c, dt), vel, cand[i])
+                    : rtg::launch_ctx_step(c, rtg::make_args<float>(c, dt), vel, cand[i]);
     }
     if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -614,7 +644,7 @@ rt_status rt_autotune(rt_ctx *c, int trial_steps, rt_tile_time *times, int cap, 
   if (e != cudaSuccess) return cuda_fail(e, "rt_autotune: trial steps");
   RT_CUDA(cudaMemcpyAsync(c->T, save_T, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   RT_CUDA(cudaMemcpyAsync(c->dEgas, save_dE, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-  RT_CUDA(cudaMemcpyAsync(c->dMom, save_dM, 3 * N * c->rs, cudaMemcpyDeviceToDevice, c->stream));
+  RT_CUDA(cudaMemcpyAsync(c->dMom, save_dM, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   RT_CUDA(cudaMemcpyAsync(c->flags, &flag0, sizeof(int), cudaMemcpyHostToDevice, c->stream));
   RT_CUDA(cudaStreamSynchronize(c->stream));
   if (ntimes) *ntimes = n_out;
@@ -636,22 +666,22 @@ struct StateHeader {
   long long N;
   double C, P;
 };
-const char kStateMagic[8] = {'R', 'T', 'S', 'T', 'A', 'T', 'E', '1'};
+const char kStateMagic[8] = {'R', 'T', 'S', 'T', 'A', 'T', 'E', '2'};
 
 // (device pointer, bytes) of every saved array, in file order.
 int state_parts(rt_ctx *c, void **ptr, size_t *bytes) {
   const size_t N = (size_t)c->N, M = (size_t)c->M, rs = c->rs;
   int k = 0;
   auto add = [&](void *p, size_t b) { ptr[k] = p; bytes[k] = b; ++k; };
-  add(c->I[c->cur], c->rsI * M * N);
-  add(c->mom[c->cur], rs * 10 * N);
+  add(c->I[c->cur], c->I_bytes);
+  add(c->mom[c->cur], 8 * 10 * N);
   add(c->T, 8 * N);
   add(c->rho, rs * N);
   add(c->sa, rs * N);
   add(c->ss, rs * N);
   add(c->v, rs * 3 * N);
   add(c->dEgas, 8 * N);
-  add(c->dMom, rs * 3 * N);
+  add(c->dMom, 8 * 3 * N);
   add(c->inflow, rs * 6 * M);
   return k;
 }
@@ -825,12 +855,11 @@ rt_status rt_moments(rt_ctx *c, double *E, double *F, double *P) {
   if (!c) return fail(RT_E_INVALID, "rt_moments: NULL context");
   if (!c->intensity_set) return fail(RT_E_STATE, "rt_moments: no intensity yet");
   const long long N = c->N;
-  const char *mom = (const char *)c->mom[c->cur];
+  const double *mom = c->mom[c->cur];
   rt_status st;
-  if ((st = convert_out(c, mom, c->stage, 10 * N)) != RT_OK) return st;
-  if (E && (st = deliver_async(c, c->stage, E, N)) != RT_OK) return st;
-  if (F && (st = deliver_async(c, c->stage + N, F, 3 * N)) != RT_OK) return st;
-  if (P && (st = deliver_async(c, c->stage + 4 * N, P, 6 * N)) != RT_OK) return st;
+  if (E && (st = deliver_async(c, mom, E, N)) != RT_OK) return st;
+  if (F && (st = deliver_async(c, mom + N, F, 3 * N)) != RT_OK) return st;
+  if (P && (st = deliver_async(c, mom + 4 * N, P, 6 * N)) != RT_OK) return st;
   return delivered(c);
 }
 
@@ -841,10 +870,7 @@ rt_status rt_sources(rt_ctx *c, double *dE_gas, double *dMom, double *T_new) {
   rt_status st;
   // the energy source and T are double on the device: copied out directly
   if (dE_gas && (st = deliver_async(c, c->dEgas, dE_gas, N)) != RT_OK) return st;
-  if (dMom) {
-    if ((st = dmom_out(c, c->stage, 0, N, c->stream)) != RT_OK) return st;
-    if ((st = deliver_async(c, c->stage, dMom, 3 * N)) != RT_OK) return st;
-  }
+  if (dMom && (st = deliver_async(c, c->dMom, dMom, 3 * N)) != RT_OK) return st;
   if (T_new && (st = deliver_async(c, c->T, T_new, N)) != RT_OK) return st;
   return delivered(c);
 }
@@ -959,9 +985,12 @@ rt_status rt_get_intensity(rt_ctx *c, double *I) {
     long long n = std::min(chunk, total - off);
     rt_status st = RT_OK;
     if (c->bf16) {
-      cudaError_t e = rtg::launch_decode_b16((const unsigned short *)c->I[c->cur], (const float *)c->mom[c->cur],
-                                             c->stage, off, n, c->N, c->stream);
+      cudaError_t e = rtg::launch_decode_b16((const unsigned short *)c->I[c->cur], c->mom[c->cur], c->stage, off, n,
+                                             c->N, c->stream);
       if (e != cudaSuccess) return cuda_fail(e, "decode");
+    } else if (c->quad) {
+      cudaError_t e = rtg::launch_quad_out((const float *)c->I[c->cur], c->stage, off, n, c->N, c->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "quad layout");
     } else {
       st = convert_out(c, (const char *)c->I[c->cur] + off * c->rs, c->stage, n);
     }

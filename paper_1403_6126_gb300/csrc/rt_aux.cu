@@ -47,14 +47,47 @@ __global__ void isotropic_kernel(const double *__restrict__ T, Real *__restrict_
   }
 }
 
+// The same in the quad-interleaved float layout: one float4 per cell and
+// quad, angles past M zero.
+__global__ void isotropic_quad_kernel(const double *__restrict__ T, float4 *__restrict__ I, int M, long long N) {
+  const int NQ = (M + 3) / 4;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+    const double t = T[c];
+    const float b = (float)(t * t * t * t / (4.0 * kPi));
+    for (int q = 0; q < NQ; ++q) {
+      const int m = 4 * q;
+      I[(long long)q * N + c] = make_float4(b, m + 1 < M ? b : 0.0f, m + 2 < M ? b : 0.0f, m + 3 < M ? b : 0.0f);
+    }
+  }
+}
+
+// Angle-major doubles, elements [off, off + n) (element i: angle i / N of
+// cell i % N), into the quad layout (element (m, c) at float (m/4) 4N + 4c
+// + m%4), and back.
+__global__ void quad_in_kernel(const double *__restrict__ src, float *__restrict__ dst, long long off, long long n,
+                               long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long g = off + i, m = g / N, c = g - m * N;
+    dst[(m >> 2) * 4 * N + 4 * c + (m & 3)] = (float)src[i];
+  }
+}
+
+__global__ void quad_out_kernel(const float *__restrict__ src, double *__restrict__ dst, long long off, long long n,
+                                long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long g = off + i, m = g / N, c = g - m * N;
+    dst[i] = (double)src[(m >> 2) * 4 * N + 4 * c + (m & 3)];
+  }
+}
+
 // bf16 storage: delta = I / J - 1 with J = E / (4 pi) of the cell (the same
 // arithmetic as the step kernel's b16_* helpers in rt_step_pair.cuh).
 constexpr float kInv4PiF = float(1.0 / (4.0 * 3.14159265358979323846));
 
-__global__ void encode_b16_kernel(const float *__restrict__ I, const float *__restrict__ E,
+__global__ void encode_b16_kernel(const float *__restrict__ I, const double *__restrict__ E,
                                   unsigned short *__restrict__ out, int M, long long N) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-    const float J = E[c] * kInv4PiF;
+    const float J = (float)E[c] * kInv4PiF;
     const float rJ = J > 1e-30f ? 1.0f / J : 0.0f;
     for (int m = 0; m < M; ++m) {
       const long long i = (long long)m * N + c;
@@ -63,11 +96,11 @@ __global__ void encode_b16_kernel(const float *__restrict__ I, const float *__re
   }
 }
 
-__global__ void decode_b16_kernel(const unsigned short *__restrict__ in, const float *__restrict__ E,
+__global__ void decode_b16_kernel(const unsigned short *__restrict__ in, const double *__restrict__ E,
                                   double *__restrict__ out, long long off, long long n, long long N) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const long long g = off + i;
-    const float J = E[g % N] * kInv4PiF;
+    const float J = (float)E[g % N] * kInv4PiF;
     out[i] = (double)fmaf(J, __bfloat162float(__ushort_as_bfloat16(in[g])), J);
   }
 }
@@ -76,7 +109,7 @@ __global__ void decode_b16_kernel(const unsigned short *__restrict__ in, const f
 // in double whatever the storage type.
 template <typename Real>
 __global__ void moments_kernel(const Real *__restrict__ I, const Real *__restrict__ ang, int M, long long N,
-                               Real *__restrict__ mom) {
+                               double *__restrict__ mom) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
     double s[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int m = 0; m < M; ++m) {
@@ -87,23 +120,25 @@ __global__ void moments_kernel(const Real *__restrict__ I, const Real *__restric
       s[4] += nx * nx * wi; s[5] += ny * ny * wi; s[6] += nz * nz * wi;
       s[7] += nx * ny * wi; s[8] += nx * nz * wi; s[9] += ny * nz * wi;
     }
-    for (int q = 0; q < 10; ++q) mom[(long long)q * N + c] = (Real)(4.0 * kPi * s[q]);
+    for (int q = 0; q < 10; ++q) mom[(long long)q * N + c] = 4.0 * kPi * s[q];
   }
 }
 
-// Float intensities: products in float and each of the ten sums compensated
-// (Kahan), the arithmetic the float step kernel uses for the same moments.
-// In double this kernel would run at the FP64 rate (~20 FP64 operations
-// per cell-angle: milliseconds for a 128^3 x 80 field).
+// Float intensities (angle-major, or the quad layout when QUAD): products
+// in float and each of the ten sums compensated (Kahan), read out as the
+// double hi - lo.  In double this kernel would run at the FP64 rate (~20 FP64
+// operations per cell-angle: milliseconds for a 128^3 x 80 field).
+template <bool QUAD>
 __global__ void moments_kernel_f(const float *__restrict__ I, const float *__restrict__ ang, int M, long long N,
-                                 float *__restrict__ mom) {
+                                 double *__restrict__ mom) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
     float hi[10], lo[10];
 #pragma unroll
     for (int q = 0; q < 10; ++q) hi[q] = lo[q] = 0.0f;
     for (int m = 0; m < M; ++m) {
       const float nx = ang[4 * m], ny = ang[4 * m + 1], nz = ang[4 * m + 2];
-      const float wi = ang[4 * m + 3] * I[(long long)m * N + c];
+      const float Im = QUAD ? I[(long long)(m >> 2) * 4 * N + 4 * c + (m & 3)] : I[(long long)m * N + c];
+      const float wi = ang[4 * m + 3] * Im;
       const float wx = nx * wi, wy = ny * wi, wz = nz * wi;
       const float term[10] = {wi, wx, wy, wz, nx * wx, ny * wy, nz * wz, ny * wx, nz * wx, nz * wy};
 #pragma unroll
@@ -114,9 +149,8 @@ __global__ void moments_kernel_f(const float *__restrict__ I, const float *__res
         hi[q] = s;
       }
     }
-    const float fourpi = (float)(4.0 * kPi);
 #pragma unroll
-    for (int q = 0; q < 10; ++q) mom[(long long)q * N + c] = fourpi * hi[q];
+    for (int q = 0; q < 10; ++q) mom[(long long)q * N + c] = 4.0 * kPi * ((double)hi[q] - (double)lo[q]);
   }
 }
 
@@ -180,17 +214,6 @@ __global__ void fields_in_kernel(const double *__restrict__ stage, long long N, 
   if (threadIdx.x == 0 && (bad || nonzero)) atomicOr(flag, (bad ? 1 : 0) | (nonzero ? 2 : 0));
 }
 
-// The three components of Delta(rho v) of cells [c0, c0 + n) to double.
-template <typename Real>
-__global__ void dmom_out_kernel(const Real *__restrict__ dMom, double *__restrict__ dst, long long N, long long c0,
-                                long long n) {
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-    const long long i = c0 + k;
-    dst[i] = (double)dMom[i];
-    dst[N + i] = (double)dMom[N + i];
-    dst[2 * N + i] = (double)dMom[2 * N + i];
-  }
-}
 
 }  // namespace
 
@@ -205,19 +228,11 @@ cudaError_t launch_fields_in(const double *stage, long long N, long long c0, lon
   return cudaGetLastError();
 }
 
-template <typename Real>
-cudaError_t launch_dmom_out(const Real *dMom, double *dst, long long N, long long c0, long long n, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  dmom_out_kernel<Real><<<grid_for(n, 256), 256, 0, s>>>(dMom, dst, N, c0, n);
-  return cudaGetLastError();
-}
 
 template cudaError_t launch_fields_in<float>(const double *, long long, long long, long long, bool, float *, float *,
                                              float *, float *, double *, int *, cudaStream_t);
 template cudaError_t launch_fields_in<double>(const double *, long long, long long, long long, bool, double *,
                                               double *, double *, double *, double *, int *, cudaStream_t);
-template cudaError_t launch_dmom_out<float>(const float *, double *, long long, long long, long long, cudaStream_t);
-template cudaError_t launch_dmom_out<double>(const double *, double *, long long, long long, long long, cudaStream_t);
 
 template <typename Real>
 cudaError_t launch_convert_in(const double *src, Real *dst, long long n, cudaStream_t s) {
@@ -234,17 +249,40 @@ cudaError_t launch_convert_out(const Real *src, double *dst, long long n, cudaSt
 }
 
 template <typename Real>
-cudaError_t launch_isotropic(const double *T, Real *I, int M, long long N, cudaStream_t s) {
+cudaError_t launch_isotropic(const double *T, Real *I, int M, long long N, bool quad, cudaStream_t s) {
+  if constexpr (sizeof(Real) == 4) {
+    if (quad) {
+      isotropic_quad_kernel<<<grid_for(N, 256), 256, 0, s>>>(T, reinterpret_cast<float4 *>(I), M, N);
+      return cudaGetLastError();
+    }
+  }
   isotropic_kernel<Real><<<grid_for(N, 256), 256, 0, s>>>(T, I, M, N);
   return cudaGetLastError();
 }
 
 template <typename Real>
-cudaError_t launch_moments(const Real *I, const Real *ang, int M, long long N, Real *mom, cudaStream_t s) {
-  if constexpr (sizeof(Real) == 4)
-    moments_kernel_f<<<grid_for(N, 256), 256, 0, s>>>(I, ang, M, N, mom);
-  else
+cudaError_t launch_moments(const Real *I, const Real *ang, int M, long long N, bool quad, double *mom,
+                           cudaStream_t s) {
+  if constexpr (sizeof(Real) == 4) {
+    if (quad)
+      moments_kernel_f<true><<<grid_for(N, 256), 256, 0, s>>>(I, ang, M, N, mom);
+    else
+      moments_kernel_f<false><<<grid_for(N, 256), 256, 0, s>>>(I, ang, M, N, mom);
+  } else {
     moments_kernel<Real><<<grid_for(N, 256), 256, 0, s>>>(I, ang, M, N, mom);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quad_in(const double *src, float *dst, long long off, long long n, long long N, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  quad_in_kernel<<<grid_for(n, 256), 256, 0, s>>>(src, dst, off, n, N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quad_out(const float *src, double *dst, long long off, long long n, long long N, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  quad_out_kernel<<<grid_for(n, 256), 256, 0, s>>>(src, dst, off, n, N);
   return cudaGetLastError();
 }
 
@@ -254,12 +292,12 @@ cudaError_t launch_check(const double *x, long long n, double lo, int strict, in
   return cudaGetLastError();
 }
 
-cudaError_t launch_encode_b16(const float *I, const float *E, unsigned short *out, int M, long long N, cudaStream_t s) {
+cudaError_t launch_encode_b16(const float *I, const double *E, unsigned short *out, int M, long long N, cudaStream_t s) {
   encode_b16_kernel<<<grid_for(N, 256), 256, 0, s>>>(I, E, out, M, N);
   return cudaGetLastError();
 }
 
-cudaError_t launch_decode_b16(const unsigned short *in, const float *E, double *out, long long off, long long n,
+cudaError_t launch_decode_b16(const unsigned short *in, const double *E, double *out, long long off, long long n,
                               long long N, cudaStream_t s) {
   decode_b16_kernel<<<grid_for(n, 256), 256, 0, s>>>(in, E, out, off, n, N);
   return cudaGetLastError();
@@ -269,9 +307,10 @@ template cudaError_t launch_convert_in<float>(const double *, float *, long long
 template cudaError_t launch_convert_in<double>(const double *, double *, long long, cudaStream_t);
 template cudaError_t launch_convert_out<float>(const float *, double *, long long, cudaStream_t);
 template cudaError_t launch_convert_out<double>(const double *, double *, long long, cudaStream_t);
-template cudaError_t launch_isotropic<float>(const double *, float *, int, long long, cudaStream_t);
-template cudaError_t launch_isotropic<double>(const double *, double *, int, long long, cudaStream_t);
-template cudaError_t launch_moments<float>(const float *, const float *, int, long long, float *, cudaStream_t);
-template cudaError_t launch_moments<double>(const double *, const double *, int, long long, double *, cudaStream_t);
+template cudaError_t launch_isotropic<float>(const double *, float *, int, long long, bool, cudaStream_t);
+template cudaError_t launch_isotropic<double>(const double *, double *, int, long long, bool, cudaStream_t);
+template cudaError_t launch_moments<float>(const float *, const float *, int, long long, bool, double *, cudaStream_t);
+template cudaError_t launch_moments<double>(const double *, const double *, int, long long, bool, double *,
+                                            cudaStream_t);
 
 }  // namespace rtg

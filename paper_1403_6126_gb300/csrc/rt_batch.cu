@@ -30,7 +30,7 @@ const BatchVariant &batch_variant(int i) {
 
 static size_t variant_smem(const BatchVariant &v, int dim, int M, bool vel) {
   const TileShape t = dim == 1 ? v.t1 : dim == 2 ? v.t2 : v.t3;
-  return stepk::smem_bytes2(dim, M, vel, t.tx, t.ty, t.tz);
+  return stepk::smem_bytes_q(dim, M, vel, t.tx, t.ty, t.tz, false);
 }
 
 bool batch_fits(int dim, int M, bool vel) {
@@ -248,7 +248,7 @@ rt_status rt_batch_autotune(rt_batch *b, int trial_steps, double *ms, int *chose
     const size_t N = (size_t)c->N;
     RT_BCUDA(cudaMemcpyAsync(c->stage, c->T, N * sizeof(double), cudaMemcpyDeviceToDevice, b->stream));
     RT_BCUDA(cudaMemcpyAsync(c->stage + N, c->dEgas, N * sizeof(double), cudaMemcpyDeviceToDevice, b->stream));
-    RT_BCUDA(cudaMemcpyAsync(c->stage + 2 * N, c->dMom, 3 * N * c->rs, cudaMemcpyDeviceToDevice, b->stream));
+    RT_BCUDA(cudaMemcpyAsync(c->stage + 2 * N, c->dMom, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, b->stream));
     RT_BCUDA(cudaMemcpyAsync(&flags[i], c->flags, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
   }
   RT_BCUDA(cudaStreamSynchronize(b->stream));
@@ -286,7 +286,7 @@ rt_status rt_batch_autotune(rt_batch *b, int trial_steps, double *ms, int *chose
     const size_t N = (size_t)c->N;
     RT_BCUDA(cudaMemcpyAsync(c->T, c->stage, N * sizeof(double), cudaMemcpyDeviceToDevice, b->stream));
     RT_BCUDA(cudaMemcpyAsync(c->dEgas, c->stage + N, N * sizeof(double), cudaMemcpyDeviceToDevice, b->stream));
-    RT_BCUDA(cudaMemcpyAsync(c->dMom, c->stage + 2 * N, 3 * N * c->rs, cudaMemcpyDeviceToDevice, b->stream));
+    RT_BCUDA(cudaMemcpyAsync(c->dMom, c->stage + 2 * N, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, b->stream));
     RT_BCUDA(cudaMemcpyAsync(c->flags, &flags[i], sizeof(int), cudaMemcpyHostToDevice, b->stream));
   }
   RT_BCUDA(cudaStreamSynchronize(b->stream));

@@ -4,7 +4,7 @@
 // tile set; all shapes of a set have the same thread count (one per cell).
 #pragma once
 
-#include "rt_step_pair.cuh"
+#include "rt_step_quad.cuh"
 
 namespace rtg {
 
@@ -47,11 +47,11 @@ __global__ void __launch_bounds__(NT, 512 / NT)
       cur = w.prob;
     }
     if (desc.dim == 3)
-      stepk::process_tile2<3, VEL, X3, Y3, Z3>(desc, tid, w.tbx, w.tby, w.tbz, smem);
+      stepk::process_tile_q<3, VEL, X3, Y3, Z3, false, 2>(desc, nullptr, tid, w.tbx, w.tby, w.tbz, smem);
     else if (desc.dim == 2)
-      stepk::process_tile2<2, VEL, X2, Y2, 1>(desc, tid, w.tbx, w.tby, 0, smem);
+      stepk::process_tile_q<2, VEL, X2, Y2, 1, false, 2>(desc, nullptr, tid, w.tbx, w.tby, 0, smem);
     else
-      stepk::process_tile2<1, VEL, NT, 1, 1>(desc, tid, w.tbx, 0, 0, smem);
+      stepk::process_tile_q<1, VEL, NT, 1, 1, false, 2>(desc, nullptr, tid, w.tbx, 0, 0, smem);
   }
 }
 

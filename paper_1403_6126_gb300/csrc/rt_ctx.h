@@ -19,22 +19,28 @@ struct rt_ctx {
   cudaStream_t stream = nullptr;
   bool fp64 = false;
   bool bf16 = false;  // intensities stored as bf16 deviations (RT_BF16)
-  size_t rs = 4;      // bytes per stored real (cell data; intensities too unless bf16)
+  size_t rs = 4;      // bytes per stored real of the cell data (rho, sigma, v)
   size_t rsI = 4;     // bytes per stored intensity
+  bool quad = false;  // float intensities in the quad-interleaved layout (RT_FP32)
+  size_t I_bytes = 0; // bytes of one intensity buffer
   float *qscr = nullptr;  // bf16 storage: float [M][N] scratch for Q_m
   bool has_v = false, material_set = false, intensity_set = false;
   rtg::TileShape tile{0, 0, 0};
   // device state (Real = double or float)
   void *I[2] = {nullptr, nullptr};
-  void *mom[2] = {nullptr, nullptr};
+  double *mom[2] = {nullptr, nullptr};   // E, F, P [10][N], double for every precision
   int cur = 0;
   void *rho = nullptr, *sa = nullptr, *ss = nullptr, *v = nullptr;
   double *T = nullptr, *dEgas = nullptr;
-  void *dMom = nullptr, *ang = nullptr, *inflow = nullptr;
+  double *dMom = nullptr;                 // Delta(rho v) [3][N]
+  void *ang = nullptr, *inflow = nullptr;
   int *flags = nullptr;  // [0] Newton failures, [1] input scan
   double *stage = nullptr;
   long long stage_len = 0;
   std::vector<double> host_n, host_w, host_inflow;
+  // the angle table [M][4] and inflow table [6][M] rounded to float, as the
+  // device tables hold them (launch-parameter tables of the float kernel)
+  std::vector<float> host_angf, host_inflowf;
   // captured multi-step graph
   cudaGraphExec_t graph = nullptr;
   double graph_dt = 0;
@@ -69,8 +75,15 @@ StepArgs<Real> make_args(rt_ctx *c, double dt);
 bool velocity_on(const rt_ctx *c);
 // Records msg as this thread's last error and returns s.
 rt_status set_error(rt_status s, const std::string &msg);
+// RT_OK, or RT_E_INVALID (message prefixed by `where`) when the Newton
+// options of o are out of range.
+rt_status check_newton_options(const rt_options &o, const char *where);
 // Device bytes rt_create allocates for N cells and M angles.
 size_t context_bytes(long long N, int M, bool fp64);
+// Launch of the fused step for context c (its host tables feed the float
+// kernel's launch-parameter table).
+cudaError_t launch_ctx_step(rt_ctx *c, const StepArgs<float> &a, bool vel, TileShape t);
+cudaError_t launch_ctx_step(rt_ctx *c, const StepArgs<double> &a, bool vel, TileShape t);
 // Whether a problem of this dimension and angle count fits the batch tile.
 bool batch_fits(int dim, int M, bool vel);
 }  // namespace rtg

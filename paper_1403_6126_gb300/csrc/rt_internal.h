@@ -25,23 +25,28 @@ struct StepArgs {
   Real dx[3];         // cell sizes
   double dt_d, kv_per_rho;  // dt and R/(gamma-1) in double
   int hold_T, estimate_v;
+  int newton_max_it;  // Newton on T: iteration cap and stopping tolerance
+  double newton_rtol;
   const Real *ang;    // [M][4]: n_x, n_y, n_z, W
   const Real *inflow; // [3][2][M]
-  const Real *I_in;   // [M][N]
-  Real *I_out;        // [M][N]
+  // Intensities.  Double: angle-major [M][N].  Float: quad-interleaved,
+  // ceil(M/4) planes of float4 ([q][c] holds angles 4q .. 4q+3 of cell c,
+  // angles past M zero).
+  const Real *I_in;
+  Real *I_out;
   const Real *rho, *sa, *ss;  // [N]
   const Real *v;      // [3][N]
   const double *T_in; // [N]
   double *T_out;      // [N]
-  const Real *mom_in; // [10][N] moments of I_in
-  Real *mom_out;      // [10][N] moments of I_out
+  const double *mom_in;  // [10][N] moments of I_in
+  double *mom_out;       // [10][N] moments of I_out
   double *dEgas;      // [N]
-  Real *dMom;         // [3][N]
+  double *dMom;       // [3][N]
   int *status;        // [0]: cells whose T Newton failed
   // bf16 storage (RT_BF16, float kernels only): the stored value of angle m
-  // in cell c is delta = I / J - 1 with J = E / (4 pi) of the cell's stored
-  // moments; I_in / I_out are unused then and Q is a float [M][N] scratch
-  // for the right-hand sides Q_m.  Null otherwise.
+  // in cell c (angle-major [M][N]) is delta = I / J - 1 with J = E / (4 pi)
+  // of the cell's stored moments; I_in / I_out are unused then and Q is a
+  // float [M][N] scratch for the right-hand sides Q_m.  Null otherwise.
   const unsigned short *I16_in;
   unsigned short *I16_out;
   float *Q;
@@ -76,25 +81,43 @@ bool tile_ok(int dim, int M, bool has_v, TileShape t);
 template <typename Real>
 int tile_candidates(int dim, int M, bool has_v, TileShape *out);
 
-// The bf16-storage step (RT_BF16): one compiled tile per dimension, the
-// default shape of the float kernel.
+// The bf16-storage step (RT_BF16): one compiled tile per dimension (16x8x4,
+// 32x16, 512); choose_tile_b16 gives it, or false when its shared memory
+// does not fit M angles.
 cudaError_t launch_b16(const StepArgs<float> &a, int dim, bool vel, TileShape t, cudaStream_t s);
+bool choose_tile_b16(int dim, int M, TileShape *out);
+
+// The float step on the quad-interleaved layout (RT_FP32).  host_ang [M][4]
+// and host_inflow [6][M] are the float tables the device holds: for M <= 80
+// they travel as a launch-parameter table, larger sets read the device
+// tables a.ang / a.inflow into shared memory.
+cudaError_t launch_step_quad(const StepArgs<float> &a, const float *host_ang, const float *host_inflow, int dim,
+                             bool vel, TileShape t, cudaStream_t s);
 
 // Elementwise helpers (all stream-ordered).
 template <typename Real>
 cudaError_t launch_convert_in(const double *src, Real *dst, long long n, cudaStream_t s);
 template <typename Real>
 cudaError_t launch_convert_out(const Real *src, double *dst, long long n, cudaStream_t s);
+// Isotropic equilibrium T^4/(4 pi): angle-major [M][N] (double), or the
+// quad-interleaved float layout with zero padding (quad = true).
 template <typename Real>
-cudaError_t launch_isotropic(const double *T, Real *I, int M, long long N, cudaStream_t s);
+cudaError_t launch_isotropic(const double *T, Real *I, int M, long long N, bool quad, cudaStream_t s);
+// E, F, P (double [10][N]) of an intensity field (angle-major, or the quad
+// layout when quad is set).
 template <typename Real>
-cudaError_t launch_moments(const Real *I, const Real *ang, int M, long long N, Real *mom, cudaStream_t s);
+cudaError_t launch_moments(const Real *I, const Real *ang, int M, long long N, bool quad, double *mom,
+                           cudaStream_t s);
+// Elements [off, off + n) of an angle-major double field (element i is angle
+// i / N of cell i % N) into / out of the quad-interleaved float layout.
+cudaError_t launch_quad_in(const double *src, float *dst, long long off, long long n, long long N, cudaStream_t s);
+cudaError_t launch_quad_out(const float *src, double *dst, long long off, long long n, long long N, cudaStream_t s);
 
 // bf16 storage: encode a float intensity array [M][N] as deviations from
 // the mean intensity of each cell (E [N] its energy density), and decode
 // elements [off, off + n) of a stored array to doubles.
-cudaError_t launch_encode_b16(const float *I, const float *E, unsigned short *out, int M, long long N, cudaStream_t s);
-cudaError_t launch_decode_b16(const unsigned short *in, const float *E, double *out, long long off, long long n,
+cudaError_t launch_encode_b16(const float *I, const double *E, unsigned short *out, int M, long long N, cudaStream_t s);
+cudaError_t launch_decode_b16(const unsigned short *in, const double *E, double *out, long long off, long long n,
                               long long N, cudaStream_t s);
 
 // Scans n doubles: ORs bit 0 into *flag for a non-finite value or one below
@@ -107,8 +130,5 @@ cudaError_t launch_check(const double *x, long long n, double lo, int strict, in
 template <typename Real>
 cudaError_t launch_fields_in(const double *stage, long long N, long long c0, long long n, bool convert, Real *rho,
                              Real *sa, Real *ss, Real *v, double *T, int *flag, cudaStream_t s);
-// Delta(rho v) of cells [c0, c0 + n), all three components, to double.
-template <typename Real>
-cudaError_t launch_dmom_out(const Real *dMom, double *dst, long long N, long long c0, long long n, cudaStream_t s);
 
 }  // namespace rtg

@@ -204,6 +204,10 @@ rt_status rt_server_create(size_t hbm_budget_bytes, const rt_options *opts, rt_s
   if (!s) return fail(RT_E_NOMEM, "rt_server_create: host allocation");
   rt_options_default(&s->opt);
   if (opts) s->opt = *opts;
+  if (rt_status st = rtg::check_newton_options(s->opt, "rt_server_create"); st != RT_OK) {
+    delete s;
+    return st;
+  }
   s->budget = hbm_budget_bytes;
   cudaError_t e = cudaGetDevice(&s->device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);

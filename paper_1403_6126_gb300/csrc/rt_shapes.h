@@ -17,9 +17,16 @@
 #define RT_SHAPES_D1(X) X(256, 1, 1) X(128, 1, 1) X(64, 1, 1) X(32, 1, 1)
 
 namespace rtg {
+namespace stepk {
+template <int P>
+struct QTable;
+}
 // Launchers of the compiled shapes, one translation unit per group; they
 // return cudaErrorInvalidConfiguration for a shape that is not compiled.
-cudaError_t launch_f3(const StepArgs<float> &a, bool vel, TileShape t, cudaStream_t s);
-cudaError_t launch_f12(const StepArgs<float> &a, int dim, bool vel, TileShape t, cudaStream_t s);
+// qt: the launch-parameter table of the float kernel, or NULL for angle sets
+// beyond it (the table is then built in shared memory).
+cudaError_t launch_f3(const StepArgs<float> &a, const stepk::QTable<40> *qt, bool vel, TileShape t, cudaStream_t s);
+cudaError_t launch_f12(const StepArgs<float> &a, const stepk::QTable<40> *qt, int dim, bool vel, TileShape t,
+                       cudaStream_t s);
 cudaError_t launch_d(const StepArgs<double> &a, int dim, bool vel, TileShape t, cudaStream_t s);
 }  // namespace rtg

@@ -632,12 +632,15 @@ __device__ __forceinline__ void process_tile(const StepArgs<Real> &a, int tid, i
     const Real c4 = dt * (Real(2) * a.P * sa * (H1 - S1 * invC) + beta * omJ1);
     bool ok = false;
     if constexpr (sizeof(Real) == 8) {
-      // same iteration and stopping rule as the FP64 reference: Newton from
-      // T^n until |dT| <= 1e-13 T, then one more step
+      // the FP64 reference's iteration and stopping rule (with its default
+      // options): Newton from T^n until |dT| <= newton_rtol T, then one more
+      // step, at most newton_max_it steps
       const double c0 = (double)c0r - kv * T0, c4d = (double)c4;
+      const double rtol = a.newton_rtol;
+      const int max_it = a.newton_max_it;
       double T = T0;
       int extra = -1, it;
-      for (it = 0; it < 60; ++it) {
+      for (it = 0; it < max_it; ++it) {
         double T3 = T * T * T;
         double f = c4d * T3 * T + kv * T + c0;
         double fp = 4.0 * c4d * T3 + kv;
@@ -646,9 +649,9 @@ __device__ __forceinline__ void process_tile(const StepArgs<Real> &a, int tid, i
         double dT = Tn - T;
         T = Tn;
         if (extra == 0) break;
-        if (extra < 0 && fabs(dT) <= 1e-13 * T) extra = 0;
+        if (extra < 0 && fabs(dT) <= rtol * T) extra = 0;
       }
-      ok = it < 60;
+      ok = it < max_it;
       T1 = T;
     } else {
       // Newton on delta = T - T^n in float, then one double-precision step

@@ -237,12 +237,12 @@ __device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid,
     sl_g[s] = (int)(g[0] + (long long)a.n[0] * (g[1] + (long long)a.n[1] * g[2]));
     if (VEL) {
       const long long cc = sl_g[s];
-      const float w3 = float(3.0 / (4.0 * kPi)) * a.mom_in[cc];
+      const float w3 = float(3.0 / (4.0 * kPi)) * (float)a.mom_in[cc];
       sl_w[s][0] = w3 * a.v[cc];
       sl_w[s][1] = w3 * a.v[N + cc];
       sl_w[s][2] = w3 * a.v[2 * N + cc];
     }
-    if (B16) sl_J[B16 ? s : 0] = b16_mean(a.mom_in[sl_g[s]]);
+    if (B16) sl_J[B16 ? s : 0] = b16_mean((float)a.mom_in[sl_g[s]]);
   }
 
   // ---- slope-extension items (see process_tile) -------------------------------
@@ -318,10 +318,10 @@ __device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid,
     if (VEL) {
       for (int d = 0; d < 3; ++d) vin[d] = a.v[d * N + c];
       if (a.estimate_v) {
-        const float E = a.mom_in[c];
+        const float E = (float)a.mom_in[c];
         const float h = 0.5f * dt * (sa + ss);
         for (int d = 0; d < 3; ++d) {
-          const float Fd = a.mom_in[(1 + d) * N + c], Pdd = a.mom_in[(4 + d) * N + c];
+          const float Fd = (float)a.mom_in[(1 + d) * N + c], Pdd = (float)a.mom_in[(4 + d) * N + c];
           const float num = rho * vin[d] + h * (C * rho * vin[d] + a.P * Fd);
           const float den = rho + h * (C * rho + a.P * (E + Pdd) / C);
           vt[d] = num / den;
@@ -569,7 +569,9 @@ __device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid,
     const float T0f = (float)T0, kvf = (float)kv;
     float d = 0.0f;
     int extra = -1, it;
-    for (it = 0; it < 40; ++it) {
+    const int max_it = a.newton_max_it;
+    const float rtol = fmaxf((float)a.newton_rtol, 1e-6f);
+    for (it = 0; it < max_it; ++it) {
       const float T = T0f + d, T2 = T * T;
       const float f = c4 * T2 * T2 + kvf * d + c0r;
       const float fp = 4.0f * c4 * T2 * T + kvf;
@@ -578,14 +580,14 @@ __device__ __forceinline__ void process_tile2(const StepArgs<float> &a, int tid,
       const float step = dn - d;
       d = dn;
       if (extra == 0) break;
-      if (extra < 0 && fabsf(step) <= 1e-6f * (T0f + d)) extra = 0;
+      if (extra < 0 && fabsf(step) <= rtol * (T0f + d)) extra = 0;
     }
     double dd = (double)d;
     const double T = T0 + dd, T2 = T * T;
     const double f = (double)c4 * T2 * T2 + kv * dd + (double)c0r;
     const float fp = 4.0f * c4 * (float)(T2 * T) + kvf;
     dd -= f * (double)(1.0f / fp);
-    if (!(it < 40 && (T0 + dd) > 0.0)) atomicAdd(a.status, 1);
+    if (!(it < max_it && (T0 + dd) > 0.0)) atomicAdd(a.status, 1);
     T1 = T0 + dd;
   }
   const float T1r = (float)T1, T1sq = T1r * T1r;

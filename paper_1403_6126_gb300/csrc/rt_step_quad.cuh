@@ -1,0 +1,729 @@
+// Fused radiation-transfer step with float intensities in a quad-interleaved
+// layout (Jiang, Stone & Davis 2014, arXiv:1403.6126, secs. 3-4).
+//
+// Storage.  The intensity of a float context is kept as Q = ceil(M/4) planes
+// of float4: I[q][c] holds angles 4q .. 4q+3 of cell c (angles past M are
+// zero padding).  A thread reads or writes the four angles of its cell with
+// one 128-bit access, and the 16 x-consecutive cells of a tile row cover two
+// whole 128-byte lines.
+//
+// Same method, tile geometry and reading of the paper as process_tile2
+// (rt_step_pair.cuh): one thread per cell, every per-angle quantity carried
+// as a pair of angles in packed FP32, four phases per angle pair separated by
+// CTA barriers (stage I~ = I - IV/C and IV, van Leer half slopes, one flux per
+// face, Delta F).  The work is split differently:
+//  * Transport loop (the phases with barriers): per pair only Delta F_m is
+//    formed and written to the output array, two pairs per 128-bit store; no
+//    implicit-step quantity lives in these registers.
+//  * Source loop (no barriers): reads I^n and Delta F back (both L2 resident:
+//    the tile read them microseconds before), forms the right-hand sides Q_m
+//    of the implicit step that Delta F belongs to (sec. 4.2: the larger
+//    opacity) and overwrites Delta F with Q_m, and takes every angle sum of
+//    Steps 4 and 5 in one pass (the intensity sums and the sums that depend
+//    only on the velocity and the opacities).
+//  * Per-cell solve (the scalar T^4 equation of sec. 4.3 and the 2x2 system
+//    of sec. 4.4), then the final loop writes I^{n+1} over Q_m and takes the
+//    quadrature of sec. 3.
+// The per-pair constants come from a table in the launch parameters (the
+// constant bank: warp-uniform loads that use neither shared memory nor its
+// bandwidth) when TAB_PARAM is set, else from shared memory (the persistent
+// multi-problem kernel, whose problems each have their own table).
+//
+// Moments E, F, P and the momentum source are written in double; the
+// compensated float sums (hi, lo) are combined into the double exactly.
+#pragma once
+
+#include "rt_step_pair.cuh"
+
+namespace rtg {
+
+namespace stepk {
+
+// Pairs a launch-parameter table can hold: 40 (80 angles) for the
+// single-problem kernels, 128 (256 angles) for the allocation-free step.
+constexpr int kQTabPairsSmall = 40;
+constexpr int kQTabPairsLarge = 128;
+
+// Launch-parameter table: kTab2 float2 entries per angle pair (see kTab2)
+// for an even number of pairs (a missing last pair is zeros: weightless,
+// motionless angles), and the inflow intensities [3][2][4 * P/2] per face
+// (zero for angles past M).
+template <int P>
+struct QTable {
+  float2 e[P * kTab2];
+  float inflow[6][2 * P];
+};
+
+// Host side: the table entries exactly as the device would form them (the
+// same float products in the same order), so that kernels reading either
+// table give bitwise the same result.  ang: [M][4] floats (n_x, n_y, n_z, W);
+// inflow: [6][M] floats or NULL.
+template <int P>
+inline void fill_qtable(QTable<P> *t, const float *ang, int M, float C, const float dtdx[3], const float *inflow) {
+  for (int i = 0; i < P * kTab2; ++i) t->e[i] = make_float2(0.0f, 0.0f);
+  for (int f = 0; f < 6; ++f)
+    for (int m = 0; m < 2 * P; ++m) t->inflow[f][m] = (inflow && m < M) ? inflow[f * M + m] : 0.0f;
+  for (int m = 0; m < M && m < 2 * P; ++m) {
+    const int k = m / 2, h = m % 2;
+    const float W = ang[4 * m + 3];
+    for (int j = 0; j < kTab2; ++j) {
+      float val;
+      if (j < 3) {
+        val = ang[4 * m + j];
+      } else if (j == 3) {
+        val = W;
+      } else {
+        const int d = (j - 4) % 3, kind = (j - 4) / 3;
+        const float mu = ang[4 * m + d], amu = mu < 0.0f ? -mu : mu;
+        const float hC = 0.5f * C;
+        val = kind == 0   ? hC * mu * dtdx[d]
+              : kind == 1 ? hC * amu * dtdx[d]
+              : kind == 2 ? mu * dtdx[d]
+                          : W * mu;
+      }
+      float2 &e = t->e[kTab2 * k + j];
+      (h == 0 ? e.x : e.y) = val;
+    }
+  }
+}
+
+// Shared memory of one CTA of the quad kernel: the float2 staging arrays
+// (I~, IV, their slopes, one flux per face), plus the pair table when it is
+// not a launch parameter.
+__host__ __device__ inline size_t smem_bytes_q(int dim, int M, bool has_v, int tx, int ty, int tz, bool tab_param) {
+  Geo g;
+  g.init(dim, tx, ty, tz);
+  const size_t q = has_v ? 2 : 1, pairs = 2 * (size_t)((M + 3) / 4);
+  const size_t n2 = (tab_param ? 0 : kTab2 * pairs) + q * g.nbox + q * g.sl_off[3] + g.fx_off[3];
+  return n2 * sizeof(f2) + 16;
+}
+
+// Exact float -> double by bit assembly (integer pipe: the FP64 pipe is the
+// scarce one on this GPU).  Subnormal floats (below 1.2e-38) give 0.
+__device__ __forceinline__ double f2d_exact(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned e = (b >> 23) & 0xffu;
+  const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b >> 3) & 0xfffffu);
+  const unsigned lo = b << 29;
+  return e == 0u ? 0.0 : __hiloint2double((int)hi, (int)lo);
+}
+
+// A compensated pair sum read out as a double: hi - lo, exact in double
+// (one FP64 add).
+__device__ __forceinline__ double ksum_double(const KSum2 &s) { return f2d_exact(s.hi) - f2d_exact(s.lo); }
+
+template <int DIM, bool VEL, int TX, int TY, int TZ, bool TAB_PARAM, int TP>
+__device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const QTable<TP> *qt, int tid, int tbx,
+                                               int tby, int tbz, unsigned char *smem_raw) {
+  using G = GeoT<DIM, TX, TY, TZ>;
+  constexpr int nthr = G::ncell;
+  constexpr int kSlots = slots_for(DIM, TX, TY, TZ);
+  constexpr int kExt = (G::next + nthr - 1) / nthr;
+  constexpr int kLow = (G::nlow + nthr - 1) / nthr;
+  static_assert(kSlots <= 4 && kExt <= 2 && kLow <= 2, "tile halo too large for the per-thread work items");
+  const int M = a.M, K = (M + 1) / 2, NQ = (M + 3) / 4, K2 = 2 * NQ;
+  const long long N = a.N;
+  const int org[3] = {tbx * TX, tby * TY, tbz * TZ};
+  const int bstride[3] = {1, G::B0, G::B0 * G::B1};
+
+  __syncthreads();   // the previous tile of a persistent CTA is done with shared memory
+  f2 *s_tab = reinterpret_cast<f2 *>(smem_raw);          // [K2][kTab2] (shared table only)
+  f2 *s_It = s_tab + (TAB_PARAM ? 0 : kTab2 * K2);       // [nbox]
+  f2 *s_IV = s_It + G::nbox;                             // [nbox]   (VEL)
+  f2 *s_sI = s_IV + (VEL ? G::nbox : 0);                 // slopes of I~
+  f2 *s_sV = s_sI + G::SL3;                              // slopes of IV (VEL)
+  f2 *s_fx = s_sV + (VEL ? G::SL3 : 0);                  // face fluxes
+  auto tab = [&](int k, int j) -> f2 {
+    if constexpr (TAB_PARAM)
+      return qt->e[kTab2 * k + j];
+    else
+      return s_tab[kTab2 * k + j];
+  };
+  auto inflow = [&](int face, int m) -> float {
+    if constexpr (TAB_PARAM)
+      return qt->inflow[face][m];
+    else
+      return m < M ? a.inflow[face * M + m] : 0.0f;
+  };
+
+  const float C = a.C, invC = a.invC, dt = a.dt;
+
+  // ---- shared pair table (as fill_qtable) --------------------------------------
+  if constexpr (!TAB_PARAM) {
+    for (int i = tid; i < kTab2 * K2; i += nthr) {
+      const int k = i / kTab2, j = i % kTab2;
+      float v[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int m = 2 * k + h;
+        float val = 0.0f;
+        if (m < M) {
+          const float W = a.ang[4 * m + 3];
+          if (j < 3) {
+            val = a.ang[4 * m + j];
+          } else if (j == 3) {
+            val = W;
+          } else {
+            const int d = (j - 4) % 3, kind = (j - 4) / 3;
+            const float mu = a.ang[4 * m + d], amu = mu < 0.0f ? -mu : mu;
+            const float hC = 0.5f * C;
+            val = kind == 0   ? hC * mu * a.dtdx[d]
+                  : kind == 1 ? hC * amu * a.dtdx[d]
+                  : kind == 2 ? mu * a.dtdx[d]
+                              : W * mu;
+          }
+        }
+        v[h] = val;
+      }
+      s_tab[i] = make_float2(v[0], v[1]);
+    }
+  }
+
+  // ---- own cell ---------------------------------------------------------------
+  const int loc[3] = {tid % TX, tid / (TX * TZ), (tid / TX) % TZ};
+  const int gx = org[0] + loc[0], gy = org[1] + loc[1], gz = org[2] + loc[2];
+  const bool valid = gx < a.n[0] && gy < a.n[1] && gz < a.n[2];
+  const long long c = valid ? gx + (long long)a.n[0] * (gy + (long long)a.n[1] * gz) : 0;
+  int bo = 0;
+  for (int d = 0; d < DIM; ++d) bo += (loc[d] + kHalo) * bstride[d];
+  int own_sl[3], own_fx[3];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    own_sl[d] = G::sl_off(d) + G::sl_idx(d, loc[0], loc[1], loc[2]);
+    own_fx[d] = G::fx_off(d) + G::fx_idx(d, loc[d], loc[0], loc[1], loc[2]);
+  }
+
+  // ---- staging slots (see process_tile) ---------------------------------------
+  int sl_box[kSlots], sl_code[kSlots], sl_g[kSlots];
+  float sl_w[kSlots][3];
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) {
+    const int k = tid + s * nthr;
+    sl_box[s] = -1; sl_code[s] = 0; sl_g[s] = 0;
+    sl_w[s][0] = sl_w[s][1] = sl_w[s][2] = 0.0f;
+    if (k >= G::ncross) continue;
+    int b[3] = {0, 0, 0};
+    if (k < G::ncell) {
+      b[0] = k % TX + (DIM >= 1 ? kHalo : 0);
+      b[2] = (k / TX) % TZ + (DIM >= 3 ? kHalo : 0);
+      b[1] = k / (TX * TZ) + (DIM >= 2 ? kHalo : 0);
+    } else {
+      int kk = k - G::ncell;
+      int d = 0;
+      while (kk >= 2 * kHalo * G::P(d)) { kk -= 2 * kHalo * G::P(d); ++d; }
+      const int layer = kk / G::P(d), o = kk % G::P(d);
+      const int side = layer / kHalo, h = layer % kHalo;
+      const int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;
+      const int bd = side == 0 ? h : G::T(d) + kHalo + h;
+      const int b1v = o % G::T(a1) + (a1 < DIM ? kHalo : 0), b2v = o / G::T(a1) + (a2 < DIM ? kHalo : 0);
+      b[0] = d == 0 ? bd : (a1 == 0 ? b1v : b2v);
+      b[1] = d == 1 ? bd : (a1 == 1 ? b1v : b2v);
+      b[2] = d == 2 ? bd : (a1 == 2 ? b1v : b2v);
+    }
+    sl_box[s] = b[0] + G::B0 * (b[1] + G::B1 * b[2]);
+    int g[3], code = 0;
+    for (int d = 0; d < 3; ++d) {
+      g[d] = d < DIM ? org[d] + b[d] - kHalo : 0;
+      if (d < DIM && (g[d] < 0 || g[d] >= a.n[d])) {
+        if (code == 0) code = 1 + 2 * d + (g[d] >= a.n[d] ? 1 : 0);
+        g[d] = map_in(g[d], a.n[d], a.bc[d][0], a.bc[d][1]);
+      }
+    }
+    if (code) {
+      const int axis = (code - 1) >> 1, side = (code - 1) & 1;
+      const int kind = a.bc[axis][side];
+      code = (kind == BC_VACUUM || kind == BC_INFLOW) ? (1 | (kind == BC_INFLOW ? 2 : 0) | (axis << 2) | (side << 4)) : 0;
+    }
+    sl_code[s] = code;
+    sl_g[s] = (int)(g[0] + (long long)a.n[0] * (g[1] + (long long)a.n[1] * g[2]));
+    if (VEL) {
+      const long long cc = sl_g[s];
+      const float w3 = float(3.0 / (4.0 * kPi)) * (float)a.mom_in[cc];
+      sl_w[s][0] = w3 * a.v[cc];
+      sl_w[s][1] = w3 * a.v[N + cc];
+      sl_w[s][2] = w3 * a.v[2 * N + cc];
+    }
+  }
+
+  // ---- slope-extension items (see process_tile) -------------------------------
+  int ext_bb[kExt > 0 ? kExt : 1], ext_st[kExt > 0 ? kExt : 1], ext_si[kExt > 0 ? kExt : 1];
+#pragma unroll
+  for (int j = 0; j < kExt; ++j) {
+    ext_bb[j] = 0; ext_st[j] = 0; ext_si[j] = -1;
+    const int e = tid + j * nthr;
+    if (e >= G::next) continue;
+    int ee = e, d = 0;
+    while (ee >= 2 * G::P(d)) { ee -= 2 * G::P(d); ++d; }
+    const int side = ee / G::P(d), o = ee % G::P(d);
+    const int a1x = d == 0 ? 1 : 0;
+    const int ld = side == 0 ? -1 : G::T(d), l1v = o % G::T(a1x), l2v = o / G::T(a1x);
+    const int l0 = d == 0 ? ld : (a1x == 0 ? l1v : l2v);
+    const int l1 = d == 1 ? ld : (a1x == 1 ? l1v : l2v);
+    const int l2 = d == 2 ? ld : (a1x == 2 ? l1v : l2v);
+    ext_bb[j] = (l0 + kHalo) + G::B0 * ((DIM >= 2 ? l1 + kHalo : 0) + G::B1 * (DIM >= 3 ? l2 + kHalo : 0));
+    ext_st[j] = G::bstride(d);
+    ext_si[j] = G::sl_off(d) + G::sl_idx(d, l0, l1, l2);
+  }
+
+  // ---- face constants (see process_tile) ---------------------------------------
+  float fu_al[3], fu_hv[3], fu_wl[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) { fu_al[d] = 1.0f; fu_hv[d] = 1.0f; fu_wl[d] = 0.5f; }
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    int gl[3] = {min(gx, a.n[0] - 1), min(gy, a.n[1] - 1), min(gz, a.n[2] - 1)};
+    int gu[3] = {gl[0], gl[1], gl[2]};
+    gu[d] = map_in((d == 0 ? gx : d == 1 ? gy : gz) + 1, a.n[d], a.bc[d][0], a.bc[d][1]);
+    face_consts<float, VEL>(a, d, gl, gu, &fu_al[d], &fu_hv[d], &fu_wl[d]);
+  }
+  int lf_d[kLow > 0 ? kLow : 1], lf_bb[kLow > 0 ? kLow : 1], lf_si[kLow > 0 ? kLow : 1],
+      lf_sstep[kLow > 0 ? kLow : 1], lf_fx[kLow > 0 ? kLow : 1];
+  float lf_al[kLow > 0 ? kLow : 1], lf_hv[kLow > 0 ? kLow : 1], lf_wl[kLow > 0 ? kLow : 1];
+#pragma unroll
+  for (int j = 0; j < kLow; ++j) {
+    lf_d[j] = 0; lf_bb[j] = 0; lf_si[j] = 0; lf_sstep[j] = 1; lf_fx[j] = -1;
+    lf_al[j] = 1.0f; lf_hv[j] = 1.0f; lf_wl[j] = 0.5f;
+    int e = tid + j * nthr;
+    if (e >= G::nlow) continue;
+    int d = 0;
+    while (e >= G::P(d)) { e -= G::P(d); ++d; }
+    const int a1x = d == 0 ? 1 : 0;
+    const int l1v = e % G::T(a1x), l2v = e / G::T(a1x);
+    const int l[3] = {d == 0 ? 0 : (a1x == 0 ? l1v : l2v), d == 1 ? 0 : (a1x == 1 ? l1v : l2v),
+                      d == 2 ? 0 : (a1x == 2 ? l1v : l2v)};
+    const int bb = (l[0] + kHalo) + G::B0 * ((DIM >= 2 ? l[1] + kHalo : 0) + G::B1 * (DIM >= 3 ? l[2] + kHalo : 0));
+    const int st = G::bstride(d);
+    lf_d[j] = d;
+    lf_bb[j] = bb - st;
+    lf_si[j] = G::sl_off(d) + G::sl_idx(d, d == 0 ? -1 : l[0], d == 1 ? -1 : l[1], d == 2 ? -1 : l[2]);
+    lf_sstep[j] = G::sl_step(d);
+    lf_fx[j] = G::fx_off(d) + G::fx_idx(d, 0, l[0], l[1], l[2]);
+    int gu[3] = {min(org[0] + l[0], a.n[0] - 1), min(org[1] + (DIM >= 2 ? l[1] : 0), a.n[1] - 1),
+                 min(org[2] + (DIM >= 3 ? l[2] : 0), a.n[2] - 1)};
+    int gl[3] = {gu[0], gu[1], gu[2]};
+    const int od = d == 0 ? org[0] : d == 1 ? org[1] : org[2], nd = d == 0 ? a.n[0] : d == 1 ? a.n[1] : a.n[2];
+    const int kl = d == 0 ? a.bc[0][0] : d == 1 ? a.bc[1][0] : a.bc[2][0];
+    const int kh = d == 0 ? a.bc[0][1] : d == 1 ? a.bc[1][1] : a.bc[2][1];
+    const int gud = min(od, nd - 1), gld = map_in(od - 1, nd, kl, kh);
+    if (d == 0) { gu[0] = gud; gl[0] = gld; } else if (d == 1) { gu[1] = gud; gl[1] = gld; } else { gu[2] = gud; gl[2] = gld; }
+    face_consts<float, VEL>(a, d, gl, gu, &lf_al[j], &lf_hv[j], &lf_wl[j]);
+  }
+
+  // ---- transport: Delta F_m of every angle pair ---------------------------------
+  const float4 *I4 = reinterpret_cast<const float4 *>(a.I_in);
+  float4 *O4 = reinterpret_cast<float4 *>(a.I_out);
+  float4 pf[kSlots];   // quad j of each staged cell
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) pf[s] = sl_box[s] >= 0 ? I4[sl_g[s]] : make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();   // the shared table is complete
+
+  const float4 *qin = I4;
+  float4 *qout = O4 + c;
+  for (int j = 0; j < NQ; ++j) {
+    f2 dFa = dup(0.0f);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = 2 * j + h;
+      if (h == 1 && k >= K) {   // odd pair count: the last quad holds one pair
+        if (valid) *qout = make_float4(dFa.x, dFa.y, 0.0f, 0.0f);
+        break;
+      }
+      const f2 nx = tab(k, 0), ny = tab(k, 1), nz = tab(k, 2);
+      const int m = 2 * k;
+      // ---- phase 1: stage I~ and IV of the cross cells ---------------------
+      f2 I0 = dup(0.0f), q0 = dup(0.0f), p0 = dup(0.0f);
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s) {
+        if (sl_box[s] < 0) continue;
+        f2 I = h == 0 ? make_float2(pf[s].x, pf[s].y) : make_float2(pf[s].z, pf[s].w);
+        if (sl_code[s]) {
+          const int axis = (sl_code[s] >> 2) & 3, side = (sl_code[s] >> 4) & 1;
+          const f2 mu = tab(k, axis);
+          const bool in0 = side ? (mu.x < 0.0f) : (mu.x > 0.0f);
+          const bool in1 = side ? (mu.y < 0.0f) : (mu.y > 0.0f);
+          const bool infl = (sl_code[s] & 2) != 0;
+          if (in0) I.x = infl ? inflow(axis * 2 + side, m) : 0.0f;
+          if (in1) I.y = infl ? inflow(axis * 2 + side, m + 1) : 0.0f;
+        }
+        f2 IV = dup(0.0f), It = I;
+        if (VEL) {
+          IV = p_fma(nx, dup(sl_w[s][0]), p_fma(ny, dup(sl_w[s][1]), p_mul(nz, dup(sl_w[s][2]))));
+          It = p_fma(IV, dup(-invC), I);
+          s_IV[sl_box[s]] = IV;
+        }
+        s_It[sl_box[s]] = It;
+        if (s == 0) { I0 = I; q0 = It; p0 = IV; }
+      }
+      (void)I0;
+      if (h == 1 && j + 1 < NQ) {
+        qin += N;
+#pragma unroll
+        for (int s = 0; s < kSlots; ++s)
+          if (sl_box[s] >= 0) pf[s] = qin[sl_g[s]];
+      }
+      __syncthreads();
+
+      // ---- phase 2: half slopes of the own cell and of the extension cells ---
+      f2 sI[3], sV[3];
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        const int st = bstride[d];
+        sI[d] = vl_half2(s_It[bo - st], q0, s_It[bo + st]);
+        s_sI[own_sl[d]] = sI[d];
+        if (VEL) {
+          sV[d] = vl_half2(s_IV[bo - st], p0, s_IV[bo + st]);
+          s_sV[own_sl[d]] = sV[d];
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < kExt; ++e) {
+        if (ext_si[e] < 0) continue;
+        const int bb = ext_bb[e], st = ext_st[e];
+        s_sI[ext_si[e]] = vl_half2(s_It[bb - st], s_It[bb], s_It[bb + st]);
+        if (VEL) s_sV[ext_si[e]] = vl_half2(s_IV[bb - st], s_IV[bb], s_IV[bb + st]);
+      }
+      __syncthreads();
+
+      // ---- phase 3: face fluxes (pre-multiplied by dt/dx) --------------------
+      f2 fhi[3];
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        const int st = bstride[d];
+        const int sn = own_sl[d] + G::sl_step(d);
+        fhi[d] = face_flux2<VEL>(q0, sI[d], s_It[bo + st], s_sI[sn], p0, VEL ? sV[d] : dup(0.0f),
+                                 VEL ? s_IV[bo + st] : dup(0.0f), VEL ? s_sV[sn] : dup(0.0f), dup(fu_al[d]),
+                                 dup(fu_hv[d]), dup(fu_wl[d]), tab(k, 4 + d), tab(k, 7 + d), tab(k, 10 + d));
+        s_fx[own_fx[d] + G::fx_step(d)] = fhi[d];
+      }
+#pragma unroll
+      for (int e = 0; e < kLow; ++e) {
+        if (lf_fx[e] < 0) continue;
+        const int d = lf_d[e], bb = lf_bb[e], st = d == 0 ? 1 : bstride[d == 1 ? 1 : 2];
+        const int si = lf_si[e], si1 = lf_si[e] + lf_sstep[e];
+        s_fx[lf_fx[e]] = face_flux2<VEL>(s_It[bb], s_sI[si], s_It[bb + st], s_sI[si1], VEL ? s_IV[bb] : dup(0.0f),
+                                         VEL ? s_sV[si] : dup(0.0f), VEL ? s_IV[bb + st] : dup(0.0f),
+                                         VEL ? s_sV[si1] : dup(0.0f), dup(lf_al[e]), dup(lf_hv[e]), dup(lf_wl[e]),
+                                         tab(k, 4 + d), tab(k, 7 + d), tab(k, 10 + d));
+      }
+      __syncthreads();
+
+      // ---- phase 4: Delta F of the pair ---------------------------------------
+      f2 dF = dup(0.0f);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) dF = p_add(dF, p_sub(s_fx[own_fx[d]], fhi[d]));
+      if (h == 0) {
+        dFa = dF;
+      } else if (valid) {
+        *qout = make_float4(dFa.x, dFa.y, dF.x, dF.y);
+      }
+    }
+    qout += N;
+  }
+
+  if (!valid) return;
+
+  // ---- per-cell constants of the implicit steps (see process_tile) -------------
+  float rho = a.rho[c], sa = a.sa[c], ss = a.ss[c], vt[3] = {0, 0, 0}, vin[3] = {0, 0, 0};
+  const double T0 = a.T_in[c];
+  if (VEL) {
+    for (int d = 0; d < 3; ++d) vin[d] = a.v[d * N + c];
+    if (a.estimate_v) {
+      const float E = (float)a.mom_in[c];
+      const float h = 0.5f * dt * (sa + ss);
+      for (int d = 0; d < 3; ++d) {
+        const float Fd = (float)a.mom_in[(1 + d) * N + c], Pdd = (float)a.mom_in[(4 + d) * N + c];
+        const float num = rho * vin[d] + h * (C * rho * vin[d] + a.P * Fd);
+        const float den = rho + h * (C * rho + a.P * (E + Pdd) / C);
+        vt[d] = num / den;
+      }
+    } else {
+      vt[0] = vin[0]; vt[1] = vin[1]; vt[2] = vin[2];
+    }
+  }
+  const bool to_scat = ss > sa;
+  const float v2 = vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2];
+  const float A0 = 1.0f + dt * C * sa, A1 = dt * sa, kap = dt * sa / C;
+  const float a0 = 1.0f + dt * C * ss, a1 = dt * ss;
+  const float bq0 = -dt * C * ss - dt * ss * v2 / C, bq1 = 2.0f * dt * ss, bq2 = -dt * ss / C;
+  const float cq = -3.0f * dt * ss;
+  const float apb0 = 1.0f - a1 * v2 * invC, apb2 = -a1 * invC;
+  const float rd0 = VEL ? 0.0f : fast_rcp(A0);
+  const float ra0 = VEL ? 0.0f : fast_rcp(a0);
+  const float nA1C = -A1 * C, na1C = -a1 * C;
+  const bool abs_inc = A1 * C < 1.0f;
+  const f2 sc = dup(to_scat ? 1.0f : 0.0f), nsc = dup(to_scat ? 0.0f : 1.0f);
+
+  // ---- source loop: Q_m over Delta F, every angle sum of Steps 4 and 5 ---------
+  // U_k = sum W vn^k r / d, AQ = sum Q / a, BQ = sum b Q / a, pre = sum W n (I^n
+  // + Delta F); T_k = sum W vn^k / d; Ap = sum pe/a, Ad = sum 1/(d a), As1 =
+  // sum 1/a, Acc = sum c/a, Bp, Bd, Bcc the b-weighted ones, B1p = sum (a'+b)/a
+  KSum2 U0, AQ;
+  U0.zero();
+  AQ.zero();
+  f2 U1 = dup(0.0f), U2 = dup(0.0f), BQ = dup(0.0f), pre0 = dup(0.0f), pre1 = dup(0.0f), pre2 = dup(0.0f);
+  f2 T0p = dup(0.0f), T1p = dup(0.0f), T2p = dup(0.0f), T3p = dup(0.0f);
+  f2 Apk = dup(0.0f), Adk = dup(0.0f), As1k = dup(0.0f), Acck = dup(0.0f);
+  f2 Bpk = dup(0.0f), Bdk = dup(0.0f), Bcck = dup(0.0f), B1pk = dup(0.0f);
+  {
+    const float4 *pi = I4 + c;
+    float4 *pq = O4 + c;
+    for (int j = 0; j < NQ; ++j) {
+      const float4 i4 = *pi, d4 = *pq;
+      f2 Qv[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = 2 * j + h;
+        const f2 nx = tab(k, 0), ny = tab(k, 1), nz = tab(k, 2), Wm = tab(k, 3);
+        const f2 I0 = h == 0 ? make_float2(i4.x, i4.y) : make_float2(i4.z, i4.w);
+        const f2 dF = h == 0 ? make_float2(d4.x, d4.y) : make_float2(d4.z, d4.w);
+        const f2 full = p_add(I0, dF);
+        f2 vn = dup(0.0f), rd = dup(rd0), ra = dup(ra0);
+        if (VEL) {
+          vn = p_fma(nx, dup(vt[0]), p_fma(ny, dup(vt[1]), p_mul(nz, dup(vt[2]))));
+          rd = p_rcp(p_fma(dup(-A1), vn, dup(A0)));
+          ra = p_rcp(p_fma(dup(-a1), vn, dup(a0)));
+        }
+        // r_m / d_m as r_m - (d_m - 1) r_m / d_m (see process_tile2)
+        const f2 rm = p_fma(nsc, dF, I0);   // I^n, plus Delta F when it goes to Step 4
+        const f2 xdn = VEL ? p_fma(dup(A1), vn, dup(nA1C)) : dup(nA1C);
+        const f2 qa = abs_inc ? p_fma(p_mul(rm, xdn), rd, rm) : p_mul(rm, rd);
+        const f2 Q = p_fma(sc, dF, qa);
+        Qv[h] = Q;
+        const f2 wq = p_mul(Wm, qa);
+        U0.part = p_add(U0.part, wq);
+        if (VEL) {
+          const f2 y1 = p_mul(wq, vn);
+          U1 = p_add(U1, y1);
+          U2 = p_fma(y1, vn, U2);
+        }
+        const f2 wa = p_mul(Wm, ra);
+        AQ.part = p_fma(wa, Q, AQ.part);
+        const f2 bm = VEL ? p_fma(vn, p_fma(dup(bq2), vn, dup(bq1)), dup(bq0)) : dup(bq0);
+        const f2 bwa = p_mul(bm, wa);
+        BQ = p_fma(bwa, Q, BQ);
+        pre0 = p_fma(tab(k, 13), full, pre0);
+        pre1 = p_fma(tab(k, 14), full, pre1);
+        pre2 = p_fma(tab(k, 15), full, pre2);
+        const f2 wrd = p_mul(Wm, rd);
+        T0p = p_add(T0p, wrd);
+        if (VEL) {
+          const f2 x1 = p_mul(wrd, vn), x2 = p_mul(x1, vn);
+          T1p = p_add(T1p, x1);
+          T2p = p_add(T2p, x2);
+          T3p = p_fma(x2, vn, T3p);
+        }
+        const f2 pe = p_mul(dup(A1), p_mul(p_fma(dup(3.0f), vn, dup(C)), rd));   // e_m / d_m
+        Apk = p_fma(wa, pe, Apk);
+        Adk = p_fma(wa, rd, Adk);
+        As1k = p_add(As1k, wa);
+        Bpk = p_fma(bwa, pe, Bpk);
+        Bdk = p_fma(bwa, rd, Bdk);
+        if (VEL) {
+          const f2 cm = p_mul(dup(cq), vn);
+          Acck = p_fma(cm, wa, Acck);
+          Bcck = p_fma(cm, bwa, Bcck);
+          B1pk = p_fma(wa, p_fma(vn, p_fma(dup(apb2), vn, dup(a1)), dup(apb0)), B1pk);
+        } else {
+          B1pk = p_add(B1pk, wa);
+        }
+      }
+      *pq = make_float4(Qv[0].x, Qv[0].y, Qv[1].x, Qv[1].y);
+      if ((j & 1) == 1) { U0.fold(); AQ.fold(); }
+      pi += N;
+      pq += N;
+    }
+  }
+  const float T0s = T0p.x + T0p.y, T1s = T1p.x + T1p.y, T2s = T2p.x + T2p.y, T3s = T3p.x + T3p.y;
+  const float Ap = Apk.x + Apk.y, Ad = Adk.x + Adk.y, As1 = As1k.x + As1k.y, Acc = Acck.x + Acck.y;
+  const float Bp = Bpk.x + Bpk.y, Bd = Bdk.x + Bdk.y, Bcc = Bcck.x + Bcck.y, B1p = B1pk.x + B1pk.y;
+
+  // ---- Step 4 solve (see process_tile) -----------------------------------------
+  const float Wr = U0.total(), Vr = U1.x + U1.y, Gr = v2 * Wr + (U2.x + U2.y);
+  const float W1 = T0s, V1 = T1s, G1 = v2 * T0s + T2s;
+  const float Ve = A1 * (C * T1s + 3.0f * T2s);
+  const float Ge = A1 * (C * (v2 * T0s + T2s) + 3.0f * (v2 * T1s + T3s));
+  const float Wq = T0s - 4.0f * A1 * T1s;     // sum W (d - e) / d
+  const float den = 1.0f + kap * G1;
+  const float S0 = Gr / den, S1 = Ge / den;
+  const float J0 = Wr - kap * S0 * W1;
+  const float H0 = Vr - kap * S0 * V1, H1 = Ve - kap * S1 * V1;
+  const float omJ1 = Wq + kap * S1 * W1;   // 1 - dJ/dtheta, cancellation-free
+  const double kv = (double)rho * a.kv_per_rho;
+  double T1 = T0;
+  if (!a.hold_T) {
+    const float beta = a.P * C * (1.0f - v2 * invC * invC) * sa;
+    const float c0r = dt * (float(8.0 * kPi) * a.P * sa * (H0 - S0 * invC) - float(4.0 * kPi) * beta * J0);
+    const float c4 = dt * (2.0f * a.P * sa * (H1 - S1 * invC) + beta * omJ1);
+    // Newton on delta = T - T^n in float, then one double-precision step (see
+    // process_tile2); the stopping tolerance is the caller's (at least 1e-6:
+    // the float iterate cannot resolve finer steps)
+    const float T0f = (float)T0, kvf = (float)kv;
+    const float rtol = fmaxf((float)a.newton_rtol, 1e-6f);
+    const int max_it = a.newton_max_it;
+    float d = 0.0f;
+    int extra = -1, it;
+    for (it = 0; it < max_it; ++it) {
+      const float T = T0f + d, T2 = T * T;
+      const float f = c4 * T2 * T2 + kvf * d + c0r;
+      const float fp = 4.0f * c4 * T2 * T + kvf;
+      float dn = d - f / fp;
+      if (!(T0f + dn > 0.0f)) dn = 0.5f * T - T0f;
+      const float step = dn - d;
+      d = dn;
+      if (extra == 0) break;
+      if (extra < 0 && fabsf(step) <= rtol * (T0f + d)) extra = 0;
+    }
+    double dd = (double)d;
+    const double T = T0 + dd, T2 = T * T;
+    const double f = (double)c4 * T2 * T2 + kv * dd + (double)c0r;
+    const float fp = 4.0f * c4 * (float)(T2 * T) + kvf;
+    dd -= f * (double)(1.0f / fp);
+    if (!(it < max_it && (T0 + dd) > 0.0)) atomicAdd(a.status, 1);
+    T1 = T0 + dd;
+  }
+  const float T1r = (float)T1, T1sq = T1r * T1r;
+  const float th = T1sq * T1sq * float(1.0 / (4.0 * kPi));
+  const float S = S0 + th * S1;
+  const float kS = kap * S;
+
+  // ---- Step 5 solve: (1+B1) s1 + Bc s2 = Br,  A1 s1 + (1+Ac) s2 = Ar -------
+  const float Ar = AQ.total() + th * Ap - kS * Ad;
+  const float Br = (BQ.x + BQ.y) + th * Bp - kS * Bd;
+  const float m11 = B1p, m12 = Bcc, m21 = As1, m22 = 1.0f + Acc;
+  const float det = m11 * m22 - m12 * m21;
+  const float s1 = (Br * m22 - m12 * Ar) / det;
+  const float s2 = (m11 * Ar - m21 * Br) / det;
+
+  // ---- I^{n+1} over Q_m, quadrature (sec. 3) ---------------------------------
+  KSum2 mE, mF[3], mP[6];
+  mE.zero();
+  for (int i = 0; i < 3; ++i) mF[i].zero();
+  for (int i = 0; i < 6; ++i) mP[i].zero();
+  {
+    float4 *pq = O4 + c;
+    float4 q4 = *pq;
+    for (int j = 0; j < NQ; ++j) {
+      const float4 cur = q4;
+      if (j + 1 < NQ) q4 = pq[N];   // the next quad, loaded before this one is overwritten
+      f2 Iv[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = 2 * j + h;
+        const f2 nx = tab(k, 0), ny = tab(k, 1), nz = tab(k, 2), Wm = tab(k, 3);
+        const f2 Q = h == 0 ? make_float2(cur.x, cur.y) : make_float2(cur.z, cur.w);
+        f2 vn = dup(0.0f), rd = dup(rd0), ra = dup(ra0);
+        if (VEL) {
+          vn = p_fma(nx, dup(vt[0]), p_fma(ny, dup(vt[1]), p_mul(nz, dup(vt[2]))));
+          rd = p_rcp(p_fma(dup(-A1), vn, dup(A0)));
+          ra = p_rcp(p_fma(dup(-a1), vn, dup(a0)));
+        }
+        const f2 pe = p_mul(dup(A1), p_mul(p_fma(dup(3.0f), vn, dup(C)), rd));
+        const f2 rs = p_fma(pe, dup(th), p_fma(rd, dup(-kS), Q));        // r'_m
+        const f2 cm = p_mul(dup(cq), vn);
+        // I^{n+1} = (r' - s1 - c s2) / a' taken as r' - ((a' - 1) r' + s1 + c s2) / a'
+        const f2 xan = VEL ? p_fma(dup(a1), vn, dup(na1C)) : dup(na1C);   // -(a'_m - 1)
+        f2 I1 = p_fma(p_fma(xan, rs, p_fma(cm, dup(-s2), dup(-s1))), ra, rs);
+        if (2 * k >= M) I1.x = 0.0f;          // padding angles stay zero
+        if (2 * k + 1 >= M) I1.y = 0.0f;
+        Iv[h] = I1;
+        const f2 wi = p_mul(Wm, I1);
+        mE.part = p_add(mE.part, wi);
+        const f2 wx = p_mul(nx, wi), wy = p_mul(ny, wi), wz = p_mul(nz, wi);
+        mF[0].part = p_add(mF[0].part, wx);
+        mF[1].part = p_add(mF[1].part, wy);
+        mF[2].part = p_add(mF[2].part, wz);
+        mP[0].part = p_fma(nx, wx, mP[0].part);
+        mP[1].part = p_fma(ny, wy, mP[1].part);
+        mP[2].part = p_fma(nz, wz, mP[2].part);
+        mP[3].part = p_fma(ny, wx, mP[3].part);
+        mP[4].part = p_fma(nz, wx, mP[4].part);
+        mP[5].part = p_fma(nz, wy, mP[5].part);
+      }
+      *pq = make_float4(Iv[0].x, Iv[0].y, Iv[1].x, Iv[1].y);
+      if ((j & 1) == 1) {
+        mE.fold();
+        for (int i = 0; i < 3; ++i) mF[i].fold();
+        for (int i = 0; i < 6; ++i) mP[i].fold();
+      }
+      pq += N;
+    }
+  }
+  const double fourpi = 4.0 * kPi;
+  mE.fold();
+  a.mom_out[c] = fourpi * ksum_double(mE);
+  float post[3];
+  for (int i = 0; i < 3; ++i) {
+    mF[i].fold();
+    post[i] = mF[i].hi;
+    a.mom_out[(1 + i) * N + c] = fourpi * ksum_double(mF[i]);
+  }
+  for (int i = 0; i < 6; ++i) {
+    mP[i].fold();
+    a.mom_out[(4 + i) * N + c] = fourpi * ksum_double(mP[i]);
+  }
+
+  // ---- gas sources (sec. 4.3: Delta E_T, eqs. momentumchange, kinetichange)
+  const float kmom = -float(4.0 * kPi) * a.P * invC;
+  float dEK = 0.0f;
+  const float pre[3] = {pre0.x + pre0.y, pre1.x + pre1.y, pre2.x + pre2.y};
+  for (int i = 0; i < 3; ++i) {
+    const float dmom = kmom * (post[i] - pre[i]);
+    a.dMom[i * N + c] = f2d_exact(dmom);
+    const float m0 = rho * vin[i];
+    dEK += ((m0 + dmom) * (m0 + dmom) - m0 * m0) / (2.0f * rho);
+  }
+  a.T_out[c] = T1;
+  a.dEgas[c] = kv * (T1 - T0) + (double)dEK;
+}
+
+template <int DIM, bool VEL, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(TX * TY * TZ, 1)
+    step_kernel_q(const StepArgs<float> a, const __grid_constant__ QTable<kQTabPairsSmall> qt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int o = a.outer_begin;
+  process_tile_q<DIM, VEL, TX, TY, TZ, true, kQTabPairsSmall>(a, &qt, threadIdx.x, blockIdx.x + (DIM == 1 ? o : 0),
+                                                              blockIdx.y + (DIM == 2 ? o : 0),
+                                                              blockIdx.z + (DIM == 3 ? o : 0), smem_raw);
+}
+
+// Same kernel for angle sets beyond the launch-parameter table: the table is
+// built in shared memory.
+template <int DIM, bool VEL, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(TX * TY * TZ, 1) step_kernel_qs(const StepArgs<float> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int o = a.outer_begin;
+  process_tile_q<DIM, VEL, TX, TY, TZ, false, 2>(a, nullptr, threadIdx.x, blockIdx.x + (DIM == 1 ? o : 0),
+                                                 blockIdx.y + (DIM == 2 ? o : 0), blockIdx.z + (DIM == 3 ? o : 0),
+                                                 smem_raw);
+}
+
+// Host: the table of a launch (M <= 2 * kQTabPairsSmall).
+inline void make_qtable(const StepArgs<float> &a, const float *host_ang, const float *host_inflow,
+                        QTable<kQTabPairsSmall> *t) {
+  fill_qtable(t, host_ang, a.M, a.C, a.dtdx, host_inflow);
+}
+
+template <int DIM, bool VEL, int TX, int TY, int TZ>
+cudaError_t launch_shape_q(const StepArgs<float> &a, const QTable<kQTabPairsSmall> *qt, cudaStream_t s) {
+  const bool param = qt != nullptr;
+  const size_t sm = smem_bytes_q(DIM, a.M, VEL, TX, TY, TZ, param);
+  dim3 block(TX * TY * TZ);
+  dim3 grid((a.n[0] + TX - 1) / TX, (a.n[1] + TY - 1) / TY, (a.n[2] + TZ - 1) / TZ);
+  if (a.outer_count > 0) (DIM == 3 ? grid.z : DIM == 2 ? grid.y : grid.x) = a.outer_count;
+  if (param) {
+    auto kern = step_kernel_q<DIM, VEL, TX, TY, TZ>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, block, sm, s>>>(a, *qt);
+  } else {
+    auto kern = step_kernel_qs<DIM, VEL, TX, TY, TZ>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, block, sm, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace stepk
+
+}  // namespace rtg

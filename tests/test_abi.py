@@ -129,3 +129,41 @@ def test_fault_inject_arguments():
         rt.rt_fault_inject(rt.RT_FAULT_ALLOC, -1)
     assert e.value.status == rt.RT_E_INVALID
     rt.rt_fault_inject(rt.RT_FAULT_NONE)
+
+
+def test_newton_options_defaults_and_validation():
+    # the T^4 Newton solve of sec. 4.3: defaults are the FP64 reference's rule
+    # (1e-13 relative step, at most 60 steps); out-of-range settings are
+    # refused by every entry point that takes options, before device work
+    o = rt.rt_options_default()
+    assert o.newton_max_it == 60 and o.newton_rtol == 1e-13
+    n, w = oracle.angles.by_name("s2")
+    n, w = np.ascontiguousarray(n), np.ascontiguousarray(w)
+    for it, tol in ((0, 1e-13), (1001, 1e-13), (60, 0.0), (60, 1e-2), (60, float("nan"))):
+        o = rt.rt_options_default()
+        o.newton_max_it, o.newton_rtol = it, tol
+        _expect(rt.RT_E_INVALID, rt.rt_create, _grid(), _angles(n, w), 10.0, 1.0, o)
+        assert "newton" in rt.rt_last_error()
+        _expect(rt.RT_E_INVALID, rt.rt_server_create, 1 << 30, o)
+        f = rt.rt_noalloc_fields()
+        for i, (k, _) in enumerate(f._fields_):
+            setattr(f, k, 4096 * (i + 1))   # never dereferenced: validation comes first
+        _expect(rt.RT_E_INVALID, rt.rt_step_noalloc, _grid(), _angles(n, w), 10.0, 1.0, o, 1e-3, f)
+
+
+def test_noalloc_refuses_in_place_buffers_on_the_host():
+    # rt_step_noalloc reads the step-n intensity and moments of neighbouring
+    # cells while it writes the new ones: one buffer for both is refused
+    n, w = oracle.angles.by_name("gl8")
+    n, w = np.ascontiguousarray(n), np.ascontiguousarray(w)
+    o = rt.rt_options_default()
+    for same in ("I", "mom"):
+        f = rt.rt_noalloc_fields()
+        for i, (k, _) in enumerate(f._fields_):
+            setattr(f, k, 4096 * (i + 1))
+        if same == "I":
+            f.I_out = f.I_in
+        else:
+            f.mom_out = f.mom_in
+        _expect(rt.RT_E_INVALID, rt.rt_step_noalloc, _grid(), _angles(n, w), 10.0, 1.0, o, 1e-3, f)
+        assert "different buffers" in rt.rt_last_error()
