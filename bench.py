@@ -187,22 +187,25 @@ def _context(wl, n, w, stream=None, precision=None):
     return ctx
 
 
-def cpu_baseline(wl_name, steps, warmup, sample_n=None):
-    """Times the FP64 oracle, as it stands, on a bounded sample of the
-    workload: the same recipe on a smaller grid, OpenMP over the host cores."""
+def cpu_baseline(wl_name, steps, warmup, sample_n=None, threads=None, wl=None):
+    """Times the FP64 oracle, as it stands, on the workload (or, with
+    sample_n, the same recipe on a smaller box): `steps` timed steps after
+    `warmup` untimed ones, OpenMP over `threads` host threads (default: all
+    cores)."""
     import oracle
     from paper_1403_6126_gb300 import workloads as wlmod
-    kw = {}
-    if wl_name == "box3d":
-        kw = dict(n=sample_n or 32)
-    wl = wlmod.by_name(wl_name, **kw)
+    if wl is None:
+        kw = {}
+        if wl_name == "box3d" and sample_n:
+            kw = dict(n=sample_n)
+        wl = wlmod.by_name(wl_name, **kw)
     n, w = oracle.angles.by_name(wl["angles"])
     dx = tuple((wl["hi"][d] - wl["lo"][d]) / wl["shape"][2 - d] for d in range(3))
     inflow = {face: wlmod.inflow_values(rule, n) for face, rule in wl["inflow"].items()}
     p = oracle.Problem(wl["shape"], dx, n, w, C=wl["C"], P=wl["P"], dim=wl["dim"], bc=wl["bc"], inflow=inflow,
                        gamma=wl["gamma"], R=wl["R"], hold_T=wl["hold_T"], estimate_v=wl["estimate_v"])
     cores = os.cpu_count() or 1
-    oracle.set_threads(cores)
+    oracle.set_threads(threads or cores)
     I = wlmod.initial_intensity(wl, len(w))
     T = wl["T"].copy()
     dt = oracle.cfl_dt(p, wl["cfl"])
@@ -215,10 +218,34 @@ def cpu_baseline(wl_name, steps, warmup, sample_n=None):
         I, T = out["I"], out["T"]
     el = time.perf_counter() - t0
     units = p.N * p.M * steps
-    return dict(value=units / el, unit="cell-angle updates/s", cores=oracle.max_threads(), kind="oracle",
-                sample="%s recipe at %s cells x %d angles, %d timed steps (+%d warm-up), FP64 C oracle, OpenMP"
-                       % (wl_name, "x".join(str(s) for s in wl["shape"][::-1]), p.M, steps, warmup),
-                seconds=el)
+    used = oracle.max_threads()
+    oracle.set_threads(cores)
+    return dict(value=units / el, unit="cell-angle updates/s", cores=used, kind="oracle",
+                sample="%s recipe at %s cells x %d angles, %d timed steps (+%d warm-up), FP64 C oracle, %d thread%s"
+                       % (wl_name, "x".join(str(s) for s in wl["shape"][::-1] if s > 1), p.M, steps, warmup, used,
+                          "s (OpenMP)" if used > 1 else ""),
+                seconds=el, steps=steps, seconds_per_step=el / max(1, steps))
+
+
+def cpu_baselines(args):
+    """The oracle timed on the host cores: the headline figure on the timed
+    workload itself (full size, two steps after one warm-up, every core),
+    beside it one step of a 48^3 sample on one thread (the per-core rate),
+    and the two small workloads (the 1-D slab in full, 2000 steps; the 2-D
+    shadow problem over 10 steps), all on every core."""
+    from paper_1403_6126_gb300 import workloads as wlmod
+    kw = {"n": args.n} if args.workload == "box3d" and args.n else {}
+    head = cpu_baseline(args.workload, 2, 1, wl=wlmod.by_name(args.workload, **kw))
+    out = {k: head[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    one = cpu_baseline(args.workload, 1, 0, sample_n=48 if args.workload == "box3d" else None, threads=1)
+    out["single_thread"] = {k: one[k] for k in ("value", "unit", "cores", "sample")}
+    slab = wlmod.slab1d()
+    s0 = cpu_baseline("slab1d", slab["steps"], 0, wl=slab)
+    sh = cpu_baseline("shadow2d", 10, 0, wl=wlmod.shadow2d())
+    out["small_configs"] = {
+        "slab1d": {k: s0[k] for k in ("value", "unit", "cores", "sample", "seconds_per_step")},
+        "shadow2d": {k: sh[k] for k in ("value", "unit", "cores", "sample", "seconds_per_step")}}
+    return out
 
 
 def arm_config(args, world):
@@ -243,14 +270,21 @@ def arm_config(args, world):
 
 
 def run_reference(args):
+    """The FP64 oracle on the host cores, on the GPU arm's own workload at
+    full size.  At about 3 s per step of the 128^3 x 80 box on 16 cores, the
+    run times at most --ref-steps steps (after one warm-up step) so that it
+    ends within a few minutes; the line's steps and warmup say what was run."""
     world, rank, _ = _dist()
     if rank != 0:
         return 0
-    res = cpu_baseline(args.workload, args.steps, args.warmup, sample_n=args.cpu_sample_n)
+    from paper_1403_6126_gb300 import workloads as wlmod
+    kw = {"n": args.n} if args.workload == "box3d" and args.n else {}
+    steps, warmup = max(1, min(args.steps, args.ref_steps)), min(args.warmup, 1)
+    res = cpu_baseline(args.workload, steps, warmup, wl=wlmod.by_name(args.workload, **kw))
     line = {
         "impl": "reference", "metric": "cell-angle updates/s", "value": res["value"], "unit": res["unit"],
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * res["seconds"] / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
+        "n_gpus": world, "steps": steps, "warmup": warmup,
+        "ms_per_step": 1e3 * res["seconds"] / steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": arm_config(args, world),
         "cpu_baseline": {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")},
@@ -366,8 +400,7 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.workload, 2, 1, sample_n=max(args.cpu_sample_n, 48))
-        cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cpu = cpu_baselines(args)
     if rank == 0:
         config = arm_config(args, world)
         assert config["cells"] == N and config["angles"] == M and abs(config["dt"] - dt) <= 1e-15 * dt
@@ -802,7 +835,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-n", type=int, default=32)
+    ap.add_argument("--ref-steps", type=int, default=5, help="most oracle steps the reference arm times")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")

@@ -219,6 +219,14 @@ rt_status rt_sync(rt_ctx *ctx);
  * waits for the stream. */
 rt_status rt_moments(rt_ctx *ctx, double *E, double *F, double *P);
 
+/* Eddington tensor of the current intensity (sec. 2: f = K/J, the radiation
+ * pressure over the energy density, f = P_r / E_r; sec. 5.2 reads f_xx and
+ * f_yy of a beamed field): f[q*N + c] = P_r[q][c] / E_r[c] for q = xx, yy,
+ * zz, xy, xz, yz, in double, from the stored moments; 0 where E_r = 0.
+ * Host pointer (the call waits for the stream) or, with device_ptrs, a
+ * device pointer.  RT_E_STATE before an intensity is set. */
+rt_status rt_eddington(rt_ctx *ctx, double *f);
+
 /* Gas sources of the last step (eqs. momentumchange, kinetichange and the
  * Delta E_T of sec. 4.3): dE_gas = Delta E_T + Delta E_K (N),
  * dMom = Delta(rho v) (3N), T_new = T^{n+1} (N).  NULL skips a field. */

@@ -95,6 +95,7 @@ def lib():
             "rt_sync": (I, [V]),
             "rt_moments": (I, [V, V, V, V]),
             "rt_sources": (I, [V, V, V, V]),
+            "rt_eddington": (I, [V, V]),
             "rt_step_coupled": (I, [V, D, V, V, V, V, V, V, V, V]),
             "rt_get_intensity": (I, [V, V]),
             "rt_destroy": (None, [V]),
@@ -236,6 +237,10 @@ def rt_sync(ctx):
 
 def rt_moments(ctx, E, F, P):
     _check(lib().rt_moments(ctx, _ptr(E), _ptr(F), _ptr(P)), "rt_moments")
+
+
+def rt_eddington(ctx, f):
+    _check(lib().rt_eddington(ctx, _ptr(f)), "rt_eddington")
 
 
 def rt_sources(ctx, dE_gas, dMom, T_new):
@@ -438,6 +443,12 @@ class Context:
         E, F, P = np.zeros(N), np.zeros((3, N)), np.zeros((6, N))
         rt_moments(self.ctx, E, F, P)
         return E, F, P
+
+    def eddington(self):
+        """f = P_r / E_r (6, N): xx, yy, zz, xy, xz, yz."""
+        f = np.zeros((6, self.N))
+        rt_eddington(self.ctx, f)
+        return f
 
     def sources(self):
         N = self.N

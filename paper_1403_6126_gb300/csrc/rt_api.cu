@@ -863,6 +863,17 @@ rt_status rt_moments(rt_ctx *c, double *E, double *F, double *P) {
   return delivered(c);
 }
 
+rt_status rt_eddington(rt_ctx *c, double *f) {
+  rtg::Range nvtx_range("rt_eddington");
+  if (!c || !f) return fail(RT_E_INVALID, "rt_eddington: NULL argument");
+  if (!c->intensity_set) return fail(RT_E_STATE, "rt_eddington: no intensity yet");
+  const long long N = c->N;
+  double *dst = c->opt.device_ptrs ? f : c->stage;
+  RT_CUDA(rtg::launch_eddington(c->mom[c->cur], dst, N, c->stream));
+  if (c->opt.device_ptrs) return RT_OK;
+  return deliver(c, c->stage, f, 6 * N);
+}
+
 rt_status rt_sources(rt_ctx *c, double *dE_gas, double *dMom, double *T_new) {
   rtg::Range nvtx_range("rt_sources");
   if (!c) return fail(RT_E_INVALID, "rt_sources: NULL context");

@@ -154,6 +154,16 @@ __global__ void moments_kernel_f(const float *__restrict__ I, const float *__res
   }
 }
 
+// f = P / E of each cell (sec. 2: f = K/J), one double reciprocal per cell.
+__global__ void eddington_kernel(const double *__restrict__ mom, double *__restrict__ f, long long N) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+    const double E = mom[c];
+    const double rE = E != 0.0 ? 1.0 / E : 0.0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) f[(long long)q * N + c] = mom[(long long)(4 + q) * N + c] * rE;
+  }
+}
+
 // Range tests on the IEEE-754 bit pattern u of a double, in integer
 // arithmetic (FP64 compares run at GB300's low FP64 rate): the finite
 // values are the patterns with |u| below that of +infinity; the positive
@@ -271,6 +281,11 @@ cudaError_t launch_moments(const Real *I, const Real *ang, int M, long long N, b
   } else {
     moments_kernel<Real><<<grid_for(N, 256), 256, 0, s>>>(I, ang, M, N, mom);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eddington(const double *mom, double *f, long long N, cudaStream_t s) {
+  eddington_kernel<<<grid_for(N, 256), 256, 0, s>>>(mom, f, N);
   return cudaGetLastError();
 }
 

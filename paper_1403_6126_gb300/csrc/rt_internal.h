@@ -108,6 +108,9 @@ cudaError_t launch_isotropic(const double *T, Real *I, int M, long long N, bool 
 template <typename Real>
 cudaError_t launch_moments(const Real *I, const Real *ang, int M, long long N, bool quad, double *mom,
                            cudaStream_t s);
+// Eddington tensor f = P / E (6 components, [6][N]) from stored moments
+// [10][N]; 0 where E = 0.
+cudaError_t launch_eddington(const double *mom, double *f, long long N, cudaStream_t s);
 // Elements [off, off + n) of an angle-major double field (element i is angle
 // i / N of cell i % N) into / out of the quad-interleaved float layout.
 cudaError_t launch_quad_in(const double *src, float *dst, long long off, long long n, long long N, cudaStream_t s);

@@ -87,15 +87,15 @@ inline void fill_qtable(QTable<P> *t, const float *ang, int M, float C, const fl
   }
 }
 
-// Shared memory of one CTA of the quad kernel: the float2 staging arrays
-// (I~, IV, their slopes, one flux per face), plus the pair table when it is
-// not a launch parameter.
+// Shared memory of one CTA of the quad kernel: the float4 staging arrays
+// (I~, IV, the slopes of I~, one flux per face), plus the pair table when it
+// is not a launch parameter.
 __host__ __device__ inline size_t smem_bytes_q(int dim, int M, bool has_v, int tx, int ty, int tz, bool tab_param) {
   Geo g;
   g.init(dim, tx, ty, tz);
   const size_t q = has_v ? 2 : 1, pairs = 2 * (size_t)((M + 3) / 4);
-  const size_t n2 = (tab_param ? 0 : kTab2 * pairs) + q * g.nbox + q * g.sl_off[3] + g.fx_off[3];
-  return n2 * sizeof(f2) + 16;
+  const size_t n4 = q * g.nbox + g.sl_off[3] + g.fx_off[3];
+  return (tab_param ? 0 : kTab2 * pairs * sizeof(f2)) + n4 * sizeof(float4) + 16;
 }
 
 // Exact float -> double by bit assembly (integer pipe: the FP64 pipe is the
@@ -106,6 +106,33 @@ __device__ __forceinline__ double f2d_exact(float x) {
   const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b >> 3) & 0xfffffu);
   const unsigned lo = b << 29;
   return e == 0u ? 0.0 : __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ f2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ f2 hi2(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float4 mk4(f2 a, f2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+
+// IV state of two angles at a face, from the upwind cell alone (sec. 4.2:
+// IV is carried at the flow velocity, upwinded by the face velocity): b is
+// the upwind cell's slot in the staged box, st the axis stride, sgn = +h
+// when the upwind cell lies below the face (its upper van Leer state) and
+// -h when above (its lower state), with h = 1 - |v_face| dt / dx.
+__device__ __forceinline__ f2 iv_state(const f2 *s_IV, int b, int st, float sgn) {
+  const f2 q = s_IV[b];
+  return p_fma(dup(sgn), vl_half2(s_IV[b - st], q, s_IV[b + st]), q);
+}
+
+// The same for the four angles of a quad (staged as float4).
+__device__ __forceinline__ float4 iv_state4(const float4 *s_IV4, int b, int st, float sgn) {
+  const float4 qm = s_IV4[b - st], q = s_IV4[b], qp = s_IV4[b + st];
+  return mk4(p_fma(dup(sgn), vl_half2(lo2(qm), lo2(q), lo2(qp)), lo2(q)),
+             p_fma(dup(sgn), vl_half2(hi2(qm), hi2(q), hi2(qp)), hi2(q)));
+}
+
+// The IV state at a face whose velocity is exactly zero: the mean of the two
+// cells' states (lower cell b, upper cell b + st).
+__device__ __forceinline__ f2 iv_state_mean(const f2 *s_IV, int b, int st, float h) {
+  return p_mul(dup(0.5f), p_add(iv_state(s_IV, b, st, h), iv_state(s_IV, b + st, st, -h)));
 }
 
 // A compensated pair sum read out as a double: hi - lo, exact in double
@@ -128,11 +155,11 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
 
   __syncthreads();   // the previous tile of a persistent CTA is done with shared memory
   f2 *s_tab = reinterpret_cast<f2 *>(smem_raw);          // [K2][kTab2] (shared table only)
-  f2 *s_It = s_tab + (TAB_PARAM ? 0 : kTab2 * K2);       // [nbox]
-  f2 *s_IV = s_It + G::nbox;                             // [nbox]   (VEL)
-  f2 *s_sI = s_IV + (VEL ? G::nbox : 0);                 // slopes of I~
-  f2 *s_sV = s_sI + G::SL3;                              // slopes of IV (VEL)
-  f2 *s_fx = s_sV + (VEL ? G::SL3 : 0);                  // face fluxes
+  // staging arrays, one float4 (the four angles of a quad) per entry
+  float4 *s_It4 = reinterpret_cast<float4 *>(s_tab + (TAB_PARAM ? 0 : kTab2 * K2));   // I~ [nbox]
+  float4 *s_IV4 = s_It4 + G::nbox;                       // IV [nbox] (VEL)
+  float4 *s_sI4 = s_IV4 + (VEL ? G::nbox : 0);           // half slopes of I~
+  float4 *s_fx4 = s_sI4 + G::SL3;                        // face fluxes
   auto tab = [&](int k, int j) -> f2 {
     if constexpr (TAB_PARAM)
       return qt->e[kTab2 * k + j];
@@ -276,6 +303,18 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
     gu[d] = map_in((d == 0 ? gx : d == 1 ? gy : gz) + 1, a.n[d], a.bc[d][0], a.bc[d][1]);
     face_consts<float, VEL>(a, d, gl, gu, &fu_al[d], &fu_hv[d], &fu_wl[d]);
   }
+  // the upper face's upwind cell for IV: offset of its slot from the own
+  // cell's (0 below the face, one stride above), the state's sign, and
+  // whether the face velocity is exactly zero (mean of both states)
+  int iv_off[3] = {0, 0, 0};
+  float iv_sg[3] = {1.0f, 1.0f, 1.0f};
+  bool iv_mean[3] = {false, false, false};
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    iv_off[d] = fu_wl[d] >= 0.5f ? 0 : bstride[d];
+    iv_sg[d] = fu_wl[d] >= 0.5f ? fu_hv[d] : -fu_hv[d];
+    iv_mean[d] = fu_wl[d] == 0.5f;
+  }
   int lf_d[kLow > 0 ? kLow : 1], lf_bb[kLow > 0 ? kLow : 1], lf_si[kLow > 0 ? kLow : 1],
       lf_sstep[kLow > 0 ? kLow : 1], lf_fx[kLow > 0 ? kLow : 1];
   float lf_al[kLow > 0 ? kLow : 1], lf_hv[kLow > 0 ? kLow : 1], lf_wl[kLow > 0 ? kLow : 1];
@@ -309,7 +348,11 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
     face_consts<float, VEL>(a, d, gl, gu, &lf_al[j], &lf_hv[j], &lf_wl[j]);
   }
 
-  // ---- transport: Delta F_m of every angle pair ---------------------------------
+  // ---- transport: Delta F_m of every angle quad ----------------------------------
+  // One quad (two pairs: ka = 2j in the low halves, kb = 2j + 1 in the high
+  // halves of every float4) per three barriers.  The own cell's values that a
+  // later phase needs are read back from shared memory rather than held
+  // across the barriers.
   const float4 *I4 = reinterpret_cast<const float4 *>(a.I_in);
   float4 *O4 = reinterpret_cast<float4 *>(a.I_out);
   float4 pf[kSlots];   // quad j of each staged cell
@@ -320,102 +363,128 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
   const float4 *qin = I4;
   float4 *qout = O4 + c;
   for (int j = 0; j < NQ; ++j) {
-    f2 dFa = dup(0.0f);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int k = 2 * j + h;
-      if (h == 1 && k >= K) {   // odd pair count: the last quad holds one pair
-        if (valid) *qout = make_float4(dFa.x, dFa.y, 0.0f, 0.0f);
-        break;
-      }
-      const f2 nx = tab(k, 0), ny = tab(k, 1), nz = tab(k, 2);
-      const int m = 2 * k;
-      // ---- phase 1: stage I~ and IV of the cross cells ---------------------
-      f2 I0 = dup(0.0f), q0 = dup(0.0f), p0 = dup(0.0f);
+    const int ka = 2 * j, kb = 2 * j + 1;   // kb past the last pair reads zero table entries
+    const int m = 4 * j;
+    // ---- phase 1: stage I~ and IV of the cross cells -----------------------
+    {
+      const f2 nxa = tab(ka, 0), nya = tab(ka, 1), nza = tab(ka, 2);
+      const f2 nxb = tab(kb, 0), nyb = tab(kb, 1), nzb = tab(kb, 2);
 #pragma unroll
       for (int s = 0; s < kSlots; ++s) {
         if (sl_box[s] < 0) continue;
-        f2 I = h == 0 ? make_float2(pf[s].x, pf[s].y) : make_float2(pf[s].z, pf[s].w);
+        f2 Ia = lo2(pf[s]), Ib = hi2(pf[s]);
         if (sl_code[s]) {
-          const int axis = (sl_code[s] >> 2) & 3, side = (sl_code[s] >> 4) & 1;
-          const f2 mu = tab(k, axis);
-          const bool in0 = side ? (mu.x < 0.0f) : (mu.x > 0.0f);
-          const bool in1 = side ? (mu.y < 0.0f) : (mu.y > 0.0f);
+          const int axis = (sl_code[s] >> 2) & 3, side = (sl_code[s] >> 4) & 1, face = axis * 2 + side;
+          const f2 mua = tab(ka, axis), mub = tab(kb, axis);
           const bool infl = (sl_code[s] & 2) != 0;
-          if (in0) I.x = infl ? inflow(axis * 2 + side, m) : 0.0f;
-          if (in1) I.y = infl ? inflow(axis * 2 + side, m + 1) : 0.0f;
+          if (side ? (mua.x < 0.0f) : (mua.x > 0.0f)) Ia.x = infl ? inflow(face, m) : 0.0f;
+          if (side ? (mua.y < 0.0f) : (mua.y > 0.0f)) Ia.y = infl ? inflow(face, m + 1) : 0.0f;
+          if (side ? (mub.x < 0.0f) : (mub.x > 0.0f)) Ib.x = infl ? inflow(face, m + 2) : 0.0f;
+          if (side ? (mub.y < 0.0f) : (mub.y > 0.0f)) Ib.y = infl ? inflow(face, m + 3) : 0.0f;
         }
-        f2 IV = dup(0.0f), It = I;
         if (VEL) {
-          IV = p_fma(nx, dup(sl_w[s][0]), p_fma(ny, dup(sl_w[s][1]), p_mul(nz, dup(sl_w[s][2]))));
-          It = p_fma(IV, dup(-invC), I);
-          s_IV[sl_box[s]] = IV;
+          const f2 w0 = dup(sl_w[s][0]), w1 = dup(sl_w[s][1]), w2 = dup(sl_w[s][2]);
+          const f2 IVa = p_fma(nxa, w0, p_fma(nya, w1, p_mul(nza, w2)));
+          const f2 IVb = p_fma(nxb, w0, p_fma(nyb, w1, p_mul(nzb, w2)));
+          s_IV4[sl_box[s]] = mk4(IVa, IVb);
+          s_It4[sl_box[s]] = mk4(p_fma(IVa, dup(-invC), Ia), p_fma(IVb, dup(-invC), Ib));
+        } else {
+          s_It4[sl_box[s]] = mk4(Ia, Ib);
         }
-        s_It[sl_box[s]] = It;
-        if (s == 0) { I0 = I; q0 = It; p0 = IV; }
       }
-      (void)I0;
-      if (h == 1 && j + 1 < NQ) {
-        qin += N;
+    }
+    if (j + 1 < NQ) {
+      qin += N;
 #pragma unroll
-        for (int s = 0; s < kSlots; ++s)
-          if (sl_box[s] >= 0) pf[s] = qin[sl_g[s]];
-      }
-      __syncthreads();
+      for (int s = 0; s < kSlots; ++s)
+        if (sl_box[s] >= 0) pf[s] = qin[sl_g[s]];
+    }
+    __syncthreads();
 
-      // ---- phase 2: half slopes of the own cell and of the extension cells ---
-      f2 sI[3], sV[3];
+    // ---- phase 2: half slopes of I~ (own cell, extension cells) --------------
+    {
+      const float4 q0 = s_It4[bo];
 #pragma unroll
       for (int d = 0; d < DIM; ++d) {
         const int st = bstride[d];
-        sI[d] = vl_half2(s_It[bo - st], q0, s_It[bo + st]);
-        s_sI[own_sl[d]] = sI[d];
-        if (VEL) {
-          sV[d] = vl_half2(s_IV[bo - st], p0, s_IV[bo + st]);
-          s_sV[own_sl[d]] = sV[d];
-        }
+        const float4 qm = s_It4[bo - st], qp = s_It4[bo + st];
+        s_sI4[own_sl[d]] = mk4(vl_half2(lo2(qm), lo2(q0), lo2(qp)), vl_half2(hi2(qm), hi2(q0), hi2(qp)));
       }
 #pragma unroll
       for (int e = 0; e < kExt; ++e) {
         if (ext_si[e] < 0) continue;
         const int bb = ext_bb[e], st = ext_st[e];
-        s_sI[ext_si[e]] = vl_half2(s_It[bb - st], s_It[bb], s_It[bb + st]);
-        if (VEL) s_sV[ext_si[e]] = vl_half2(s_IV[bb - st], s_IV[bb], s_IV[bb + st]);
+        const float4 qm = s_It4[bb - st], qc = s_It4[bb], qp = s_It4[bb + st];
+        s_sI4[ext_si[e]] = mk4(vl_half2(lo2(qm), lo2(qc), lo2(qp)), vl_half2(hi2(qm), hi2(qc), hi2(qp)));
       }
-      __syncthreads();
+    }
+    __syncthreads();
 
-      // ---- phase 3: face fluxes (pre-multiplied by dt/dx) --------------------
-      f2 fhi[3];
+    // ---- phase 3: face fluxes (pre-multiplied by dt/dx) ----------------------
+    float4 fhi[3];
+    {
+      const float4 q0 = s_It4[bo];
 #pragma unroll
       for (int d = 0; d < DIM; ++d) {
         const int st = bstride[d];
-        const int sn = own_sl[d] + G::sl_step(d);
-        fhi[d] = face_flux2<VEL>(q0, sI[d], s_It[bo + st], s_sI[sn], p0, VEL ? sV[d] : dup(0.0f),
-                                 VEL ? s_IV[bo + st] : dup(0.0f), VEL ? s_sV[sn] : dup(0.0f), dup(fu_al[d]),
-                                 dup(fu_hv[d]), dup(fu_wl[d]), tab(k, 4 + d), tab(k, 7 + d), tab(k, 10 + d));
-        s_fx[own_fx[d] + G::fx_step(d)] = fhi[d];
+        const int sl = own_sl[d], sn = own_sl[d] + G::sl_step(d);
+        const float4 s0 = s_sI4[sl], q1 = s_It4[bo + st], s1 = s_sI4[sn];
+        f2 fa = face_flux2<false>(lo2(q0), lo2(s0), lo2(q1), lo2(s1), lo2(q0), lo2(q0), lo2(q0), lo2(q0),
+                                  dup(fu_al[d]), dup(1.0f), dup(0.5f), tab(ka, 4 + d), tab(ka, 7 + d), tab(ka, 10 + d));
+        f2 fb = face_flux2<false>(hi2(q0), hi2(s0), hi2(q1), hi2(s1), hi2(q0), hi2(q0), hi2(q0), hi2(q0),
+                                  dup(fu_al[d]), dup(1.0f), dup(0.5f), tab(kb, 4 + d), tab(kb, 7 + d), tab(kb, 10 + d));
+        if (VEL) {
+          float4 iv;
+          if (iv_mean[d]) {
+            const float4 l = iv_state4(s_IV4, bo, st, fu_hv[d]), r = iv_state4(s_IV4, bo + st, st, -fu_hv[d]);
+            iv = mk4(p_mul(dup(0.5f), p_add(lo2(l), lo2(r))), p_mul(dup(0.5f), p_add(hi2(l), hi2(r))));
+          } else {
+            iv = iv_state4(s_IV4, bo + iv_off[d], st, iv_sg[d]);
+          }
+          fa = p_fma(tab(ka, 10 + d), lo2(iv), fa);
+          fb = p_fma(tab(kb, 10 + d), hi2(iv), fb);
+        }
+        fhi[d] = mk4(fa, fb);
+        s_fx4[own_fx[d] + G::fx_step(d)] = fhi[d];
       }
 #pragma unroll
       for (int e = 0; e < kLow; ++e) {
         if (lf_fx[e] < 0) continue;
         const int d = lf_d[e], bb = lf_bb[e], st = d == 0 ? 1 : bstride[d == 1 ? 1 : 2];
         const int si = lf_si[e], si1 = lf_si[e] + lf_sstep[e];
-        s_fx[lf_fx[e]] = face_flux2<VEL>(s_It[bb], s_sI[si], s_It[bb + st], s_sI[si1], VEL ? s_IV[bb] : dup(0.0f),
-                                         VEL ? s_sV[si] : dup(0.0f), VEL ? s_IV[bb + st] : dup(0.0f),
-                                         VEL ? s_sV[si1] : dup(0.0f), dup(lf_al[e]), dup(lf_hv[e]), dup(lf_wl[e]),
-                                         tab(k, 4 + d), tab(k, 7 + d), tab(k, 10 + d));
+        const float4 qL = s_It4[bb], sL = s_sI4[si], qR = s_It4[bb + st], sR = s_sI4[si1];
+        f2 fa = face_flux2<false>(lo2(qL), lo2(sL), lo2(qR), lo2(sR), lo2(qL), lo2(qL), lo2(qL), lo2(qL),
+                                  dup(lf_al[e]), dup(1.0f), dup(0.5f), tab(ka, 4 + d), tab(ka, 7 + d), tab(ka, 10 + d));
+        f2 fb = face_flux2<false>(hi2(qL), hi2(sL), hi2(qR), hi2(sR), hi2(qL), hi2(qL), hi2(qL), hi2(qL),
+                                  dup(lf_al[e]), dup(1.0f), dup(0.5f), tab(kb, 4 + d), tab(kb, 7 + d), tab(kb, 10 + d));
+        if (VEL) {
+          // the low face lies between slots bb (below) and bb + st (above)
+          const float wl = lf_wl[e], hv = lf_hv[e];
+          float4 iv;
+          if (wl == 0.5f) {
+            const float4 l = iv_state4(s_IV4, bb, st, hv), r = iv_state4(s_IV4, bb + st, st, -hv);
+            iv = mk4(p_mul(dup(0.5f), p_add(lo2(l), lo2(r))), p_mul(dup(0.5f), p_add(hi2(l), hi2(r))));
+          } else {
+            iv = iv_state4(s_IV4, wl > 0.5f ? bb : bb + st, st, wl > 0.5f ? hv : -hv);
+          }
+          fa = p_fma(tab(ka, 10 + d), lo2(iv), fa);
+          fb = p_fma(tab(kb, 10 + d), hi2(iv), fb);
+        }
+        s_fx4[lf_fx[e]] = mk4(fa, fb);
       }
-      __syncthreads();
+    }
+    __syncthreads();
 
-      // ---- phase 4: Delta F of the pair ---------------------------------------
-      f2 dF = dup(0.0f);
+    // ---- phase 4: Delta F of the quad ---------------------------------------
+    {
+      f2 da = dup(0.0f), db = dup(0.0f);
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) dF = p_add(dF, p_sub(s_fx[own_fx[d]], fhi[d]));
-      if (h == 0) {
-        dFa = dF;
-      } else if (valid) {
-        *qout = make_float4(dFa.x, dFa.y, dF.x, dF.y);
+      for (int d = 0; d < DIM; ++d) {
+        const float4 fl = s_fx4[own_fx[d]];
+        da = p_add(da, p_sub(lo2(fl), lo2(fhi[d])));
+        db = p_add(db, p_sub(hi2(fl), hi2(fhi[d])));
       }
+      if (valid) *qout = mk4(da, db);
     }
     qout += N;
   }
@@ -467,8 +536,13 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
   {
     const float4 *pi = I4 + c;
     float4 *pq = O4 + c;
+    float4 i4n = *pi, d4n = *pq;   // the next quad's I^n and Delta F, loaded a quad ahead
     for (int j = 0; j < NQ; ++j) {
-      const float4 i4 = *pi, d4 = *pq;
+      const float4 i4 = i4n, d4 = d4n;
+      if (j + 1 < NQ) {
+        i4n = pi[N];
+        d4n = pq[N];
+      }
       f2 Qv[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -676,8 +750,14 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
   a.dEgas[c] = kv * (T1 - T0) + (double)dEK;
 }
 
+// Resident CTAs per SM a tile shape is compiled for: 512 threads per SM
+// (128 registers per thread), so that smaller tiles run as several
+// independent barrier domains per SM.
+template <int NT>
+constexpr int kQMinBlocks = NT >= 512 ? 1 : 512 / NT;
+
 template <int DIM, bool VEL, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(TX * TY * TZ, 1)
+__global__ void __launch_bounds__(TX * TY * TZ, kQMinBlocks<TX * TY * TZ>)
     step_kernel_q(const StepArgs<float> a, const __grid_constant__ QTable<kQTabPairsSmall> qt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int o = a.outer_begin;
@@ -689,7 +769,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, 1)
 // Same kernel for angle sets beyond the launch-parameter table: the table is
 // built in shared memory.
 template <int DIM, bool VEL, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(TX * TY * TZ, 1) step_kernel_qs(const StepArgs<float> a) {
+__global__ void __launch_bounds__(TX * TY * TZ, kQMinBlocks<TX * TY * TZ>) step_kernel_qs(const StepArgs<float> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int o = a.outer_begin;
   process_tile_q<DIM, VEL, TX, TY, TZ, false, 2>(a, nullptr, threadIdx.x, blockIdx.x + (DIM == 1 ? o : 0),

@@ -43,3 +43,15 @@ def test_stated_samples_read_and_score():
         assert err["E_r"] == 0.0 and err["abs_F_r"] == 0.0
         E[cells[0]] += 1e-6 * scal["E_max"]
         assert abs(bench._stated_errors(E, F, ref, wl["dim"])["E_r"] - 1e-6) < 1e-12
+
+
+def test_cpu_baseline_reports_the_threads_it_used():
+    # the oracle timed on a tiny box: the line must say how many threads ran
+    # and what was timed (grid, angles, steps)
+    from paper_1403_6126_gb300 import workloads as wlmod
+    wl = wlmod.box3d(n=6, angles="s2")
+    one = bench.cpu_baseline("box3d", 1, 0, wl=wl, threads=1)
+    assert one["cores"] == 1 and one["value"] > 0 and one["steps"] == 1
+    assert "6x6x6 cells x 8 angles" in one["sample"] and "1 thread" in one["sample"]
+    two = bench.cpu_baseline("box3d", 2, 1, wl=wl, threads=2)
+    assert two["cores"] == 2 and "2 timed steps (+1 warm-up)" in two["sample"]

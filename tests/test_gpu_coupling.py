@@ -66,6 +66,7 @@ def _gpu_history(opacity, precision):
 
     E0, F0, _ = ctx.moments()
     hist = drag_history(step, NSTEPS, rho, T, v, E0, F0, C, P, R / (GAMMA - 1.0))
+    hist[-1]["f"] = ctx.eddington()   # rt_eddington of the last step's intensity
     ctx.close()
     return hist
 
@@ -92,5 +93,11 @@ def test_drag_to_equilibrium_matches_oracle(opacity, precision):
     np.testing.assert_allclose(last["F"][0], Fv, rtol=1e-9 if precision == "fp64" else 1e-5)
     assert max(h["dmom"] for h in got) < (1e-12 if precision == "fp64" else 1e-6)
     assert max(h["den"] for h in got) < 3 * vals["moving_energy_error"]
-    np.testing.assert_allclose(last["P"][0] / last["E"], vals["beaming_fxx"], atol=0.005)
-    np.testing.assert_allclose(last["P"][1] / last["E"], vals["beaming_fyy"], atol=0.0025)
+    # the Eddington tensor f = P / E (sec. 2) as the library outputs it: the
+    # stored moments' ratio, the oracle's ratio, and the values sec. 5.2 prints
+    f = last["f"]
+    np.testing.assert_allclose(f, last["P"] / last["E"], rtol=1e-14, atol=0)
+    fo = ref[-1]["P"] / ref[-1]["E"]
+    assert np.abs(f - fo).max() <= (1e-11 if precision == "fp64" else 5e-5), np.abs(f - fo).max()
+    np.testing.assert_allclose(f[0], vals["beaming_fxx"], atol=0.005)
+    np.testing.assert_allclose(f[1], vals["beaming_fyy"], atol=0.0025)
