@@ -589,8 +589,8 @@ def _stated_workload(name):
     """The inputs the stored oracle values were computed from (float32-rounded
     fields; see tests/golden/make_stated_steps.py)."""
     from paper_1403_6126_gb300 import workloads as wlmod
-    if name == "serving_req8":
-        base = wlmod.serving_request(8)
+    if name.startswith("serving_req"):
+        base = wlmod.serving_request(int(name[len("serving_req"):]))
     else:
         base = wlmod.by_name(name, **({"n": 128} if name == "box3d" else {}))
     return wlmod.rounded_to_float32(base)
@@ -789,24 +789,43 @@ def bench_serving(args):
     over = np.cumsum(gaps / (2.0 * capacity))      # the same stream at 2x capacity
     over -= over[0]
     over_makespan, over_lat, _ = run(over)
-    # one at a time, FP64: time a subset, then scale to the whole stream by
-    # its cell-angle-steps (the subset's seconds per cell-angle-step)
+    # one at a time, FP64: a seeded sample stratified by dimension and angle
+    # count (up to --serve-fp64-per-stratum requests from each of 2-D / 3-D
+    # x 24 / 80 angles), each timed over at most --serve-fp64-steps steps
+    # (one CUDA graph, after one untimed step) and scaled to its full step
+    # count; the stream's total is each stratum's seconds per
+    # cell-angle-step times the stratum's cell-angle-steps
     work = [int(np.prod(wl["shape"])) * len(r[2][1]) * wl["steps"] for r, wl in zip(reqs, wls)]
-    k = max(1, min(len(reqs), args.serve_fp64_n))
-    t0 = time.perf_counter()
-    for (g, a, (n, w), f), wl in list(zip(reqs, wls))[:k]:
-        c = _context(wl, n, w, precision="fp64")
-        c.set_material(*f)
-        c.run(0.0, wl["steps"])
-        try:
+    strata = {}
+    for i, (r, wl) in enumerate(zip(reqs, wls)):
+        strata.setdefault((wl["dim"], len(r[2][1])), []).append(i)
+    rng_s = np.random.default_rng(61)
+    sample = {key: sorted(rng_s.choice(idx, size=min(args.serve_fp64_per_stratum, len(idx)), replace=False).tolist())
+              for key, idx in sorted(strata.items())}
+    t_fp64 = {}
+    for key, idx in sample.items():
+        for i in idx:
+            (g, a, (n, w), f), wl = reqs[i], wls[i]
+            c = _context(wl, n, w, precision="fp64")
+            c.set_material(*f)
+            S = min(wl["steps"], args.serve_fp64_steps)
+            c.run(0.0, 1)
             c.sync()
-            c.moments()
-        except rt.RTError as e:
-            if e.status != rt.RT_E_NONFINITE:
-                raise
-        c.close()
-    fp64_s = time.perf_counter() - t0
-    fp64_rate = len(reqs) / (fp64_s * sum(work) / sum(work[:k]))
+            t0 = time.perf_counter()
+            c.run(0.0, S)
+            try:
+                c.sync()
+            except rt.RTError as e:
+                if e.status != rt.RT_E_NONFINITE:
+                    raise
+            t_fp64[i] = (time.perf_counter() - t0) * wl["steps"] / S
+            c.close()
+    total = 0.0
+    for key, idx in strata.items():
+        rate = sum(t_fp64[i] for i in sample[key]) / sum(work[i] for i in sample[key])
+        total += rate * sum(work[i] for i in idx)
+    fp64_rate = len(reqs) / total
+    mix = ", ".join("%d-D x %d angles: %d of %d" % (k[0], k[1], len(sample[k]), len(strata[k])) for k in sorted(strata))
     # both paths against the oracle's stored values for one request
     accuracy = _serving_accuracy(o, args.serve_budget_gb)
     return {"workload": "%d requests: 2-D 64..512^2 and 3-D 64..192^3 (sides in steps of 32), 24/80 angles, %d steps each, box gas fields; "
@@ -818,9 +837,11 @@ def bench_serving(args):
             "overload_2x": {"value": (len(reqs) - failed[2]) / over_makespan, "unit": "solves/s",
                             "p50_latency_s": float(np.percentile(over_lat, 50)),
                             "p99_latency_s": float(np.percentile(over_lat, 99))},
-            "fp64_one_at_a_time": {"value": fp64_rate, "unit": "solves/s", "timed_requests": k,
-                                   "note": "first %d requests timed (%.1f s), scaled to the whole stream by "
-                                           "cell-angle-steps" % (k, fp64_s)},
+            "fp64_one_at_a_time": {"value": fp64_rate, "unit": "solves/s", "timed_requests": len(t_fp64),
+                                   "note": "seeded sample stratified by dimension and angle count (%s), each "
+                                           "request timed over %d steps and scaled to its step count; each "
+                                           "stratum scaled to the stream by its cell-angle-steps"
+                                           % (mix, args.serve_fp64_steps)},
             "accuracy_vs_oracle": accuracy}
 
 
@@ -846,7 +867,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--serve-n", type=int, default=64)
     ap.add_argument("--serve-steps", type=int, default=200)
-    ap.add_argument("--serve-fp64-n", type=int, default=6)
+    ap.add_argument("--serve-fp64-per-stratum", type=int, default=4)
+    ap.add_argument("--serve-fp64-steps", type=int, default=20)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":

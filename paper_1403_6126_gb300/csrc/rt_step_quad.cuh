@@ -537,6 +537,7 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
     const float4 *pi = I4 + c;
     float4 *pq = O4 + c;
     float4 i4n = *pi, d4n = *pq;   // the next quad's I^n and Delta F, loaded a quad ahead
+#pragma unroll 2
     for (int j = 0; j < NQ; ++j) {
       const float4 i4 = i4n, d4 = d4n;
       if (j + 1 < NQ) {
@@ -602,7 +603,7 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
         }
       }
       *pq = make_float4(Qv[0].x, Qv[0].y, Qv[1].x, Qv[1].y);
-      if ((j & 1) == 1) { U0.fold(); AQ.fold(); }
+      if ((j & 3) == 3) { U0.fold(); AQ.fold(); }
       pi += N;
       pq += N;
     }
@@ -714,7 +715,7 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
         mP[5].part = p_fma(nz, wy, mP[5].part);
       }
       *pq = make_float4(Iv[0].x, Iv[0].y, Iv[1].x, Iv[1].y);
-      if ((j & 1) == 1) {
+      if ((j & 3) == 3) {   // compensated fold every 8 angle pairs
         mE.fold();
         for (int i = 0; i < 3; ++i) mF[i].fold();
         for (int i = 0; i < 6; ++i) mP[i].fold();

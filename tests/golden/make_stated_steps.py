@@ -1,8 +1,9 @@
 """Writes the FP64 oracle's E_r and F_r after the full step count of each
 single-problem workload (the 1-D slab: 2000 steps, the 2-D shadow problem:
-4000 steps, the 3-D box: 500 steps), at full size, and of request 8 of the
-serving stream (a 96^2 box2d problem with 24 angles, 200 steps), for
-tests/test_gpu_stated_steps.py and the accuracy report of bench.py.
+4000 steps, the 3-D box: 500 steps), at full size, and of requests 8 and 41
+of the serving stream (a 96^2 box2d and a 64^3 box3d problem, 24 angles,
+200 steps each), for tests/test_gpu_stated_steps.py, tests/test_gpu_server.py
+and the accuracy report of bench.py.
 
 Only the CPU oracle (oracle/) computes anything here; the inputs come from
 the seeded generators of paper_1403_6126_gb300.workloads, rounded to float32
@@ -12,7 +13,7 @@ scales max E_r, max |F_r| (over the active axes) and sum E_r, and E_r, F_r
 at a seeded sample of cells (every cell of the slab) plus the cells of
 largest and smallest E_r and of largest |F_r|.
 
-usage: python tests/golden/make_stated_steps.py [slab1d] [shadow2d] [box3d] [serving_req8]
+usage: python tests/golden/make_stated_steps.py [slab1d] [shadow2d] [box3d] [serving_req8] [serving_req41]
 (the box takes a few CPU-hours on eight cores; the others minutes)
 """
 import os
@@ -34,6 +35,7 @@ CASES = {
     "shadow2d": (dict(), 4000, 600),
     "box3d": (dict(n=128), 500, 600),
     "serving_req8": (dict(index=8), 200, 600),
+    "serving_req41": (dict(index=41), 200, 600),
 }
 
 

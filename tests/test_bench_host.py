@@ -29,7 +29,7 @@ def test_arm_config_other_workloads():
 
 
 def test_stated_samples_read_and_score():
-    for name in ("slab1d", "shadow2d", "box3d", "serving_req8"):
+    for name in ("slab1d", "shadow2d", "box3d", "serving_req8", "serving_req41"):
         ref = bench._stated_sample(name)
         assert ref is not None, name
         dt, steps, scal, cells, Eo, Fo = ref

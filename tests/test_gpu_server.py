@@ -2,6 +2,8 @@
 are admitted as memory frees up, share the persistent launches, and each
 result is bitwise the one the problem gets alone."""
 import ctypes
+import os
+import sys
 import time
 
 import numpy as np
@@ -12,6 +14,8 @@ import paper_1403_6126_gb300 as rt
 from paper_1403_6126_gb300 import workloads as wlmod
 
 from _helpers import gpu_context
+
+sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
 
 pytestmark = pytest.mark.gpu
 
@@ -155,3 +159,39 @@ print("leaving")
     r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, (r.returncode, r.stderr[-2000:])
     assert "leaving" in r.stdout
+
+
+@pytest.mark.parametrize("req", [8, 41])
+def test_served_result_matches_the_oracle(req):
+    # Requests of the serving stream (8: 96^2 box2d, 41: 64^3 box3d, both 24
+    # angles, 200 steps) submitted through rt_submit, alongside another
+    # request so that they share the persistent launches, against the FP64
+    # oracle's stored values (tests/golden/stated_serving_req*.txt, written
+    # by make_stated_steps.py from the oracle alone): E_r and |F_r| within
+    # the 1e-5 bound of the float path, at the stored cells, relative to the
+    # whole-grid maxima.
+    import make_stated_steps as golden
+    name = "serving_req%d" % req
+    dt, steps, scal, cells, Eo, Fo = golden.read(name)
+    wl, n, w, I0, _, _ = golden.inputs(name)
+    g, a, angs, fields = _request(wl)
+    other = _problems()[0]
+    og, oa, oangs, ofields = _request(other)
+    server = rt.rt_server_create(8 << 30, _opts())
+    try:
+        t_other = rt.rt_submit(server, og, oa, other["C"], other["P"], *ofields, 50)
+        t = rt.rt_submit(server, g, a, wl["C"], wl["P"], *fields, steps)
+        rt.rt_server_wait(server, t, 600.0)
+        N = int(np.prod(wl["shape"]))
+        E, F = np.zeros(N), np.zeros((3, N))
+        rt.rt_poll(server, t, E, F, None)
+        rt.rt_server_wait(server, t_other, 600.0)
+        rt.rt_poll(server, t_other)
+    finally:
+        rt.rt_server_destroy(server)
+    dim = wl["dim"]
+    Fg = golden.active_flux(F[:, cells], dim)
+    Fa = golden.active_flux(Fo, dim)
+    eE = np.abs(E[cells] - Eo).max() / scal["E_max"]
+    eF = np.abs(Fg - Fa).max() / max(scal["F_max"], 1e-3 * scal["E_max"])
+    assert eE <= 1e-5 and eF <= 1e-5, (eE, eF)

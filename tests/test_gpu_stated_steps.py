@@ -49,7 +49,7 @@ def stated_errors(name, precision):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("name", ["slab1d", "shadow2d", "box3d", "serving_req8"])
+@pytest.mark.parametrize("name", ["slab1d", "shadow2d", "box3d", "serving_req8", "serving_req41"])
 def test_full_step_count_matches_oracle(name, precision):
     err = stated_errors(name, precision)
     tol = TOL_FLOAT_SLAB if (name, precision) == ("slab1d", "fp32") else TOL[precision]
