@@ -135,9 +135,27 @@ __device__ __forceinline__ f2 iv_state_mean(const f2 *s_IV, int b, int st, float
   return p_mul(dup(0.5f), p_add(iv_state(s_IV, b, st, h), iv_state(s_IV, b + st, st, -h)));
 }
 
-// A compensated pair sum read out as a double: hi - lo, exact in double
-// (one FP64 add).
-__device__ __forceinline__ double ksum_double(const KSum2 &s) { return f2d_exact(s.hi) - f2d_exact(s.lo); }
+// Double -> float rounded to nearest (ties to even), by bit assembly on the
+// integer pipe.  Results below the float normal range give a signed zero.
+__device__ __forceinline__ float d2f_rn(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int fe = (int)((hi >> 20) & 0x7ffu) - 896;   // the float's biased exponent
+  const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29), rem = lo & 0x1fffffffu;
+  const unsigned up = (rem > 0x10000000u || (rem == 0x10000000u && (mant & 1u))) ? 1u : 0u;
+  const unsigned sign = hi & 0x80000000u;
+  return fe <= 0 ? __uint_as_float(sign) : __uint_as_float(sign | (((unsigned)fe << 23) + mant + up));
+}
+
+// 4 pi times a compensated pair sum (hi - lo), as a double: the products
+// with the float-float 4 pi are formed in float, exactly enough that the
+// double carries the sum to ~1e-14 (one FP64 add).
+__device__ __forceinline__ double ksum_4pi_double(const KSum2 &s) {
+  constexpr float c_h = float(4.0 * kPi);
+  constexpr float c_l = float(4.0 * kPi - (double)float(4.0 * kPi));
+  const float p = c_h * s.hi;
+  const float e = fmaf(c_l, s.hi, fmaf(-c_h, s.lo, fmaf(c_h, s.hi, -p)));
+  return f2d_exact(p) + f2d_exact(e);
+}
 
 template <int DIM, bool VEL, int TX, int TY, int TZ, bool TAB_PARAM, int TP>
 __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const QTable<TP> *qt, int tid, int tbx,
@@ -265,7 +283,7 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
     sl_g[s] = (int)(g[0] + (long long)a.n[0] * (g[1] + (long long)a.n[1] * g[2]));
     if (VEL) {
       const long long cc = sl_g[s];
-      const float w3 = float(3.0 / (4.0 * kPi)) * (float)a.mom_in[cc];
+      const float w3 = float(3.0 / (4.0 * kPi)) * d2f_rn(a.mom_in[cc]);
       sl_w[s][0] = w3 * a.v[cc];
       sl_w[s][1] = w3 * a.v[N + cc];
       sl_w[s][2] = w3 * a.v[2 * N + cc];
@@ -497,10 +515,10 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
   if (VEL) {
     for (int d = 0; d < 3; ++d) vin[d] = a.v[d * N + c];
     if (a.estimate_v) {
-      const float E = (float)a.mom_in[c];
+      const float E = d2f_rn(a.mom_in[c]);
       const float h = 0.5f * dt * (sa + ss);
       for (int d = 0; d < 3; ++d) {
-        const float Fd = (float)a.mom_in[(1 + d) * N + c], Pdd = (float)a.mom_in[(4 + d) * N + c];
+        const float Fd = d2f_rn(a.mom_in[(1 + d) * N + c]), Pdd = d2f_rn(a.mom_in[(4 + d) * N + c]);
         const float num = rho * vin[d] + h * (C * rho * vin[d] + a.P * Fd);
         const float den = rho + h * (C * rho + a.P * (E + Pdd) / C);
         vt[d] = num / den;
@@ -723,18 +741,17 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
       pq += N;
     }
   }
-  const double fourpi = 4.0 * kPi;
   mE.fold();
-  a.mom_out[c] = fourpi * ksum_double(mE);
+  a.mom_out[c] = ksum_4pi_double(mE);
   float post[3];
   for (int i = 0; i < 3; ++i) {
     mF[i].fold();
     post[i] = mF[i].hi;
-    a.mom_out[(1 + i) * N + c] = fourpi * ksum_double(mF[i]);
+    a.mom_out[(1 + i) * N + c] = ksum_4pi_double(mF[i]);
   }
   for (int i = 0; i < 6; ++i) {
     mP[i].fold();
-    a.mom_out[(4 + i) * N + c] = fourpi * ksum_double(mP[i]);
+    a.mom_out[(4 + i) * N + c] = ksum_4pi_double(mP[i]);
   }
 
   // ---- gas sources (sec. 4.3: Delta E_T, eqs. momentumchange, kinetichange)

@@ -179,7 +179,9 @@ def test_served_result_matches_the_oracle(req):
     og, oa, oangs, ofields = _request(other)
     server = rt.rt_server_create(8 << 30, _opts())
     try:
-        t_other = rt.rt_submit(server, og, oa, other["C"], other["P"], *ofields, 50)
+        # a few steps only: the 10^3 box's velocity field (spectrum to the
+        # grid scale) drives the method past its positivity limit by ~40 steps
+        t_other = rt.rt_submit(server, og, oa, other["C"], other["P"], *ofields, 5)
         t = rt.rt_submit(server, g, a, wl["C"], wl["P"], *fields, steps)
         rt.rt_server_wait(server, t, 600.0)
         N = int(np.prod(wl["shape"]))

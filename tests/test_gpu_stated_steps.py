@@ -54,3 +54,37 @@ def test_full_step_count_matches_oracle(name, precision):
     err = stated_errors(name, precision)
     tol = TOL_FLOAT_SLAB if (name, precision) == ("slab1d", "fp32") else TOL[precision]
     assert err["E_r"] <= tol and err["abs_F_r"] <= tol and err["sum_E_r"] <= tol, err
+
+
+@pytest.mark.gpu
+def test_box_whole_grid_float_against_fp64():
+    # The 128^3 x 80 box after its 500 steps, every cell: the float path
+    # against the FP64 path (itself within 1e-12 of the oracle's stored
+    # sample, test above).  E_r and sum E_r meet the 1e-5 bar over the
+    # whole grid (measured 8.6e-6 and 3.9e-6).  |F_r| does not: 2.7e-5,
+    # reached in a few cells whose coupled gas-radiation mode amplifies the
+    # float path's per-angle rounding (~25x over some 60 steps); the stored
+    # sample of ~600 cells meets 1e-5 (test above).  The bound below is that
+    # measured envelope with margin, so that a regression of the float
+    # arithmetic still fails here.
+    name = "box3d"
+    dt, steps, scal, cells, Eo, Fo = golden.read(name)
+    wl, n, w, I0, _, _ = golden.inputs(name)
+    out = {}
+    for precision in ("fp64", "fp32"):
+        ctx = gpu_context(wl, n, w, precision)
+        try:
+            ctx.set_intensity(I0)
+            ctx.set_material(wl["rho"], wl["T"], wl["v"], wl["sa"], wl["ss"])
+            ctx.run(dt, steps)
+            ctx.sync()
+            out[precision] = ctx.moments()[:2]
+        finally:
+            ctx.close()
+    (E64, F64), (E32, F32) = out["fp64"], out["fp32"]
+    Fa64, Fa32 = golden.active_flux(F64, 3), golden.active_flux(F32, 3)
+    eE = np.abs(E32 - E64).max() / np.abs(E64).max()
+    eF = np.abs(Fa32 - Fa64).max() / max(Fa64.max(), 1e-3 * np.abs(E64).max())
+    eS = abs(E32.sum() - E64.sum()) / E64.sum()
+    assert eE <= 1e-5 and eS <= 1e-5, (eE, eS)
+    assert eF <= 4e-5, eF
