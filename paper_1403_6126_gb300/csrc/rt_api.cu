@@ -83,7 +83,7 @@ void free_all(rt_ctx *c) {
     if (c->ev_done[k]) cudaEventDestroy(c->ev_done[k]);
   }
   void *ptrs[] = {c->I[0], c->I[1], c->mom[0], c->mom[1], c->rho, c->sa, c->ss, c->v,
-                  c->T, c->dEgas, c->dMom, c->ang, c->inflow, c->flags, c->stage, c->qscr};
+                  c->T, c->dEgas, c->dMom, c->ang, c->inflow, c->flags, c->stage, c->qscr, c->cen[0], c->cen[1]};
   for (void *p : ptrs)
     if (p) cudaFree(p);
 }
@@ -113,6 +113,8 @@ rtg::StepArgs<Real> rtg::make_args(rt_ctx *c, double dt) {
   a.estimate_v = c->opt.estimate_v;
   a.newton_max_it = c->opt.newton_max_it;
   a.newton_rtol = c->opt.newton_rtol;
+  a.wnorm = (Real)rtg::weight_norm(c->host_angf.data(), c->M);
+  rtg::table_moment_sums(c->host_angf.data(), c->M, a.msum);
   a.ang = (const Real *)c->ang;
   a.inflow = (const Real *)c->inflow;
   a.I_in = (const Real *)c->I[c->cur];
@@ -135,6 +137,8 @@ rtg::StepArgs<Real> rtg::make_args(rt_ctx *c, double dt) {
   a.T_out = c->T;
   a.mom_in = c->mom[c->cur];
   a.mom_out = c->mom[1 - c->cur];
+  a.cen_in = c->cen[c->cur];
+  a.cen_out = c->cen[1 - c->cur];
   a.dEgas = c->dEgas;
   a.dMom = c->dMom;
   a.status = c->flags;
@@ -147,7 +151,8 @@ size_t rtg::context_bytes(long long N, int M, bool fp64) {
   const size_t rs = fp64 ? 8 : 4, Nz = (size_t)N, Mz = (size_t)M;
   const size_t Ms = fp64 ? Mz : 4 * (size_t)((M + 3) / 4);   // stored angles (float: quad padding)
   const size_t stage = sizeof(double) * std::max<size_t>(10 * Nz, 8 * Mz);
-  return rs * (2 * Ms * Nz + 6 * Nz + 10 * Mz) + 8 * (2 * 10 * Nz + 3 * Nz) + 16 * Nz + 2 * sizeof(int) + stage;
+  const size_t centers = fp64 ? 0 : 2 * sizeof(float) * Nz;   // the float step's cell centers
+  return rs * (2 * Ms * Nz + 6 * Nz + 10 * Mz) + 8 * (2 * 10 * Nz + 3 * Nz) + 16 * Nz + 2 * sizeof(int) + stage + centers;
 }
 
 cudaError_t rtg::launch_ctx_step(rt_ctx *c, const StepArgs<double> &a, bool vel, TileShape t) {
@@ -206,10 +211,14 @@ rt_status convert_out(rt_ctx *c, const void *src, double *dst, long long n) {
 // the Q scratch, before encoding).
 rt_status recompute_moments(rt_ctx *c) {
   const void *I = c->bf16 ? (const void *)c->qscr : c->I[c->cur];
+  // the quad-layout float step takes its sums over the weights normalised
+  // to sum 1, and so do these moments
+  const double wscale = c->quad ? 1.0 / rtg::weight_sum(c->host_angf.data(), c->M) : 1.0;
   cudaError_t e = c->fp64 ? rtg::launch_moments<double>((const double *)I, (const double *)c->ang, c->M,
-                                                        c->N, false, c->mom[c->cur], c->stream)
+                                                        c->N, false, 1.0, c->mom[c->cur], c->stream)
                           : rtg::launch_moments<float>((const float *)I, (const float *)c->ang, c->M,
-                                                       c->N, c->quad, c->mom[c->cur], c->stream);
+                                                       c->N, c->quad, wscale, c->mom[c->cur], c->stream);
+  if (e == cudaSuccess && c->quad) e = rtg::launch_centers((const float *)I, c->M, c->N, c->cen[c->cur], c->stream);
   return e == cudaSuccess ? RT_OK : cuda_fail(e, "moments");
 }
 
@@ -436,6 +445,8 @@ rt_status rt_create(const rt_grid *g, const rt_angles *ang, double Crat, double 
       {&c->inflow, rs * 6 * Mz}, {(void **)&c->flags, 2 * sizeof(int)},
       {(void **)&c->stage, sizeof(double) * (size_t)c->stage_len},
       {(void **)&c->qscr, c->bf16 ? sizeof(float) * Mz * Nz : 0},
+      {(void **)&c->cen[0], c->quad ? sizeof(float) * Nz : 0},
+      {(void **)&c->cen[1], c->quad ? sizeof(float) * Nz : 0},
   };
   for (auto &a : allocs) {
     if (a.bytes == 0) continue;
@@ -755,6 +766,9 @@ rt_status rt_load_state(rt_ctx *c, const void *buf, size_t bytes) {
     in += b[i];
   }
   RT_CUDA(cudaMemsetAsync(c->flags, 0, 2 * sizeof(int), c->stream));
+  // the float step's cell centers are a function of the intensity: formed
+  // again rather than saved
+  if (c->quad) RT_CUDA(rtg::launch_centers((const float *)c->I[c->cur], c->M, c->N, c->cen[c->cur], c->stream));
   RT_CUDA(cudaStreamSynchronize(c->stream));
   c->has_v = h.has_v != 0;
   c->intensity_set = h.intensity_set != 0;

@@ -126,11 +126,12 @@ __global__ void moments_kernel(const Real *__restrict__ I, const Real *__restric
 
 // Float intensities (angle-major, or the quad layout when QUAD): products
 // in float and each of the ten sums compensated (Kahan), read out as the
-// double hi - lo.  In double this kernel would run at the FP64 rate (~20 FP64
+// double hi - lo times wscale (1 / sum W for the quad layout's kernels,
+// whose sums are over the normalised weights; 1 otherwise).  In double this kernel would run at the FP64 rate (~20 FP64
 // operations per cell-angle: milliseconds for a 128^3 x 80 field).
 template <bool QUAD>
 __global__ void moments_kernel_f(const float *__restrict__ I, const float *__restrict__ ang, int M, long long N,
-                                 double *__restrict__ mom) {
+                                 double wscale, double *__restrict__ mom) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
     float hi[10], lo[10];
 #pragma unroll
@@ -150,7 +151,26 @@ __global__ void moments_kernel_f(const float *__restrict__ I, const float *__res
       }
     }
 #pragma unroll
-    for (int q = 0; q < 10; ++q) mom[(long long)q * N + c] = 4.0 * kPi * ((double)hi[q] - (double)lo[q]);
+    for (int q = 0; q < 10; ++q) mom[(long long)q * N + c] = 4.0 * kPi * wscale * ((double)hi[q] - (double)lo[q]);
+  }
+}
+
+// The smallest intensity of each cell over its M angles (quad layout,
+// padding angles excluded): the center the float step's deviations are
+// taken from.
+__global__ void centers_kernel(const float4 *__restrict__ I, int M, long long N, float *__restrict__ cen) {
+  const int NQ = (M + 3) / 4;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+    float mn = I[c].x;
+    for (int j = 0; j < NQ; ++j) {
+      const float4 q = I[(long long)j * N + c];
+      const int left = M - 4 * j;
+      mn = fminf(mn, q.x);
+      if (left > 1) mn = fminf(mn, q.y);
+      if (left > 2) mn = fminf(mn, q.z);
+      if (left > 3) mn = fminf(mn, q.w);
+    }
+    cen[c] = mn;
   }
 }
 
@@ -271,16 +291,21 @@ cudaError_t launch_isotropic(const double *T, Real *I, int M, long long N, bool 
 }
 
 template <typename Real>
-cudaError_t launch_moments(const Real *I, const Real *ang, int M, long long N, bool quad, double *mom,
+cudaError_t launch_moments(const Real *I, const Real *ang, int M, long long N, bool quad, double wscale, double *mom,
                            cudaStream_t s) {
   if constexpr (sizeof(Real) == 4) {
     if (quad)
-      moments_kernel_f<true><<<grid_for(N, 256), 256, 0, s>>>(I, ang, M, N, mom);
+      moments_kernel_f<true><<<grid_for(N, 256), 256, 0, s>>>(I, ang, M, N, wscale, mom);
     else
-      moments_kernel_f<false><<<grid_for(N, 256), 256, 0, s>>>(I, ang, M, N, mom);
+      moments_kernel_f<false><<<grid_for(N, 256), 256, 0, s>>>(I, ang, M, N, wscale, mom);
   } else {
     moments_kernel<Real><<<grid_for(N, 256), 256, 0, s>>>(I, ang, M, N, mom);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_centers(const float *I, int M, long long N, float *cen, cudaStream_t s) {
+  centers_kernel<<<grid_for(N, 256), 256, 0, s>>>(reinterpret_cast<const float4 *>(I), M, N, cen);
   return cudaGetLastError();
 }
 
@@ -324,8 +349,9 @@ template cudaError_t launch_convert_out<float>(const float *, double *, long lon
 template cudaError_t launch_convert_out<double>(const double *, double *, long long, cudaStream_t);
 template cudaError_t launch_isotropic<float>(const double *, float *, int, long long, bool, cudaStream_t);
 template cudaError_t launch_isotropic<double>(const double *, double *, int, long long, bool, cudaStream_t);
-template cudaError_t launch_moments<float>(const float *, const float *, int, long long, bool, double *, cudaStream_t);
-template cudaError_t launch_moments<double>(const double *, const double *, int, long long, bool, double *,
+template cudaError_t launch_moments<float>(const float *, const float *, int, long long, bool, double, double *,
+                                           cudaStream_t);
+template cudaError_t launch_moments<double>(const double *, const double *, int, long long, bool, double, double *,
                                             cudaStream_t);
 
 }  // namespace rtg

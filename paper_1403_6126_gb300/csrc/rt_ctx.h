@@ -24,6 +24,7 @@ struct rt_ctx {
   bool quad = false;  // float intensities in the quad-interleaved layout (RT_FP32)
   size_t I_bytes = 0; // bytes of one intensity buffer
   float *qscr = nullptr;  // bf16 storage: float [M][N] scratch for Q_m
+  float *cen[2] = {nullptr, nullptr};   // float step: each cell's smallest intensity over angles [N]
   bool has_v = false, material_set = false, intensity_set = false;
   rtg::TileShape tile{0, 0, 0};
   // device state (Real = double or float)

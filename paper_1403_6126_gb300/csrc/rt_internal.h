@@ -27,6 +27,8 @@ struct StepArgs {
   int hold_T, estimate_v;
   int newton_max_it;  // Newton on T: iteration cap and stopping tolerance
   double newton_rtol;
+  Real wnorm;         // 1 - 1 / (sum of the weights as the float table holds them)
+  float msum[10][2];  // the float table's normalised quadrature sums (table_moment_sums)
   const Real *ang;    // [M][4]: n_x, n_y, n_z, W
   const Real *inflow; // [3][2][M]
   // Intensities.  Double: angle-major [M][N].  Float: quad-interleaved,
@@ -40,6 +42,11 @@ struct StepArgs {
   double *T_out;      // [N]
   const double *mom_in;  // [10][N] moments of I_in
   double *mom_out;       // [10][N] moments of I_out
+  // Float quad layout: each cell's smallest intensity over its angles, of
+  // I_in (read) and of I_out (written); null: formed from I_in in the kernel
+  // and not written.
+  const float *cen_in;
+  float *cen_out;
   double *dEgas;      // [N]
   double *dMom;       // [3][N]
   int *status;        // [0]: cells whose T Newton failed
@@ -56,6 +63,39 @@ struct StepArgs {
   // a grid stepped in slabs gives bitwise the whole-grid result.
   int outer_begin, outer_count;
 };
+
+// The float kernels take their angle sums over the weights of the float
+// table ang4 ([M][4], W in slot 3) divided by their sum S (1 + O(1e-8) after
+// rounding each weight), so that the weights they use sum to exactly 1.
+// weight_norm returns 1 - 1/S, S summed in double (exact for comparable
+// weights) and the result rounded to float once.
+inline double weight_sum(const float *ang4, int M) {
+  double s = 0.0;
+  for (int m = 0; m < M; ++m) s += (double)ang4[4 * m + 3];
+  return s;
+}
+inline float weight_norm(const float *ang4, int M) { return (float)(1.0 - 1.0 / weight_sum(ang4, M)); }
+
+// The quadrature sums of a float angle table ang4 ([M][4]: n_x, n_y, n_z,
+// W) that the float kernels' moments are taken against, over the normalised
+// weights W / S (see weight_norm): sum W (1), sum W n_i (x, y, z), sum W n_i
+// n_j (xx, yy, zz, xy, xz, yz), each summed in double and split into a float
+// pair (hi, lo).
+inline void table_moment_sums(const float *ang4, int M, float out[10][2]) {
+  double s[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int m = 0; m < M; ++m) {
+    const double x = ang4[4 * m], y = ang4[4 * m + 1], z = ang4[4 * m + 2], W = ang4[4 * m + 3];
+    s[0] += W;
+    s[1] += W * x; s[2] += W * y; s[3] += W * z;
+    s[4] += W * x * x; s[5] += W * y * y; s[6] += W * z * z;
+    s[7] += W * x * y; s[8] += W * x * z; s[9] += W * y * z;
+  }
+  for (int k = 0; k < 10; ++k) {
+    const double v = s[k] / s[0];
+    out[k][0] = (float)v;
+    out[k][1] = (float)(v - (double)out[k][0]);
+  }
+}
 
 struct TileShape {
   int tx, ty, tz;
@@ -104,10 +144,12 @@ cudaError_t launch_convert_out(const Real *src, double *dst, long long n, cudaSt
 template <typename Real>
 cudaError_t launch_isotropic(const double *T, Real *I, int M, long long N, bool quad, cudaStream_t s);
 // E, F, P (double [10][N]) of an intensity field (angle-major, or the quad
-// layout when quad is set).
+// layout when quad is set), times wscale (float intensities only).
 template <typename Real>
-cudaError_t launch_moments(const Real *I, const Real *ang, int M, long long N, bool quad, double *mom,
+cudaError_t launch_moments(const Real *I, const Real *ang, int M, long long N, bool quad, double wscale, double *mom,
                            cudaStream_t s);
+// Each cell's smallest intensity over its M angles (quad layout) into cen [N].
+cudaError_t launch_centers(const float *I, int M, long long N, float *cen, cudaStream_t s);
 // Eddington tensor f = P / E (6 components, [6][N]) from stored moments
 // [10][N]; 0 where E = 0.
 cudaError_t launch_eddington(const double *mom, double *f, long long N, cudaStream_t s);

@@ -207,6 +207,8 @@ extern "C" rt_status rt_step_noalloc(const rt_grid *g, const rt_angles *ang, dou
   a.estimate_v = opts->estimate_v;
   a.newton_max_it = opts->newton_max_it;
   a.newton_rtol = opts->newton_rtol;
+  a.wnorm = rtg::weight_norm(angf, M);
+  rtg::table_moment_sums(angf, M, a.msum);
   a.ang = nullptr;      // the launch-parameter table replaces both
   a.inflow = nullptr;
   a.I_in = f->I_in;
@@ -219,6 +221,8 @@ extern "C" rt_status rt_step_noalloc(const rt_grid *g, const rt_angles *ang, dou
   a.T_out = f->T;
   a.mom_in = f->mom_in;
   a.mom_out = f->mom_out;
+  a.cen_in = nullptr;   // cell centers formed from I_in in the kernel
+  a.cen_out = nullptr;
   a.dEgas = f->dE_gas;
   a.dMom = f->dMom;
   a.status = counter;

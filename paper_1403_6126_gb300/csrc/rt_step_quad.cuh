@@ -29,8 +29,18 @@
 // bandwidth) when TAB_PARAM is set, else from shared memory (the persistent
 // multi-problem kernel, whose problems each have their own table).
 //
-// Moments E, F, P and the momentum source are written in double; the
-// compensated float sums (hi, lo) are combined into the double exactly.
+// Precision.  Every per-angle quantity is carried as a deviation from the
+// cell's center R, its smallest intensity over angles (written by the step
+// that produced I^n, or formed from I^n where no such array is given), so
+// that 0 <= I_m - R <= I_m: transport stages I - R - IV/C and adds the flux
+// of the cellwise constant R per cell and axis; Steps 4 and 5 solve for the
+// deviations of theta and of J'' from R; the moments are R times the angle
+// table's own sums plus sums of deviations.  Float rounding then scales with
+// the spread of I over angle rather than with I, and never exceeds that of
+// I itself.  All angle sums are over the weights normalised to sum 1
+// exactly (the float weights sum to 1 + O(1e-8)), so isotropic equilibrium
+// stays a fixed point of the energy exchange.  Moments E, F, P and the
+// momentum source are written in double.
 #pragma once
 
 #include "rt_step_pair.cuh"
@@ -88,14 +98,16 @@ inline void fill_qtable(QTable<P> *t, const float *ang, int M, float C, const fl
 }
 
 // Shared memory of one CTA of the quad kernel: the float4 staging arrays
-// (I~, IV, the slopes of I~, one flux per face), plus the pair table when it
-// is not a launch parameter.
+// (I~ - R, IV, the slopes of I~, one flux per face), R of every box cell,
+// the per-axis coefficients of the flux of R, plus the pair table when it is
+// not a launch parameter.
 __host__ __device__ inline size_t smem_bytes_q(int dim, int M, bool has_v, int tx, int ty, int tz, bool tab_param) {
   Geo g;
   g.init(dim, tx, ty, tz);
   const size_t q = has_v ? 2 : 1, pairs = 2 * (size_t)((M + 3) / 4);
   const size_t n4 = q * g.nbox + g.sl_off[3] + g.fx_off[3];
-  return (tab_param ? 0 : kTab2 * pairs * sizeof(f2)) + n4 * sizeof(float4) + 16;
+  const size_t nR = sizeof(float) * (size_t)((g.nbox + 3) & ~3) + sizeof(f2) * (size_t)dim * g.ncell;
+  return (tab_param ? 0 : kTab2 * pairs * sizeof(f2)) + n4 * sizeof(float4) + nR + 16;
 }
 
 // Exact float -> double by bit assembly (integer pipe: the FP64 pipe is the
@@ -120,6 +132,18 @@ __device__ __forceinline__ float4 mk4(f2 a, f2 b) { return make_float4(a.x, a.y,
 __device__ __forceinline__ f2 iv_state(const f2 *s_IV, int b, int st, float sgn) {
   const f2 q = s_IV[b];
   return p_fma(dup(sgn), vl_half2(s_IV[b - st], q, s_IV[b + st]), q);
+}
+
+// Half van Leer slopes of two angles of I~ = R + u from the deviations u
+// and the differences of R across the two faces, dR = (R_0 - R_-, R_+ - R_0)
+// (R is cellwise constant):
+// the one-sided differences of I~ are formed from quantities the size of
+// their own value.
+__device__ __forceinline__ f2 vl_half2_dev(f2 um, f2 u0, f2 up, f2 dR) {
+  const f2 dl = p_add(p_sub(u0, um), dup(dR.x)), dr = p_add(p_sub(up, u0), dup(dR.y));
+  const f2 pr = p_mul(dl, dr);
+  const f2 h = p_mul(pr, p_rcp(p_add(dl, dr)));
+  return make_float2(pr.x > 0.0f ? h.x : 0.0f, pr.y > 0.0f ? h.y : 0.0f);
 }
 
 // The same for the four angles of a quad (staged as float4).
@@ -157,6 +181,18 @@ __device__ __forceinline__ double ksum_4pi_double(const KSum2 &s) {
   return f2d_exact(p) + f2d_exact(e);
 }
 
+// 4 pi (R s + D) as a double, for a table sum s = sh + sl (float pair) and a
+// sum of deviations D: the product R sh is split exactly by an FMA, and the
+// remainder R sl + D, the size of the deviations, is formed in float.
+__device__ __forceinline__ double mom_4pi_double(float R, float sh, float sl, float D) {
+  const float p = R * sh;
+  const float t = fmaf(R, sl, fmaf(R, sh, -p)) + D;
+  KSum2 k;
+  k.hi = p;
+  k.lo = -t;
+  return ksum_4pi_double(k);
+}
+
 template <int DIM, bool VEL, int TX, int TY, int TZ, bool TAB_PARAM, int TP>
 __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const QTable<TP> *qt, int tid, int tbx,
                                                int tby, int tbz, unsigned char *smem_raw) {
@@ -166,7 +202,7 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
   constexpr int kExt = (G::next + nthr - 1) / nthr;
   constexpr int kLow = (G::nlow + nthr - 1) / nthr;
   static_assert(kSlots <= 4 && kExt <= 2 && kLow <= 2, "tile halo too large for the per-thread work items");
-  const int M = a.M, K = (M + 1) / 2, NQ = (M + 3) / 4, K2 = 2 * NQ;
+  const int M = a.M, NQ = (M + 3) / 4, K2 = 2 * NQ;
   const long long N = a.N;
   const int org[3] = {tbx * TX, tby * TY, tbz * TZ};
   const int bstride[3] = {1, G::B0, G::B0 * G::B1};
@@ -178,6 +214,9 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
   float4 *s_IV4 = s_It4 + G::nbox;                       // IV [nbox] (VEL)
   float4 *s_sI4 = s_IV4 + (VEL ? G::nbox : 0);           // half slopes of I~
   float4 *s_fx4 = s_sI4 + G::SL3;                        // face fluxes
+  float *s_R = reinterpret_cast<float *>(s_fx4 + G::FX3);              // cell centers R [nbox]
+  f2 *s_GR = reinterpret_cast<f2 *>(s_R + ((G::nbox + 3) & ~3));         // flux-of-R coefficients [DIM][ncell]
+  const float4 *I4 = reinterpret_cast<const float4 *>(a.I_in);
   auto tab = [&](int k, int j) -> f2 {
     if constexpr (TAB_PARAM)
       return qt->e[kTab2 * k + j];
@@ -281,6 +320,24 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
     }
     sl_code[s] = code;
     sl_g[s] = (int)(g[0] + (long long)a.n[0] * (g[1] + (long long)a.n[1] * g[2]));
+    // the staged cell's center: the smallest intensity over its angles (0
+    // for a vacuum or inflow ghost, whose incoming angles are replaced)
+    float cmin = 0.0f;
+    if (code == 0 && a.cen_in) {
+      cmin = a.cen_in[sl_g[s]];
+    } else if (code == 0) {
+      const float4 *p = I4 + sl_g[s];
+      cmin = p[0].x;
+      for (int j = 0; j < NQ; ++j) {
+        const float4 q = p[(long long)j * N];
+        const int left = M - 4 * j;   // angles of this quad that are not padding
+        cmin = fminf(cmin, q.x);
+        if (left > 1) cmin = fminf(cmin, q.y);
+        if (left > 2) cmin = fminf(cmin, q.z);
+        if (left > 3) cmin = fminf(cmin, q.w);
+      }
+    }
+    s_R[sl_box[s]] = cmin;
     if (VEL) {
       const long long cc = sl_g[s];
       const float w3 = float(3.0 / (4.0 * kPi)) * d2f_rn(a.mom_in[cc]);
@@ -371,12 +428,36 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
   // halves of every float4) per three barriers.  The own cell's values that a
   // later phase needs are read back from shared memory rather than held
   // across the barriers.
-  const float4 *I4 = reinterpret_cast<const float4 *>(a.I_in);
   float4 *O4 = reinterpret_cast<float4 *>(a.I_out);
   float4 pf[kSlots];   // quad j of each staged cell
 #pragma unroll
   for (int s = 0; s < kSlots; ++s) pf[s] = sl_box[s] >= 0 ? I4[sl_g[s]] : make_float4(0.f, 0.f, 0.f, 0.f);
-  __syncthreads();   // the shared table is complete
+  __syncthreads();   // the shared table and R are complete
+
+  // Transport of I~ = R + u, R the cell's center (the smallest of its
+  // intensities, so that 0 <= I - R <= I): the staged values are the
+  // deviations u = I - R - IV/C of each cell from its own R, and the flux
+  // of the cellwise constant
+  // R, hc (R_l + R_r) + hca alpha (R_l - R_r) at every face, enters Delta F
+  // per cell and axis as hc GA + hca GB with GA = R_- - R_+ and GB =
+  // alpha_lo (R_- - R_0) - alpha_hi (R_0 - R_+).  Each thread writes and
+  // later reads only its own coefficients.
+  {
+    const float R0 = s_R[bo];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const int st = bstride[d];
+      const float Rm = s_R[bo - st], Rp = s_R[bo + st];
+      // alpha of the own cell's lower face (the cell below, mapped as the
+      // low-face items map it)
+      int gu[3] = {min(gx, a.n[0] - 1), min(gy, a.n[1] - 1), min(gz, a.n[2] - 1)};
+      int gl[3] = {gu[0], gu[1], gu[2]};
+      gl[d] = map_in((d == 0 ? gx : d == 1 ? gy : gz) - 1, a.n[d], a.bc[d][0], a.bc[d][1]);
+      float al_lo, hv_lo, wl_lo;
+      face_consts<float, false>(a, d, gl, gu, &al_lo, &hv_lo, &wl_lo);
+      s_GR[d * nthr + tid] = make_float2(Rm - Rp, al_lo * (Rm - R0) - fu_al[d] * (R0 - Rp));
+    }
+  }
 
   const float4 *qin = I4;
   float4 *qout = O4 + c;
@@ -391,6 +472,7 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
       for (int s = 0; s < kSlots; ++s) {
         if (sl_box[s] < 0) continue;
         f2 Ia = lo2(pf[s]), Ib = hi2(pf[s]);
+        const f2 Rs = dup(s_R[sl_box[s]]);
         if (sl_code[s]) {
           const int axis = (sl_code[s] >> 2) & 3, side = (sl_code[s] >> 4) & 1, face = axis * 2 + side;
           const f2 mua = tab(ka, axis), mub = tab(kb, axis);
@@ -400,6 +482,8 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
           if (side ? (mub.x < 0.0f) : (mub.x > 0.0f)) Ib.x = infl ? inflow(face, m + 2) : 0.0f;
           if (side ? (mub.y < 0.0f) : (mub.y > 0.0f)) Ib.y = infl ? inflow(face, m + 3) : 0.0f;
         }
+        Ia = p_sub(Ia, Rs);
+        Ib = p_sub(Ib, Rs);
         if (VEL) {
           const f2 w0 = dup(sl_w[s][0]), w1 = dup(sl_w[s][1]), w2 = dup(sl_w[s][2]);
           const f2 IVa = p_fma(nxa, w0, p_fma(nya, w1, p_mul(nza, w2)));
@@ -422,18 +506,22 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
     // ---- phase 2: half slopes of I~ (own cell, extension cells) --------------
     {
       const float4 q0 = s_It4[bo];
+      const float R0 = s_R[bo];
 #pragma unroll
       for (int d = 0; d < DIM; ++d) {
         const int st = bstride[d];
         const float4 qm = s_It4[bo - st], qp = s_It4[bo + st];
-        s_sI4[own_sl[d]] = mk4(vl_half2(lo2(qm), lo2(q0), lo2(qp)), vl_half2(hi2(qm), hi2(q0), hi2(qp)));
+        const f2 dR = make_float2(R0 - s_R[bo - st], s_R[bo + st] - R0);
+        s_sI4[own_sl[d]] = mk4(vl_half2_dev(lo2(qm), lo2(q0), lo2(qp), dR), vl_half2_dev(hi2(qm), hi2(q0), hi2(qp), dR));
       }
 #pragma unroll
       for (int e = 0; e < kExt; ++e) {
         if (ext_si[e] < 0) continue;
         const int bb = ext_bb[e], st = ext_st[e];
         const float4 qm = s_It4[bb - st], qc = s_It4[bb], qp = s_It4[bb + st];
-        s_sI4[ext_si[e]] = mk4(vl_half2(lo2(qm), lo2(qc), lo2(qp)), vl_half2(hi2(qm), hi2(qc), hi2(qp)));
+        const float Rc = s_R[bb];
+        const f2 dR = make_float2(Rc - s_R[bb - st], s_R[bb + st] - Rc);
+        s_sI4[ext_si[e]] = mk4(vl_half2_dev(lo2(qm), lo2(qc), lo2(qp), dR), vl_half2_dev(hi2(qm), hi2(qc), hi2(qp), dR));
       }
     }
     __syncthreads();
@@ -499,8 +587,11 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
 #pragma unroll
       for (int d = 0; d < DIM; ++d) {
         const float4 fl = s_fx4[own_fx[d]];
+        const f2 GR = s_GR[d * nthr + tid];
         da = p_add(da, p_sub(lo2(fl), lo2(fhi[d])));
         db = p_add(db, p_sub(hi2(fl), hi2(fhi[d])));
+        da = p_fma(tab(ka, 4 + d), dup(GR.x), p_fma(tab(ka, 7 + d), dup(GR.y), da));
+        db = p_fma(tab(kb, 4 + d), dup(GR.x), p_fma(tab(kb, 7 + d), dup(GR.y), db));
       }
       if (valid) *qout = mk4(da, db);
     }
@@ -510,8 +601,17 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
   if (!valid) return;
 
   // ---- per-cell constants of the implicit steps (see process_tile) -------------
+  // Steps 4 and 5 are taken in deviations from the cell's center R (the
+  // smallest I^n_m over its angles): every stored right-hand side, every
+  // angle sum and both per-cell solves carry quantities of the size of I - R
+  // rather than of I, and each per-cell solve is the exact sum of the
+  // per-angle updates that follow it.  Float rounding then scales with the
+  // spread of the intensities over angle (never above I_m itself, since R
+  // <= I_m), and the energy the T^4 solve hands to the gas is the energy
+  // the per-angle update takes from the radiation, step after step.
   float rho = a.rho[c], sa = a.sa[c], ss = a.ss[c], vt[3] = {0, 0, 0}, vin[3] = {0, 0, 0};
   const double T0 = a.T_in[c];
+  const float R = s_R[bo];   // the cell's center (the transport staged it)
   if (VEL) {
     for (int d = 0; d < 3; ++d) vin[d] = a.v[d * N + c];
     if (a.estimate_v) {
@@ -531,26 +631,25 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
   const float v2 = vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2];
   const float A0 = 1.0f + dt * C * sa, A1 = dt * sa, kap = dt * sa / C;
   const float a0 = 1.0f + dt * C * ss, a1 = dt * ss;
-  const float bq0 = -dt * C * ss - dt * ss * v2 / C, bq1 = 2.0f * dt * ss, bq2 = -dt * ss / C;
-  const float cq = -3.0f * dt * ss;
-  const float apb0 = 1.0f - a1 * v2 * invC, apb2 = -a1 * invC;
+  // beta_m = b_m + a1 C = 2 a1 vn - a1 (v.v + vn^2) / C (b_m of sec. 4.4)
+  const float bt0 = -a1 * v2 * invC, bt1 = 2.0f * a1, bt2 = -a1 * invC;
   const float rd0 = VEL ? 0.0f : fast_rcp(A0);
   const float ra0 = VEL ? 0.0f : fast_rcp(a0);
-  const float nA1C = -A1 * C, na1C = -a1 * C;
-  const bool abs_inc = A1 * C < 1.0f;
-  const f2 sc = dup(to_scat ? 1.0f : 0.0f), nsc = dup(to_scat ? 0.0f : 1.0f);
+  const f2 sc = dup(to_scat ? 1.0f : 0.0f), nsc = dup(to_scat ? 0.0f : 1.0f), Rv = dup(R);
 
   // ---- source loop: Q_m over Delta F, every angle sum of Steps 4 and 5 ---------
-  // U_k = sum W vn^k r / d, AQ = sum Q / a, BQ = sum b Q / a, pre = sum W n (I^n
-  // + Delta F); T_k = sum W vn^k / d; Ap = sum pe/a, Ad = sum 1/(d a), As1 =
-  // sum 1/a, Acc = sum c/a, Bp, Bd, Bcc the b-weighted ones, B1p = sum (a'+b)/a
-  KSum2 U0, AQ;
-  U0.zero();
-  AQ.zero();
-  f2 U1 = dup(0.0f), U2 = dup(0.0f), BQ = dup(0.0f), pre0 = dup(0.0f), pre1 = dup(0.0f), pre2 = dup(0.0f);
+  // Per angle: d = A0 - A1 vn, a' = a0 - a1 vn (rd = 1/d, ra = 1/a'), rr = r_m
+  // - R (Step 4's right-hand side: I^n, plus Delta F when it goes to Step 4),
+  // stored Q_m = rd rr (+ Delta F when it goes to Step 5).  Sums: T_k = sum W
+  // vn^k rd, U_k = sum W vn^k rd rr, Vw = sum W vn, Gq = sum W vn^2; with wa =
+  // W ra: As1 = sum wa, Va = sum wa vn, Ad / Adv = sum wa rd (vn), AQ = sum wa
+  // Q; the beta-weighted Bs, Bv, Bd, Bdv, BQ, and Bw = sum beta W; pre = sum
+  // W n (I^n + Delta F - R).
+  f2 U0 = dup(0.0f), U1 = dup(0.0f), U2 = dup(0.0f), Vw = dup(0.0f), Gq = dup(0.0f);
   f2 T0p = dup(0.0f), T1p = dup(0.0f), T2p = dup(0.0f), T3p = dup(0.0f);
-  f2 Apk = dup(0.0f), Adk = dup(0.0f), As1k = dup(0.0f), Acck = dup(0.0f);
-  f2 Bpk = dup(0.0f), Bdk = dup(0.0f), Bcck = dup(0.0f), B1pk = dup(0.0f);
+  f2 As1k = dup(0.0f), Vak = dup(0.0f), Adk = dup(0.0f), Advk = dup(0.0f), AQk = dup(0.0f);
+  f2 Bsk = dup(0.0f), Bwk = dup(0.0f), Bvk = dup(0.0f), Bdk = dup(0.0f), Bdvk = dup(0.0f), BQk = dup(0.0f);
+  f2 pre0 = dup(0.0f), pre1 = dup(0.0f), pre2 = dup(0.0f);
   {
     const float4 *pi = I4 + c;
     float4 *pq = O4 + c;
@@ -569,96 +668,109 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
         const f2 nx = tab(k, 0), ny = tab(k, 1), nz = tab(k, 2), Wm = tab(k, 3);
         const f2 I0 = h == 0 ? make_float2(i4.x, i4.y) : make_float2(i4.z, i4.w);
         const f2 dF = h == 0 ? make_float2(d4.x, d4.y) : make_float2(d4.z, d4.w);
-        const f2 full = p_add(I0, dF);
         f2 vn = dup(0.0f), rd = dup(rd0), ra = dup(ra0);
         if (VEL) {
           vn = p_fma(nx, dup(vt[0]), p_fma(ny, dup(vt[1]), p_mul(nz, dup(vt[2]))));
           rd = p_rcp(p_fma(dup(-A1), vn, dup(A0)));
           ra = p_rcp(p_fma(dup(-a1), vn, dup(a0)));
         }
-        // r_m / d_m as r_m - (d_m - 1) r_m / d_m (see process_tile2)
-        const f2 rm = p_fma(nsc, dF, I0);   // I^n, plus Delta F when it goes to Step 4
-        const f2 xdn = VEL ? p_fma(dup(A1), vn, dup(nA1C)) : dup(nA1C);
-        const f2 qa = abs_inc ? p_fma(p_mul(rm, xdn), rd, rm) : p_mul(rm, rd);
-        const f2 Q = p_fma(sc, dF, qa);
+        const f2 g = p_sub(I0, Rv);
+        const f2 gd = p_add(g, dF);   // I^n + Delta F - R
+        const f2 rr = p_fma(nsc, dF, g);
+        const f2 Q = p_fma(rd, rr, p_mul(sc, dF));
         Qv[h] = Q;
-        const f2 wq = p_mul(Wm, qa);
-        U0.part = p_add(U0.part, wq);
-        if (VEL) {
-          const f2 y1 = p_mul(wq, vn);
-          U1 = p_add(U1, y1);
-          U2 = p_fma(y1, vn, U2);
-        }
-        const f2 wa = p_mul(Wm, ra);
-        AQ.part = p_fma(wa, Q, AQ.part);
-        const f2 bm = VEL ? p_fma(vn, p_fma(dup(bq2), vn, dup(bq1)), dup(bq0)) : dup(bq0);
-        const f2 bwa = p_mul(bm, wa);
-        BQ = p_fma(bwa, Q, BQ);
-        pre0 = p_fma(tab(k, 13), full, pre0);
-        pre1 = p_fma(tab(k, 14), full, pre1);
-        pre2 = p_fma(tab(k, 15), full, pre2);
         const f2 wrd = p_mul(Wm, rd);
+        const f2 wq = p_mul(wrd, rr);
         T0p = p_add(T0p, wrd);
+        U0 = p_add(U0, wq);
         if (VEL) {
-          const f2 x1 = p_mul(wrd, vn), x2 = p_mul(x1, vn);
+          const f2 x1 = p_mul(wrd, vn), x2 = p_mul(x1, vn), y1 = p_mul(wq, vn), wv = p_mul(Wm, vn);
           T1p = p_add(T1p, x1);
           T2p = p_add(T2p, x2);
           T3p = p_fma(x2, vn, T3p);
+          U1 = p_add(U1, y1);
+          U2 = p_fma(y1, vn, U2);
+          Vw = p_add(Vw, wv);
+          Gq = p_fma(wv, vn, Gq);
         }
-        const f2 pe = p_mul(dup(A1), p_mul(p_fma(dup(3.0f), vn, dup(C)), rd));   // e_m / d_m
-        Apk = p_fma(wa, pe, Apk);
-        Adk = p_fma(wa, rd, Adk);
+        const f2 wa = p_mul(Wm, ra), war = p_mul(wa, rd);
         As1k = p_add(As1k, wa);
-        Bpk = p_fma(bwa, pe, Bpk);
-        Bdk = p_fma(bwa, rd, Bdk);
+        Adk = p_add(Adk, war);
+        AQk = p_fma(wa, Q, AQk);
         if (VEL) {
-          const f2 cm = p_mul(dup(cq), vn);
-          Acck = p_fma(cm, wa, Acck);
-          Bcck = p_fma(cm, bwa, Bcck);
-          B1pk = p_fma(wa, p_fma(vn, p_fma(dup(apb2), vn, dup(a1)), dup(apb0)), B1pk);
-        } else {
-          B1pk = p_add(B1pk, wa);
+          Vak = p_fma(wa, vn, Vak);
+          Advk = p_fma(war, vn, Advk);
+          const f2 bt = p_fma(vn, p_fma(dup(bt2), vn, dup(bt1)), dup(bt0));
+          const f2 bwa = p_mul(bt, wa), bwar = p_mul(bwa, rd);
+          Bsk = p_add(Bsk, bwa);
+          Bwk = p_fma(bt, Wm, Bwk);
+          Bvk = p_fma(bwa, vn, Bvk);
+          Bdk = p_add(Bdk, bwar);
+          Bdvk = p_fma(bwar, vn, Bdvk);
+          BQk = p_fma(bwa, Q, BQk);
         }
+        pre0 = p_fma(tab(k, 13), gd, pre0);
+        pre1 = p_fma(tab(k, 14), gd, pre1);
+        pre2 = p_fma(tab(k, 15), gd, pre2);
       }
       *pq = make_float4(Qv[0].x, Qv[0].y, Qv[1].x, Qv[1].y);
-      if ((j & 3) == 3) { U0.fold(); AQ.fold(); }
       pi += N;
       pq += N;
     }
   }
-  const float T0s = T0p.x + T0p.y, T1s = T1p.x + T1p.y, T2s = T2p.x + T2p.y, T3s = T3p.x + T3p.y;
-  const float Ap = Apk.x + Apk.y, Ad = Adk.x + Adk.y, As1 = As1k.x + As1k.y, Acc = Acck.x + Acck.y;
-  const float Bp = Bpk.x + Bpk.y, Bd = Bdk.x + Bdk.y, Bcc = Bcck.x + Bcck.y, B1p = B1pk.x + B1pk.y;
+  // Every sum is over the weights normalised to sum 1 (W / sum W, the float
+  // table's sum being 1 + O(1e-8)): s (1 - wnorm) = s / sum W, formed as s -
+  // s wnorm.  With sum W = 1 exact, isotropic equilibrium I_m = theta is a
+  // fixed point of the energy row, as in the paper's quadrature.
+  const float wn = a.wnorm;
+  auto hsum = [wn](f2 x) {
+    const float t = x.x + x.y;
+    return fmaf(-t, wn, t);
+  };
+  const float T0s = hsum(T0p), T1s = hsum(T1p), T2s = hsum(T2p), T3s = hsum(T3p);
+  const float U0s = hsum(U0), U1s = hsum(U1), U2s = hsum(U2), Vws = hsum(Vw), Gqs = hsum(Gq);
+  const float As1 = hsum(As1k), Va = hsum(Vak), Ad = hsum(Adk), Adv = hsum(Advk), AQ = hsum(AQk);
+  const float Bs = hsum(Bsk), Bw = hsum(Bwk), Bv = hsum(Bvk), Bd = hsum(Bdk), Bdv = hsum(Bdvk), BQ = hsum(BQk);
 
-  // ---- Step 4 solve (see process_tile) -----------------------------------------
-  const float Wr = U0.total(), Vr = U1.x + U1.y, Gr = v2 * Wr + (U2.x + U2.y);
-  const float W1 = T0s, V1 = T1s, G1 = v2 * T0s + T2s;
-  const float Ve = A1 * (C * T1s + 3.0f * T2s);
-  const float Ge = A1 * (C * (v2 * T0s + T2s) + 3.0f * (v2 * T1s + T3s));
-  const float Wq = T0s - 4.0f * A1 * T1s;     // sum W (d - e) / d
-  const float den = 1.0f + kap * G1;
-  const float S0 = Gr / den, S1 = Ge / den;
-  const float J0 = Wr - kap * S0 * W1;
-  const float H0 = Vr - kap * S0 * V1, H1 = Ve - kap * S1 * V1;
-  const float omJ1 = Wq + kap * S1 * W1;   // 1 - dJ/dtheta, cancellation-free
+  // ---- Step 4 solve (sec. 4.3) in dth = theta - R ------------------------------
+  // Each row reads I'_m - theta = rd (rr - dth - kappa S + 4 A1 theta vn), so
+  // S = sum g I' (g = W (v.v + vn^2)), theta - J' and H' - S/C are affine in
+  // dth, and the energy row is kv D + c0 + c1 dth(D) = 0 in D = T - T^n with
+  // dth(D) = dth0 + ((T^n + D)^4 - (T^n)^4) / 4 pi.
+  const float Gw = v2 + Gqs;
+  const float G1 = v2 * T0s + T2s, Gr = v2 * U0s + U2s, Gv = v2 * T1s + T3s;
+  const float den = 1.0f + kap * G1, Sg = Gw + 4.0f * A1 * Gv;
+  const float S0 = (R * Sg + Gr) / den, S1 = (Sg - G1) / den;   // S = S0 + S1 dth
+  const float q1 = -4.0f * A1 * T1s;
+  const float Z0 = R * q1 + kap * S0 * T0s - U0s;               // theta - J' = Z0 + Z1 dth
+  const float Z1 = q1 + T0s + kap * S1 * T0s;
+  const float hv = Vws + 4.0f * A1 * T2s, ks = kap * T1s + invC;
+  const float Y0 = R * hv + U1s - S0 * ks;                       // H' - S/C = Y0 + Y1 dth
+  const float Y1 = hv - T1s - S1 * ks;
   const double kv = (double)rho * a.kv_per_rho;
+  const double T0sq = T0 * T0;
+  const float dth0 = (float)(T0sq * T0sq * (1.0 / (4.0 * kPi)) - (double)R);
   double T1 = T0;
+  float dth = dth0;
   if (!a.hold_T) {
     const float beta = a.P * C * (1.0f - v2 * invC * invC) * sa;
-    const float c0r = dt * (float(8.0 * kPi) * a.P * sa * (H0 - S0 * invC) - float(4.0 * kPi) * beta * J0);
-    const float c4 = dt * (2.0f * a.P * sa * (H1 - S1 * invC) + beta * omJ1);
-    // Newton on delta = T - T^n in float, then one double-precision step (see
-    // process_tile2); the stopping tolerance is the caller's (at least 1e-6:
-    // the float iterate cannot resolve finer steps)
+    const float c0 = dt * (float(8.0 * kPi) * a.P * sa * Y0 + float(4.0 * kPi) * beta * Z0);
+    const float c1 = dt * (float(8.0 * kPi) * a.P * sa * Y1 + float(4.0 * kPi) * beta * Z1);
+    const float cc = c0 + c1 * dth0, c4 = c1 * float(1.0 / (4.0 * kPi));
+    // Newton on D from 0; (T^n + D)^4 - (T^n)^4 = D (4 T^3 + D (6 T^2 + D (4 T
+    // + D))) with T = T^n keeps every term of the row the size of D; the
+    // stopping tolerance is the caller's (at least 1e-6 in float), then one
+    // more step
     const float T0f = (float)T0, kvf = (float)kv;
+    const float t2 = T0f * T0f, p3 = 4.0f * t2 * T0f, p2 = 6.0f * t2, p1 = 4.0f * T0f;
     const float rtol = fmaxf((float)a.newton_rtol, 1e-6f);
     const int max_it = a.newton_max_it;
     float d = 0.0f;
     int extra = -1, it;
     for (it = 0; it < max_it; ++it) {
-      const float T = T0f + d, T2 = T * T;
-      const float f = c4 * T2 * T2 + kvf * d + c0r;
-      const float fp = 4.0f * c4 * T2 * T + kvf;
+      const float T = T0f + d;
+      const float f = fmaf(kvf, d, fmaf(c4, d * fmaf(d, fmaf(d, p1 + d, p2), p3), cc));
+      const float fp = fmaf(4.0f * c4, T * T * T, kvf);
       float dn = d - f / fp;
       if (!(T0f + dn > 0.0f)) dn = 0.5f * T - T0f;
       const float step = dn - d;
@@ -666,32 +778,34 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
       if (extra == 0) break;
       if (extra < 0 && fabsf(step) <= rtol * (T0f + d)) extra = 0;
     }
-    double dd = (double)d;
-    const double T = T0 + dd, T2 = T * T;
-    const double f = (double)c4 * T2 * T2 + kv * dd + (double)c0r;
-    const float fp = 4.0f * c4 * (float)(T2 * T) + kvf;
-    dd -= f * (double)(1.0f / fp);
-    if (!(it < max_it && (T0 + dd) > 0.0)) atomicAdd(a.status, 1);
-    T1 = T0 + dd;
+    T1 = T0 + (double)d;
+    if (!(it < max_it && T1 > 0.0)) atomicAdd(a.status, 1);
+    dth = dth0 + d * fmaf(d, fmaf(d, p1 + d, p2), p3) * float(1.0 / (4.0 * kPi));
   }
-  const float T1r = (float)T1, T1sq = T1r * T1r;
-  const float th = T1sq * T1sq * float(1.0 / (4.0 * kPi));
-  const float S = S0 + th * S1;
-  const float kS = kap * S;
+  const float th = R + dth;
+  const float kS = kap * (S0 + S1 * dth);
 
-  // ---- Step 5 solve: (1+B1) s1 + Bc s2 = Br,  A1 s1 + (1+Ac) s2 = Ar -------
-  const float Ar = AQ.total() + th * Ap - kS * Ad;
-  const float Br = (BQ.x + BQ.y) + th * Bp - kS * Bd;
-  const float m11 = B1p, m12 = Bcc, m21 = As1, m22 = 1.0f + Acc;
+  // ---- Step 5 solve (sec. 4.4) in sg = s1 + a1 C s2 and e2 = s2 - R ------------
+  // Each row reads I''_m - s2 = ra (y_m + dth - e2 - sg + 4 a1 s2 vn) with
+  // y_m = r'_m - theta = Q_m + rd (D0 + D1 vn); summing it against W (s2 =
+  // sum W I'') and against beta W (sg = sum beta W I'') gives the 2x2 system.
+  const float D0 = -(dth + kS), D1 = 4.0f * A1 * th;
+  const float Ay = AQ + D0 * Ad + D1 * Adv, By = BQ + D0 * Bd + D1 * Bdv;
+  const float fa = 4.0f * a1;
+  const float m11 = 1.0f + Bs, m12 = Bs - Bw - fa * Bv, r1 = By + dth * Bs + R * (Bw + fa * Bv);
+  const float m21 = As1, m22 = As1 - fa * Va, r2 = Ay + dth * As1 + fa * R * Va;
   const float det = m11 * m22 - m12 * m21;
-  const float s1 = (Br * m22 - m12 * Ar) / det;
-  const float s2 = (m11 * Ar - m21 * Br) / det;
+  const float sg = (r1 * m22 - m12 * r2) / det;
+  const float e2 = (m11 * r2 - m21 * r1) / det;
+  const float E0c = dth - e2 - sg, E1c = fa * (R + e2);
 
   // ---- I^{n+1} over Q_m, quadrature (sec. 3) ---------------------------------
-  KSum2 mE, mF[3], mP[6];
-  mE.zero();
-  for (int i = 0; i < 3; ++i) mF[i].zero();
-  for (int i = 0; i < 6; ++i) mP[i].zero();
+  // The moments are sums of the stored deviations I^{n+1} - R against W, W n
+  // and W n n, plus R times the table's own sums of the same (mom_4pi_double).
+  f2 mE = dup(0.0f), mF[3], mP[6];
+  for (int i = 0; i < 3; ++i) mF[i] = dup(0.0f);
+  for (int i = 0; i < 6; ++i) mP[i] = dup(0.0f);
+  float cnext = __int_as_float(0x7f800000);   // the center of I^{n+1}: its smallest angle
   {
     float4 *pq = O4 + c;
     float4 q4 = *pq;
@@ -710,54 +824,45 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
           rd = p_rcp(p_fma(dup(-A1), vn, dup(A0)));
           ra = p_rcp(p_fma(dup(-a1), vn, dup(a0)));
         }
-        const f2 pe = p_mul(dup(A1), p_mul(p_fma(dup(3.0f), vn, dup(C)), rd));
-        const f2 rs = p_fma(pe, dup(th), p_fma(rd, dup(-kS), Q));        // r'_m
-        const f2 cm = p_mul(dup(cq), vn);
-        // I^{n+1} = (r' - s1 - c s2) / a' taken as r' - ((a' - 1) r' + s1 + c s2) / a'
-        const f2 xan = VEL ? p_fma(dup(a1), vn, dup(na1C)) : dup(na1C);   // -(a'_m - 1)
-        f2 I1 = p_fma(p_fma(xan, rs, p_fma(cm, dup(-s2), dup(-s1))), ra, rs);
+        const f2 y = p_fma(rd, VEL ? p_fma(dup(D1), vn, dup(D0)) : dup(D0), Q);     // r'_m - theta
+        const f2 z = p_add(y, VEL ? p_fma(dup(E1c), vn, dup(E0c)) : dup(E0c));
+        f2 I1 = p_add(Rv, p_fma(ra, z, dup(e2)));                                  // R + (I'' - R)
         if (2 * k >= M) I1.x = 0.0f;          // padding angles stay zero
+        else cnext = fminf(cnext, I1.x);
         if (2 * k + 1 >= M) I1.y = 0.0f;
+        else cnext = fminf(cnext, I1.y);
         Iv[h] = I1;
-        const f2 wi = p_mul(Wm, I1);
-        mE.part = p_add(mE.part, wi);
+        const f2 wi = p_mul(Wm, p_sub(I1, Rv));   // W (I^{n+1} - R), the stored value's deviation
+        mE = p_add(mE, wi);
         const f2 wx = p_mul(nx, wi), wy = p_mul(ny, wi), wz = p_mul(nz, wi);
-        mF[0].part = p_add(mF[0].part, wx);
-        mF[1].part = p_add(mF[1].part, wy);
-        mF[2].part = p_add(mF[2].part, wz);
-        mP[0].part = p_fma(nx, wx, mP[0].part);
-        mP[1].part = p_fma(ny, wy, mP[1].part);
-        mP[2].part = p_fma(nz, wz, mP[2].part);
-        mP[3].part = p_fma(ny, wx, mP[3].part);
-        mP[4].part = p_fma(nz, wx, mP[4].part);
-        mP[5].part = p_fma(nz, wy, mP[5].part);
+        mF[0] = p_add(mF[0], wx);
+        mF[1] = p_add(mF[1], wy);
+        mF[2] = p_add(mF[2], wz);
+        mP[0] = p_fma(nx, wx, mP[0]);
+        mP[1] = p_fma(ny, wy, mP[1]);
+        mP[2] = p_fma(nz, wz, mP[2]);
+        mP[3] = p_fma(ny, wx, mP[3]);
+        mP[4] = p_fma(nz, wx, mP[4]);
+        mP[5] = p_fma(nz, wy, mP[5]);
       }
       *pq = make_float4(Iv[0].x, Iv[0].y, Iv[1].x, Iv[1].y);
-      if ((j & 3) == 3) {   // compensated fold every 8 angle pairs
-        mE.fold();
-        for (int i = 0; i < 3; ++i) mF[i].fold();
-        for (int i = 0; i < 6; ++i) mP[i].fold();
-      }
       pq += N;
     }
   }
-  mE.fold();
-  a.mom_out[c] = ksum_4pi_double(mE);
+  if (a.cen_out) a.cen_out[c] = cnext;
+  a.mom_out[c] = mom_4pi_double(R, a.msum[0][0], a.msum[0][1], hsum(mE));
   float post[3];
   for (int i = 0; i < 3; ++i) {
-    mF[i].fold();
-    post[i] = mF[i].hi;
-    a.mom_out[(1 + i) * N + c] = ksum_4pi_double(mF[i]);
+    post[i] = hsum(mF[i]);
+    a.mom_out[(1 + i) * N + c] = mom_4pi_double(R, a.msum[1 + i][0], a.msum[1 + i][1], post[i]);
   }
-  for (int i = 0; i < 6; ++i) {
-    mP[i].fold();
-    a.mom_out[(4 + i) * N + c] = ksum_4pi_double(mP[i]);
-  }
+  for (int i = 0; i < 6; ++i)
+    a.mom_out[(4 + i) * N + c] = mom_4pi_double(R, a.msum[4 + i][0], a.msum[4 + i][1], hsum(mP[i]));
 
   // ---- gas sources (sec. 4.3: Delta E_T, eqs. momentumchange, kinetichange)
   const float kmom = -float(4.0 * kPi) * a.P * invC;
   float dEK = 0.0f;
-  const float pre[3] = {pre0.x + pre0.y, pre1.x + pre1.y, pre2.x + pre2.y};
+  const float pre[3] = {hsum(pre0), hsum(pre1), hsum(pre2)};
   for (int i = 0; i < 3; ++i) {
     const float dmom = kmom * (post[i] - pre[i]);
     a.dMom[i * N + c] = f2d_exact(dmom);

@@ -17,12 +17,12 @@ sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "gol
 import make_stated_steps as golden  # noqa: E402
 
 TOL = {"fp64": 1e-12, "fp32": 1e-5}
-# The slab is an FP64 workload; its float run is held to a looser bound.
-# Far from steady state but slowly diffusing, many of its cells change by
-# less than half a float ulp per step, which float storage cannot hold: the
-# float result drifts by ~1.5e-8 per step (3.1e-5 after 2000 steps) whatever
-# the arithmetic of the step.
-TOL_FLOAT_SLAB = 5e-5
+# The slab is an FP64 workload; its float run is held to a looser bound on
+# |F_r| alone.  Far from steady state but slowly diffusing, many of its
+# cells change by less than a float ulp per step, which float storage
+# cannot hold: after 2000 steps E_r is within 5.8e-6 and |F_r| within
+# 1.09e-5 of the oracle.
+TOL_FLOAT_SLAB = 2e-5
 
 
 def stated_errors(name, precision):
@@ -52,21 +52,17 @@ def stated_errors(name, precision):
 @pytest.mark.parametrize("name", ["slab1d", "shadow2d", "box3d", "serving_req8", "serving_req41"])
 def test_full_step_count_matches_oracle(name, precision):
     err = stated_errors(name, precision)
-    tol = TOL_FLOAT_SLAB if (name, precision) == ("slab1d", "fp32") else TOL[precision]
-    assert err["E_r"] <= tol and err["abs_F_r"] <= tol and err["sum_E_r"] <= tol, err
+    tol = TOL[precision]
+    tol_F = TOL_FLOAT_SLAB if (name, precision) == ("slab1d", "fp32") else tol
+    assert err["E_r"] <= tol and err["abs_F_r"] <= tol_F and err["sum_E_r"] <= tol, err
 
 
 @pytest.mark.gpu
 def test_box_whole_grid_float_against_fp64():
     # The 128^3 x 80 box after its 500 steps, every cell: the float path
     # against the FP64 path (itself within 1e-12 of the oracle's stored
-    # sample, test above).  E_r and sum E_r meet the 1e-5 bar over the
-    # whole grid (measured 8.6e-6 and 3.9e-6).  |F_r| does not: 2.7e-5,
-    # reached in a few cells whose coupled gas-radiation mode amplifies the
-    # float path's per-angle rounding (~25x over some 60 steps); the stored
-    # sample of ~600 cells meets 1e-5 (test above).  The bound below is that
-    # measured envelope with margin, so that a regression of the float
-    # arithmetic still fails here.
+    # sample, test above), at the 1e-5 bar on E_r, sum E_r and |F_r| over
+    # the whole grid (measured 2.3e-6, 1.5e-7 and 6.8e-6).
     name = "box3d"
     dt, steps, scal, cells, Eo, Fo = golden.read(name)
     wl, n, w, I0, _, _ = golden.inputs(name)
@@ -86,5 +82,4 @@ def test_box_whole_grid_float_against_fp64():
     eE = np.abs(E32 - E64).max() / np.abs(E64).max()
     eF = np.abs(Fa32 - Fa64).max() / max(Fa64.max(), 1e-3 * np.abs(E64).max())
     eS = abs(E32.sum() - E64.sum()) / E64.sum()
-    assert eE <= 1e-5 and eS <= 1e-5, (eE, eS)
-    assert eF <= 4e-5, eF
+    assert eE <= 1e-5 and eS <= 1e-5 and eF <= 1e-5, (eE, eS, eF)
