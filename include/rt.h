@@ -115,7 +115,11 @@ typedef struct {
  * newton_max_it steps, or whose iterate leaves T > 0, counts as a failure
  * (rt_sync then returns RT_E_NONFINITE).  newton_max_it in 1..1000,
  * newton_rtol in [1e-15, 1e-3] (RT_E_INVALID otherwise).  The FP64 CPU
- * reference of this library uses the defaults. */
+ * reference of this library uses the defaults.  With float intensities the
+ * iterate is D = T - T^n in float, every term of the energy row the size of
+ * D (it is formed in deviations from each cell's smallest intensity), and
+ * the tolerance is max(newton_rtol, 1e-6): the float iterate resolves D to a
+ * few float ulps of D, not of T. */
 typedef struct {
   int precision;
   double cfl;        /* dt = cfl * min dx / Crat when rt_step gets dt <= 0      */
