@@ -29,15 +29,14 @@
 // bandwidth) when TAB_PARAM is set, else from shared memory (the persistent
 // multi-problem kernel, whose problems each have their own table).
 //
-// Precision.  Every per-angle quantity is carried as a deviation from the
-// cell's center R, its smallest intensity over angles (written by the step
-// that produced I^n, or formed from I^n where no such array is given), so
-// that 0 <= I_m - R <= I_m: transport stages I - R - IV/C and adds the flux
-// of the cellwise constant R per cell and axis; Steps 4 and 5 solve for the
-// deviations of theta and of J'' from R; the moments are R times the angle
-// table's own sums plus sums of deviations.  Float rounding then scales with
-// the spread of I over angle rather than with I, and never exceeds that of
-// I itself.  All angle sums are over the weights normalised to sum 1
+// Precision.  Every per-angle quantity of the implicit steps is carried as a
+// deviation from the cell's center R, its smallest intensity over angles
+// (written by the step that produced I^n, or formed from I^n where no such
+// array is given), so that 0 <= I_m - R <= I_m: Steps 4 and 5 solve for the
+// deviations of theta and of J'' from R, and the moments are R times the
+// angle table's own sums plus sums of deviations.  Float rounding then
+// scales with the spread of I over angle rather than with I, and never
+// exceeds that of I itself.  All angle sums are over the weights normalised to sum 1
 // exactly (the float weights sum to 1 + O(1e-8)), so isotropic equilibrium
 // stays a fixed point of the energy exchange.  Moments E, F, P and the
 // momentum source are written in double.
@@ -98,16 +97,14 @@ inline void fill_qtable(QTable<P> *t, const float *ang, int M, float C, const fl
 }
 
 // Shared memory of one CTA of the quad kernel: the float4 staging arrays
-// (I~ - R, IV, the slopes of I~, one flux per face), R of every box cell,
-// the per-axis coefficients of the flux of R, plus the pair table when it is
-// not a launch parameter.
+// (I~, IV, the slopes of I~, one flux per face), plus the pair table when it
+// is not a launch parameter.
 __host__ __device__ inline size_t smem_bytes_q(int dim, int M, bool has_v, int tx, int ty, int tz, bool tab_param) {
   Geo g;
   g.init(dim, tx, ty, tz);
   const size_t q = has_v ? 2 : 1, pairs = 2 * (size_t)((M + 3) / 4);
   const size_t n4 = q * g.nbox + g.sl_off[3] + g.fx_off[3];
-  const size_t nR = sizeof(float) * (size_t)((g.nbox + 3) & ~3) + sizeof(f2) * (size_t)dim * g.ncell;
-  return (tab_param ? 0 : kTab2 * pairs * sizeof(f2)) + n4 * sizeof(float4) + nR + 16;
+  return (tab_param ? 0 : kTab2 * pairs * sizeof(f2)) + n4 * sizeof(float4) + 16;
 }
 
 // Exact float -> double by bit assembly (integer pipe: the FP64 pipe is the
@@ -132,18 +129,6 @@ __device__ __forceinline__ float4 mk4(f2 a, f2 b) { return make_float4(a.x, a.y,
 __device__ __forceinline__ f2 iv_state(const f2 *s_IV, int b, int st, float sgn) {
   const f2 q = s_IV[b];
   return p_fma(dup(sgn), vl_half2(s_IV[b - st], q, s_IV[b + st]), q);
-}
-
-// Half van Leer slopes of two angles of I~ = R + u from the deviations u
-// and the differences of R across the two faces, dR = (R_0 - R_-, R_+ - R_0)
-// (R is cellwise constant):
-// the one-sided differences of I~ are formed from quantities the size of
-// their own value.
-__device__ __forceinline__ f2 vl_half2_dev(f2 um, f2 u0, f2 up, f2 dR) {
-  const f2 dl = p_add(p_sub(u0, um), dup(dR.x)), dr = p_add(p_sub(up, u0), dup(dR.y));
-  const f2 pr = p_mul(dl, dr);
-  const f2 h = p_mul(pr, p_rcp(p_add(dl, dr)));
-  return make_float2(pr.x > 0.0f ? h.x : 0.0f, pr.y > 0.0f ? h.y : 0.0f);
 }
 
 // The same for the four angles of a quad (staged as float4).
@@ -214,8 +199,6 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
   float4 *s_IV4 = s_It4 + G::nbox;                       // IV [nbox] (VEL)
   float4 *s_sI4 = s_IV4 + (VEL ? G::nbox : 0);           // half slopes of I~
   float4 *s_fx4 = s_sI4 + G::SL3;                        // face fluxes
-  float *s_R = reinterpret_cast<float *>(s_fx4 + G::FX3);              // cell centers R [nbox]
-  f2 *s_GR = reinterpret_cast<f2 *>(s_R + ((G::nbox + 3) & ~3));         // flux-of-R coefficients [DIM][ncell]
   const float4 *I4 = reinterpret_cast<const float4 *>(a.I_in);
   auto tab = [&](int k, int j) -> f2 {
     if constexpr (TAB_PARAM)
@@ -320,24 +303,6 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
     }
     sl_code[s] = code;
     sl_g[s] = (int)(g[0] + (long long)a.n[0] * (g[1] + (long long)a.n[1] * g[2]));
-    // the staged cell's center: the smallest intensity over its angles (0
-    // for a vacuum or inflow ghost, whose incoming angles are replaced)
-    float cmin = 0.0f;
-    if (code == 0 && a.cen_in) {
-      cmin = a.cen_in[sl_g[s]];
-    } else if (code == 0) {
-      const float4 *p = I4 + sl_g[s];
-      cmin = p[0].x;
-      for (int j = 0; j < NQ; ++j) {
-        const float4 q = p[(long long)j * N];
-        const int left = M - 4 * j;   // angles of this quad that are not padding
-        cmin = fminf(cmin, q.x);
-        if (left > 1) cmin = fminf(cmin, q.y);
-        if (left > 2) cmin = fminf(cmin, q.z);
-        if (left > 3) cmin = fminf(cmin, q.w);
-      }
-    }
-    s_R[sl_box[s]] = cmin;
     if (VEL) {
       const long long cc = sl_g[s];
       const float w3 = float(3.0 / (4.0 * kPi)) * d2f_rn(a.mom_in[cc]);
@@ -432,32 +397,7 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
   float4 pf[kSlots];   // quad j of each staged cell
 #pragma unroll
   for (int s = 0; s < kSlots; ++s) pf[s] = sl_box[s] >= 0 ? I4[sl_g[s]] : make_float4(0.f, 0.f, 0.f, 0.f);
-  __syncthreads();   // the shared table and R are complete
-
-  // Transport of I~ = R + u, R the cell's center (the smallest of its
-  // intensities, so that 0 <= I - R <= I): the staged values are the
-  // deviations u = I - R - IV/C of each cell from its own R, and the flux
-  // of the cellwise constant
-  // R, hc (R_l + R_r) + hca alpha (R_l - R_r) at every face, enters Delta F
-  // per cell and axis as hc GA + hca GB with GA = R_- - R_+ and GB =
-  // alpha_lo (R_- - R_0) - alpha_hi (R_0 - R_+).  Each thread writes and
-  // later reads only its own coefficients.
-  {
-    const float R0 = s_R[bo];
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      const int st = bstride[d];
-      const float Rm = s_R[bo - st], Rp = s_R[bo + st];
-      // alpha of the own cell's lower face (the cell below, mapped as the
-      // low-face items map it)
-      int gu[3] = {min(gx, a.n[0] - 1), min(gy, a.n[1] - 1), min(gz, a.n[2] - 1)};
-      int gl[3] = {gu[0], gu[1], gu[2]};
-      gl[d] = map_in((d == 0 ? gx : d == 1 ? gy : gz) - 1, a.n[d], a.bc[d][0], a.bc[d][1]);
-      float al_lo, hv_lo, wl_lo;
-      face_consts<float, false>(a, d, gl, gu, &al_lo, &hv_lo, &wl_lo);
-      s_GR[d * nthr + tid] = make_float2(Rm - Rp, al_lo * (Rm - R0) - fu_al[d] * (R0 - Rp));
-    }
-  }
+  __syncthreads();   // the shared table is complete
 
   const float4 *qin = I4;
   float4 *qout = O4 + c;
@@ -472,7 +412,6 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
       for (int s = 0; s < kSlots; ++s) {
         if (sl_box[s] < 0) continue;
         f2 Ia = lo2(pf[s]), Ib = hi2(pf[s]);
-        const f2 Rs = dup(s_R[sl_box[s]]);
         if (sl_code[s]) {
           const int axis = (sl_code[s] >> 2) & 3, side = (sl_code[s] >> 4) & 1, face = axis * 2 + side;
           const f2 mua = tab(ka, axis), mub = tab(kb, axis);
@@ -482,8 +421,6 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
           if (side ? (mub.x < 0.0f) : (mub.x > 0.0f)) Ib.x = infl ? inflow(face, m + 2) : 0.0f;
           if (side ? (mub.y < 0.0f) : (mub.y > 0.0f)) Ib.y = infl ? inflow(face, m + 3) : 0.0f;
         }
-        Ia = p_sub(Ia, Rs);
-        Ib = p_sub(Ib, Rs);
         if (VEL) {
           const f2 w0 = dup(sl_w[s][0]), w1 = dup(sl_w[s][1]), w2 = dup(sl_w[s][2]);
           const f2 IVa = p_fma(nxa, w0, p_fma(nya, w1, p_mul(nza, w2)));
@@ -506,22 +443,18 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
     // ---- phase 2: half slopes of I~ (own cell, extension cells) --------------
     {
       const float4 q0 = s_It4[bo];
-      const float R0 = s_R[bo];
 #pragma unroll
       for (int d = 0; d < DIM; ++d) {
         const int st = bstride[d];
         const float4 qm = s_It4[bo - st], qp = s_It4[bo + st];
-        const f2 dR = make_float2(R0 - s_R[bo - st], s_R[bo + st] - R0);
-        s_sI4[own_sl[d]] = mk4(vl_half2_dev(lo2(qm), lo2(q0), lo2(qp), dR), vl_half2_dev(hi2(qm), hi2(q0), hi2(qp), dR));
+        s_sI4[own_sl[d]] = mk4(vl_half2(lo2(qm), lo2(q0), lo2(qp)), vl_half2(hi2(qm), hi2(q0), hi2(qp)));
       }
 #pragma unroll
       for (int e = 0; e < kExt; ++e) {
         if (ext_si[e] < 0) continue;
         const int bb = ext_bb[e], st = ext_st[e];
         const float4 qm = s_It4[bb - st], qc = s_It4[bb], qp = s_It4[bb + st];
-        const float Rc = s_R[bb];
-        const f2 dR = make_float2(Rc - s_R[bb - st], s_R[bb + st] - Rc);
-        s_sI4[ext_si[e]] = mk4(vl_half2_dev(lo2(qm), lo2(qc), lo2(qp), dR), vl_half2_dev(hi2(qm), hi2(qc), hi2(qp), dR));
+        s_sI4[ext_si[e]] = mk4(vl_half2(lo2(qm), lo2(qc), lo2(qp)), vl_half2(hi2(qm), hi2(qc), hi2(qp)));
       }
     }
     __syncthreads();
@@ -587,11 +520,8 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
 #pragma unroll
       for (int d = 0; d < DIM; ++d) {
         const float4 fl = s_fx4[own_fx[d]];
-        const f2 GR = s_GR[d * nthr + tid];
         da = p_add(da, p_sub(lo2(fl), lo2(fhi[d])));
         db = p_add(db, p_sub(hi2(fl), hi2(fhi[d])));
-        da = p_fma(tab(ka, 4 + d), dup(GR.x), p_fma(tab(ka, 7 + d), dup(GR.y), da));
-        db = p_fma(tab(kb, 4 + d), dup(GR.x), p_fma(tab(kb, 7 + d), dup(GR.y), db));
       }
       if (valid) *qout = mk4(da, db);
     }
@@ -611,7 +541,23 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
   // the per-angle update takes from the radiation, step after step.
   float rho = a.rho[c], sa = a.sa[c], ss = a.ss[c], vt[3] = {0, 0, 0}, vin[3] = {0, 0, 0};
   const double T0 = a.T_in[c];
-  const float R = s_R[bo];   // the cell's center (the transport staged it)
+  // the cell's center: written by the step that produced I^n, or formed
+  // here from I^n (padding angles excluded)
+  float R;
+  if (a.cen_in) {
+    R = a.cen_in[c];
+  } else {
+    const float4 *p = I4 + c;
+    R = p[0].x;
+    for (int j = 0; j < NQ; ++j) {
+      const float4 q = p[(long long)j * N];
+      const int left = M - 4 * j;
+      R = fminf(R, q.x);
+      if (left > 1) R = fminf(R, q.y);
+      if (left > 2) R = fminf(R, q.z);
+      if (left > 3) R = fminf(R, q.w);
+    }
+  }
   if (VEL) {
     for (int d = 0; d < 3; ++d) vin[d] = a.v[d * N + c];
     if (a.estimate_v) {
@@ -679,33 +625,37 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
         const f2 rr = p_fma(nsc, dF, g);
         const f2 Q = p_fma(rd, rr, p_mul(sc, dF));
         Qv[h] = Q;
-        const f2 wrd = p_mul(Wm, rd);
-        const f2 wq = p_mul(wrd, rr);
-        T0p = p_add(T0p, wrd);
-        U0 = p_add(U0, wq);
+        // Every product below feeds a fused multiply-add as a factor, never
+        // a separate add: the compiler may fuse a packed multiply into a
+        // following add when the product has no other use, so a sum written
+        // as add(mul) could round differently in the velocity and
+        // no-velocity variants.  Written this way both round alike.
+        const f2 wrd = p_mul(Wm, rd), wa = p_mul(Wm, ra);
+        T0p = p_fma(Wm, rd, T0p);
+        U0 = p_fma(wrd, rr, U0);
         if (VEL) {
-          const f2 x1 = p_mul(wrd, vn), x2 = p_mul(x1, vn), y1 = p_mul(wq, vn), wv = p_mul(Wm, vn);
-          T1p = p_add(T1p, x1);
-          T2p = p_add(T2p, x2);
+          const f2 x1 = p_mul(wrd, vn), x2 = p_mul(x1, vn), y1 = p_mul(p_mul(wrd, rr), vn);
+          T1p = p_fma(wrd, vn, T1p);
+          T2p = p_fma(x1, vn, T2p);
           T3p = p_fma(x2, vn, T3p);
           U1 = p_add(U1, y1);
           U2 = p_fma(y1, vn, U2);
-          Vw = p_add(Vw, wv);
-          Gq = p_fma(wv, vn, Gq);
+          Vw = p_fma(Wm, vn, Vw);
+          Gq = p_fma(p_mul(Wm, vn), vn, Gq);
         }
-        const f2 wa = p_mul(Wm, ra), war = p_mul(wa, rd);
-        As1k = p_add(As1k, wa);
-        Adk = p_add(Adk, war);
+        As1k = p_fma(Wm, ra, As1k);
+        Adk = p_fma(wa, rd, Adk);
         AQk = p_fma(wa, Q, AQk);
         if (VEL) {
+          const f2 war = p_mul(wa, rd);
           Vak = p_fma(wa, vn, Vak);
           Advk = p_fma(war, vn, Advk);
           const f2 bt = p_fma(vn, p_fma(dup(bt2), vn, dup(bt1)), dup(bt0));
           const f2 bwa = p_mul(bt, wa), bwar = p_mul(bwa, rd);
-          Bsk = p_add(Bsk, bwa);
+          Bsk = p_fma(bt, wa, Bsk);
           Bwk = p_fma(bt, Wm, Bwk);
           Bvk = p_fma(bwa, vn, Bvk);
-          Bdk = p_add(Bdk, bwar);
+          Bdk = p_fma(bwa, rd, Bdk);
           Bdvk = p_fma(bwar, vn, Bdvk);
           BQk = p_fma(bwa, Q, BQk);
         }
@@ -832,12 +782,13 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
         if (2 * k + 1 >= M) I1.y = 0.0f;
         else cnext = fminf(cnext, I1.y);
         Iv[h] = I1;
-        const f2 wi = p_mul(Wm, p_sub(I1, Rv));   // W (I^{n+1} - R), the stored value's deviation
-        mE = p_add(mE, wi);
+        const f2 dv = p_sub(I1, Rv);   // the stored value's deviation (exact)
+        const f2 wi = p_mul(Wm, dv);
+        mE = p_fma(Wm, dv, mE);
         const f2 wx = p_mul(nx, wi), wy = p_mul(ny, wi), wz = p_mul(nz, wi);
-        mF[0] = p_add(mF[0], wx);
-        mF[1] = p_add(mF[1], wy);
-        mF[2] = p_add(mF[2], wz);
+        mF[0] = p_fma(nx, wi, mF[0]);
+        mF[1] = p_fma(ny, wi, mF[1]);
+        mF[2] = p_fma(nz, wi, mF[2]);
         mP[0] = p_fma(nx, wx, mP[0]);
         mP[1] = p_fma(ny, wy, mP[1]);
         mP[2] = p_fma(nz, wz, mP[2]);
