@@ -752,14 +752,14 @@ def bench_serving(args):
 
     failed = []
 
-    def run(gaps):
+    def run(gaps, nreq):
         # a request whose T^4 Newton fails (the positivity limit of the
         # method on under-resolved velocity fields) is counted, not fatal
         server = rt.rt_server_create(int(args.serve_budget_gb * 2 ** 30), o)
         try:
             t0 = time.perf_counter()
             tickets = []
-            for (g, a, _, f), wl, gap in zip(reqs, wls, gaps):
+            for (g, a, _, f), wl, gap in zip(reqs[:nreq], wls[:nreq], gaps):
                 while time.perf_counter() - t0 < gap:
                     time.sleep(0.0005)
                 tickets.append(rt.rt_submit(server, g, a, wl["C"], wl["P"], *f, wl["steps"]))
@@ -779,16 +779,20 @@ def bench_serving(args):
         failed.append(nfail)
         return makespan, np.array(lat), steps
 
-    burst, _, _ = run(np.zeros(len(reqs)))          # capacity: all at once
-    capacity = (len(reqs) - failed[0]) / burst
+    # capacity (all at once) and the 2x overload on the stream's first
+    # --serve-cap-n requests (the same mix); the Poisson stream at 0.8x
+    # capacity on all of them
+    ncap = min(args.serve_cap_n, len(reqs))
+    burst, _, _ = run(np.zeros(ncap), ncap)
+    capacity = (ncap - failed[0]) / burst
     rng = np.random.default_rng(60)
     gaps = rng.exponential(1.0, len(reqs))
     arrivals = np.cumsum(gaps / (0.8 * capacity))
     arrivals -= arrivals[0]
-    makespan, lat, steps = run(arrivals)
-    over = np.cumsum(gaps / (2.0 * capacity))      # the same stream at 2x capacity
+    makespan, lat, steps = run(arrivals, len(reqs))
+    over = np.cumsum(gaps[:ncap] / (2.0 * capacity))      # the first ncap at 2x capacity
     over -= over[0]
-    over_makespan, over_lat, _ = run(over)
+    over_makespan, over_lat, _ = run(over, ncap)
     # one at a time, FP64: a seeded sample stratified by dimension and angle
     # count (up to --serve-fp64-per-stratum requests from each of 2-D / 3-D
     # x 24 / 80 angles), each timed over at most --serve-fp64-steps steps
@@ -832,9 +836,10 @@ def bench_serving(args):
                         "Poisson arrivals at 0.8 x measured capacity" % (len(reqs), args.serve_steps),
             "value": (len(reqs) - failed[1]) / makespan, "unit": "solves/s", "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)), "capacity_solves_s": capacity,
+            "capacity_requests": ncap,
             "batch_steps": steps, "budget_gb": args.serve_budget_gb,
             "failed_requests_per_run": failed,
-            "overload_2x": {"value": (len(reqs) - failed[2]) / over_makespan, "unit": "solves/s",
+            "overload_2x": {"value": (ncap - failed[2]) / over_makespan, "unit": "solves/s", "requests": ncap,
                             "p50_latency_s": float(np.percentile(over_lat, 50)),
                             "p99_latency_s": float(np.percentile(over_lat, 99))},
             "fp64_one_at_a_time": {"value": fp64_rate, "unit": "solves/s", "timed_requests": len(t_fp64),
@@ -865,7 +870,9 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-n", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=20)
-    ap.add_argument("--serve-n", type=int, default=64)
+    ap.add_argument("--serve-n", type=int, default=500)
+    ap.add_argument("--serve-cap-n", type=int, default=64,
+                    help="requests of the capacity and 2x-overload runs (the stream's first ones)")
     ap.add_argument("--serve-steps", type=int, default=200)
     ap.add_argument("--serve-fp64-per-stratum", type=int, default=4)
     ap.add_argument("--serve-fp64-steps", type=int, default=20)

@@ -14,6 +14,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "librt_gb300.so")
+# The index-checking build (RT_BOUNDS_CHECK): every shared- and global-memory
+# index of the float step's per-tile code is range checked and a violation
+# is reported as a step failure; for tests, not for measurement.
+LIB_CHECK = os.path.join(HERE, "librt_gb300_check.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 # Units that instantiate the float step kernel (rt_step_pair.cuh).  Its
@@ -34,18 +38,20 @@ def _inputs():
             + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)])
 
 
-def up_to_date():
-    if not os.path.exists(LIB):
+def up_to_date(lib=LIB):
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def build(force=False, verbose=False):
-    """Compile and link; returns the library path."""
-    if not force and up_to_date():
-        return LIB
-    objdir = os.path.join(HERE, "_build")
+def build(force=False, verbose=False, check=False):
+    """Compile and link; returns the library path (the index-checking build
+    when check is set)."""
+    lib = LIB_CHECK if check else LIB
+    if not force and up_to_date(lib):
+        return lib
+    objdir = os.path.join(HERE, "_build_check" if check else "_build")
     os.makedirs(objdir, exist_ok=True)
     procs = []
     for src in _sources():
@@ -54,6 +60,8 @@ def build(force=False, verbose=False):
                                "-c", src, "-o", obj]
         if os.path.basename(src) in NO_CONTRACT:
             cmd += ["-fmad=false"]
+        if check:
+            cmd += ["-DRT_BOUNDS_CHECK"]
         if src.endswith(".cu"):
             cmd += ["-Xptxas", "-warn-spills"] if verbose else []
         procs.append((src, obj, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -67,11 +75,11 @@ def build(force=False, verbose=False):
         objs.append(obj)
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
-    tmp = LIB + ".%d.tmp" % os.getpid()
+    tmp = lib + ".%d.tmp" % os.getpid()
     subprocess.check_call([NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-lrt", "-ldl", "-lpthread"])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, check="--check" in sys.argv))

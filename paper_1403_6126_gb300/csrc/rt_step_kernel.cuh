@@ -43,6 +43,24 @@ namespace rtg {
 namespace stepk {
 
 constexpr int kHalo = 2;
+
+// Index checking.  A debug build defines RT_BOUNDS_CHECK: every shared- and
+// global-memory index of the float step's per-tile code then passes through
+// RT_IDX(i, n), and an index outside [0, n) adds one to the step's failure
+// count (the same word as a failed temperature solve, so rt_sync reports
+// it) and is replaced by 0, which turns an out-of-bounds access into a
+// reported error instead of a fault.  In the product build RT_IDX(i, n) is
+// i and costs nothing.
+__device__ __forceinline__ long long checked_index(long long i, long long n, int *status) {
+  if (i >= 0 && i < n) return i;
+  atomicAdd(status, 1);
+  return 0;
+}
+#ifdef RT_BOUNDS_CHECK
+#define RT_IDX(i, n) (::rtg::stepk::checked_index((i), (n), a.status))
+#else
+#define RT_IDX(i, n) (i)
+#endif
 constexpr double kPi = 3.14159265358979323846;
 
 enum { BC_PERIODIC = 0, BC_VACUUM = 1, BC_COPY = 2, BC_INFLOW = 3 };
@@ -243,8 +261,9 @@ __device__ __forceinline__ void face_consts(const StepArgs<Real> &a, int d, cons
   const long long N = a.N;
   const long long cl = gl[0] + (long long)a.n[0] * (gl[1] + (long long)a.n[1] * gl[2]);
   const long long cu = gu[0] + (long long)a.n[0] * (gu[1] + (long long)a.n[1] * gu[2]);
-  *al = Real(0.5) * (alpha_of(a.dx[d], a.sa[cl] + a.ss[cl]) + alpha_of(a.dx[d], a.sa[cu] + a.ss[cu]));
-  const Real vf = VEL ? Real(0.5) * (a.v[d * N + cl] + a.v[d * N + cu]) : Real(0);
+  *al = Real(0.5) * (alpha_of(a.dx[d], a.sa[RT_IDX(cl, N)] + a.ss[RT_IDX(cl, N)]) +
+                     alpha_of(a.dx[d], a.sa[RT_IDX(cu, N)] + a.ss[RT_IDX(cu, N)]));
+  const Real vf = VEL ? Real(0.5) * (a.v[d * N + RT_IDX(cl, N)] + a.v[d * N + RT_IDX(cu, N)]) : Real(0);
   *hv = Real(1) - (vf < Real(0) ? -vf : vf) * a.dtdx[d];
   *wl = vf > Real(0) ? Real(1) : (vf < Real(0) ? Real(0) : Real(0.5));
 }

@@ -133,7 +133,7 @@ __device__ __forceinline__ f2 iv_state(const f2 *s_IV, int b, int st, float sgn)
 
 // The same for the four angles of a quad (staged as float4).
 __device__ __forceinline__ float4 iv_state4(const float4 *s_IV4, int b, int st, float sgn) {
-  const float4 qm = s_IV4[b - st], q = s_IV4[b], qp = s_IV4[b + st];
+  const float4 qm = s_IV4[b - st], q = s_IV4[b], qp = s_IV4[b + st];   // callers check b - st .. b + st
   return mk4(p_fma(dup(sgn), vl_half2(lo2(qm), lo2(q), lo2(qp)), lo2(q)),
              p_fma(dup(sgn), vl_half2(hi2(qm), hi2(q), hi2(qp)), hi2(q)));
 }
@@ -305,10 +305,10 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
     sl_g[s] = (int)(g[0] + (long long)a.n[0] * (g[1] + (long long)a.n[1] * g[2]));
     if (VEL) {
       const long long cc = sl_g[s];
-      const float w3 = float(3.0 / (4.0 * kPi)) * d2f_rn(a.mom_in[cc]);
-      sl_w[s][0] = w3 * a.v[cc];
-      sl_w[s][1] = w3 * a.v[N + cc];
-      sl_w[s][2] = w3 * a.v[2 * N + cc];
+      const float w3 = float(3.0 / (4.0 * kPi)) * d2f_rn(a.mom_in[RT_IDX(cc, N)]);
+      sl_w[s][0] = w3 * a.v[RT_IDX(cc, N)];
+      sl_w[s][1] = w3 * a.v[N + RT_IDX(cc, N)];
+      sl_w[s][2] = w3 * a.v[2 * N + RT_IDX(cc, N)];
     }
   }
 
@@ -396,7 +396,7 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
   float4 *O4 = reinterpret_cast<float4 *>(a.I_out);
   float4 pf[kSlots];   // quad j of each staged cell
 #pragma unroll
-  for (int s = 0; s < kSlots; ++s) pf[s] = sl_box[s] >= 0 ? I4[sl_g[s]] : make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int s = 0; s < kSlots; ++s) pf[s] = sl_box[s] >= 0 ? I4[RT_IDX(sl_g[s], N)] : make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();   // the shared table is complete
 
   const float4 *qin = I4;
@@ -425,10 +425,10 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
           const f2 w0 = dup(sl_w[s][0]), w1 = dup(sl_w[s][1]), w2 = dup(sl_w[s][2]);
           const f2 IVa = p_fma(nxa, w0, p_fma(nya, w1, p_mul(nza, w2)));
           const f2 IVb = p_fma(nxb, w0, p_fma(nyb, w1, p_mul(nzb, w2)));
-          s_IV4[sl_box[s]] = mk4(IVa, IVb);
-          s_It4[sl_box[s]] = mk4(p_fma(IVa, dup(-invC), Ia), p_fma(IVb, dup(-invC), Ib));
+          s_IV4[RT_IDX(sl_box[s], G::nbox)] = mk4(IVa, IVb);
+          s_It4[RT_IDX(sl_box[s], G::nbox)] = mk4(p_fma(IVa, dup(-invC), Ia), p_fma(IVb, dup(-invC), Ib));
         } else {
-          s_It4[sl_box[s]] = mk4(Ia, Ib);
+          s_It4[RT_IDX(sl_box[s], G::nbox)] = mk4(Ia, Ib);
         }
       }
     }
@@ -436,25 +436,26 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
       qin += N;
 #pragma unroll
       for (int s = 0; s < kSlots; ++s)
-        if (sl_box[s] >= 0) pf[s] = qin[sl_g[s]];
+        if (sl_box[s] >= 0) pf[s] = qin[RT_IDX(sl_g[s], N)];
     }
     __syncthreads();
 
     // ---- phase 2: half slopes of I~ (own cell, extension cells) --------------
     {
-      const float4 q0 = s_It4[bo];
+      const float4 q0 = s_It4[RT_IDX(bo, G::nbox)];
 #pragma unroll
       for (int d = 0; d < DIM; ++d) {
         const int st = bstride[d];
-        const float4 qm = s_It4[bo - st], qp = s_It4[bo + st];
-        s_sI4[own_sl[d]] = mk4(vl_half2(lo2(qm), lo2(q0), lo2(qp)), vl_half2(hi2(qm), hi2(q0), hi2(qp)));
+        const float4 qm = s_It4[RT_IDX(bo - st, G::nbox)], qp = s_It4[RT_IDX(bo + st, G::nbox)];
+        s_sI4[RT_IDX(own_sl[d], G::SL3)] = mk4(vl_half2(lo2(qm), lo2(q0), lo2(qp)), vl_half2(hi2(qm), hi2(q0), hi2(qp)));
       }
 #pragma unroll
       for (int e = 0; e < kExt; ++e) {
         if (ext_si[e] < 0) continue;
         const int bb = ext_bb[e], st = ext_st[e];
-        const float4 qm = s_It4[bb - st], qc = s_It4[bb], qp = s_It4[bb + st];
-        s_sI4[ext_si[e]] = mk4(vl_half2(lo2(qm), lo2(qc), lo2(qp)), vl_half2(hi2(qm), hi2(qc), hi2(qp)));
+        const float4 qm = s_It4[RT_IDX(bb - st, G::nbox)], qc = s_It4[RT_IDX(bb, G::nbox)],
+                     qp = s_It4[RT_IDX(bb + st, G::nbox)];
+        s_sI4[RT_IDX(ext_si[e], G::SL3)] = mk4(vl_half2(lo2(qm), lo2(qc), lo2(qp)), vl_half2(hi2(qm), hi2(qc), hi2(qp)));
       }
     }
     __syncthreads();
@@ -467,7 +468,7 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
       for (int d = 0; d < DIM; ++d) {
         const int st = bstride[d];
         const int sl = own_sl[d], sn = own_sl[d] + G::sl_step(d);
-        const float4 s0 = s_sI4[sl], q1 = s_It4[bo + st], s1 = s_sI4[sn];
+        const float4 s0 = s_sI4[RT_IDX(sl, G::SL3)], q1 = s_It4[RT_IDX(bo + st, G::nbox)], s1 = s_sI4[RT_IDX(sn, G::SL3)];
         f2 fa = face_flux2<false>(lo2(q0), lo2(s0), lo2(q1), lo2(s1), lo2(q0), lo2(q0), lo2(q0), lo2(q0),
                                   dup(fu_al[d]), dup(1.0f), dup(0.5f), tab(ka, 4 + d), tab(ka, 7 + d), tab(ka, 10 + d));
         f2 fb = face_flux2<false>(hi2(q0), hi2(s0), hi2(q1), hi2(s1), hi2(q0), hi2(q0), hi2(q0), hi2(q0),
@@ -475,23 +476,28 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
         if (VEL) {
           float4 iv;
           if (iv_mean[d]) {
+            (void)RT_IDX(bo - st, G::nbox);
+            (void)RT_IDX(bo + 2 * st, G::nbox);
             const float4 l = iv_state4(s_IV4, bo, st, fu_hv[d]), r = iv_state4(s_IV4, bo + st, st, -fu_hv[d]);
             iv = mk4(p_mul(dup(0.5f), p_add(lo2(l), lo2(r))), p_mul(dup(0.5f), p_add(hi2(l), hi2(r))));
           } else {
+            (void)RT_IDX(bo + iv_off[d] - st, G::nbox);
+            (void)RT_IDX(bo + iv_off[d] + st, G::nbox);
             iv = iv_state4(s_IV4, bo + iv_off[d], st, iv_sg[d]);
           }
           fa = p_fma(tab(ka, 10 + d), lo2(iv), fa);
           fb = p_fma(tab(kb, 10 + d), hi2(iv), fb);
         }
         fhi[d] = mk4(fa, fb);
-        s_fx4[own_fx[d] + G::fx_step(d)] = fhi[d];
+        s_fx4[RT_IDX(own_fx[d] + G::fx_step(d), G::FX3)] = fhi[d];
       }
 #pragma unroll
       for (int e = 0; e < kLow; ++e) {
         if (lf_fx[e] < 0) continue;
         const int d = lf_d[e], bb = lf_bb[e], st = d == 0 ? 1 : bstride[d == 1 ? 1 : 2];
         const int si = lf_si[e], si1 = lf_si[e] + lf_sstep[e];
-        const float4 qL = s_It4[bb], sL = s_sI4[si], qR = s_It4[bb + st], sR = s_sI4[si1];
+        const float4 qL = s_It4[RT_IDX(bb, G::nbox)], sL = s_sI4[RT_IDX(si, G::SL3)], qR = s_It4[RT_IDX(bb + st, G::nbox)],
+                     sR = s_sI4[RT_IDX(si1, G::SL3)];
         f2 fa = face_flux2<false>(lo2(qL), lo2(sL), lo2(qR), lo2(sR), lo2(qL), lo2(qL), lo2(qL), lo2(qL),
                                   dup(lf_al[e]), dup(1.0f), dup(0.5f), tab(ka, 4 + d), tab(ka, 7 + d), tab(ka, 10 + d));
         f2 fb = face_flux2<false>(hi2(qL), hi2(sL), hi2(qR), hi2(sR), hi2(qL), hi2(qL), hi2(qL), hi2(qL),
@@ -501,15 +507,19 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
           const float wl = lf_wl[e], hv = lf_hv[e];
           float4 iv;
           if (wl == 0.5f) {
+            (void)RT_IDX(bb - st, G::nbox);
+            (void)RT_IDX(bb + 2 * st, G::nbox);
             const float4 l = iv_state4(s_IV4, bb, st, hv), r = iv_state4(s_IV4, bb + st, st, -hv);
             iv = mk4(p_mul(dup(0.5f), p_add(lo2(l), lo2(r))), p_mul(dup(0.5f), p_add(hi2(l), hi2(r))));
           } else {
+            (void)RT_IDX((wl > 0.5f ? bb : bb + st) - st, G::nbox);
+            (void)RT_IDX((wl > 0.5f ? bb : bb + st) + st, G::nbox);
             iv = iv_state4(s_IV4, wl > 0.5f ? bb : bb + st, st, wl > 0.5f ? hv : -hv);
           }
           fa = p_fma(tab(ka, 10 + d), lo2(iv), fa);
           fb = p_fma(tab(kb, 10 + d), hi2(iv), fb);
         }
-        s_fx4[lf_fx[e]] = mk4(fa, fb);
+        s_fx4[RT_IDX(lf_fx[e], G::FX3)] = mk4(fa, fb);
       }
     }
     __syncthreads();
@@ -519,7 +529,7 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
       f2 da = dup(0.0f), db = dup(0.0f);
 #pragma unroll
       for (int d = 0; d < DIM; ++d) {
-        const float4 fl = s_fx4[own_fx[d]];
+        const float4 fl = s_fx4[RT_IDX(own_fx[d], G::FX3)];
         da = p_add(da, p_sub(lo2(fl), lo2(fhi[d])));
         db = p_add(db, p_sub(hi2(fl), hi2(fhi[d])));
       }
