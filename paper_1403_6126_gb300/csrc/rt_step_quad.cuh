@@ -9,9 +9,9 @@
 //
 // Same method, tile geometry and reading of the paper as process_tile2
 // (rt_step_pair.cuh): one thread per cell, every per-angle quantity carried
-// as a pair of angles in packed FP32, four phases per angle pair separated by
-// CTA barriers (stage I~ = I - IV/C and IV, van Leer half slopes, one flux per
-// face, Delta F).  The work is split differently:
+// as a pair of angles in packed FP32, four phases per angle quad separated by
+// three CTA barriers (stage I~ = I - IV/C and IV, van Leer half slopes, one
+// flux per face, Delta F).  The work is split differently:
 //  * Transport loop (the phases with barriers): per pair only Delta F_m is
 //    formed and written to the output array, two pairs per 128-bit store; no
 //    implicit-step quantity lives in these registers.
@@ -155,9 +155,9 @@ __device__ __forceinline__ float d2f_rn(double x) {
   return fe <= 0 ? __uint_as_float(sign) : __uint_as_float(sign | (((unsigned)fe << 23) + mant + up));
 }
 
-// 4 pi times a compensated pair sum (hi - lo), as a double: the products
-// with the float-float 4 pi are formed in float, exactly enough that the
-// double carries the sum to ~1e-14 (one FP64 add).
+// 4 pi times a float pair (hi - lo), as a double: the products with the
+// float-float 4 pi are formed in float, exactly enough that the double
+// carries the value to ~1e-14 (one FP64 add).
 __device__ __forceinline__ double ksum_4pi_double(const KSum2 &s) {
   constexpr float c_h = float(4.0 * kPi);
   constexpr float c_l = float(4.0 * kPi - (double)float(4.0 * kPi));
