@@ -40,7 +40,7 @@ using NoallocTable = stepk::QTable<stepk::kQTabPairsLarge>;
 // ... (the tiles cost alike, so no claim has to stand between one tile and
 // the next).
 template <int DIM, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(TX * TY * TZ, 1)
+__global__ void __launch_bounds__(TX * TY * TZ, stepk::kQMinBlocks<TX * TY * TZ>)
     noalloc_kernel(const StepArgs<float> a, const __grid_constant__ NoallocTable qt) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int ntx = (a.n[0] + TX - 1) / TX, nty = (a.n[1] + TY - 1) / TY, ntz = (a.n[2] + TZ - 1) / TZ;
@@ -160,7 +160,7 @@ extern "C" rt_status rt_step_noalloc(const rt_grid *g, const rt_angles *ang, dou
   if (rt_status st = rtg::check_newton_options(*opts, "rt_step_noalloc"); st != RT_OK) return st;
   const size_t sm_need = g->dim == 1   ? rtg::stepk::smem_bytes_q(1, M, true, 512, 1, 1, true)
                          : g->dim == 2 ? rtg::stepk::smem_bytes_q(2, M, true, 32, 16, 1, true)
-                                       : rtg::stepk::smem_bytes_q(3, M, true, 16, 8, 4, true);
+                                       : rtg::stepk::smem_bytes_q(3, M, true, 8, 8, 4, true);
   if (sm_need > 227 * 1024) return set_error(RT_E_INVALID, "rt_step_noalloc: too many angles for one tile's shared memory");
   double wsum = 0;
   for (int m = 0; m < M; ++m) {
@@ -238,7 +238,7 @@ extern "C" rt_status rt_step_noalloc(const rt_grid *g, const rt_angles *ang, dou
   if (e != cudaSuccess) return set_error(RT_E_CUDA, std::string("rt_step_noalloc: clear: ") + cudaGetErrorString(e));
   e = g->dim == 1   ? rtg::launch_noalloc<1, 512, 1, 1>(a, qt, dev, s)
       : g->dim == 2 ? rtg::launch_noalloc<2, 32, 16, 1>(a, qt, dev, s)
-                    : rtg::launch_noalloc<3, 16, 8, 4>(a, qt, dev, s);
+                    : rtg::launch_noalloc<3, 8, 8, 4>(a, qt, dev, s);
   if (e != cudaSuccess) return set_error(RT_E_CUDA, std::string("rt_step_noalloc: launch: ") + cudaGetErrorString(e));
   if (newton_failures) {
     e = cudaMemcpyAsync(newton_failures, counter, sizeof(int), cudaMemcpyDeviceToHost, s);

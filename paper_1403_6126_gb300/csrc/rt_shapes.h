@@ -9,7 +9,7 @@
 
 #include "rt_internal.h"
 
-#define RT_SHAPES_F3(X) X(16, 8, 4) X(8, 8, 4) X(8, 4, 4) X(4, 4, 4)
+#define RT_SHAPES_F3(X) X(8, 8, 4) X(16, 8, 4) X(8, 4, 4) X(4, 4, 4)
 #define RT_SHAPES_F2(X) X(32, 16, 1) X(16, 16, 1) X(16, 8, 1) X(8, 8, 1) X(8, 4, 1)
 #define RT_SHAPES_F1(X) X(512, 1, 1) X(256, 1, 1) X(128, 1, 1) X(64, 1, 1) X(32, 1, 1)
 #define RT_SHAPES_D3(X) X(8, 8, 4) X(8, 4, 4) X(4, 4, 4)

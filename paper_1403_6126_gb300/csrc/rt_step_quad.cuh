@@ -53,13 +53,15 @@ namespace stepk {
 constexpr int kQTabPairsSmall = 40;
 constexpr int kQTabPairsLarge = 128;
 
-// Launch-parameter table: kTab2 float2 entries per angle pair (see kTab2)
-// for an even number of pairs (a missing last pair is zeros: weightless,
-// motionless angles), and the inflow intensities [3][2][4 * P/2] per face
-// (zero for angles past M).
+// Launch-parameter table: the kTab2 entries of every angle (see kTab2),
+// interleaved by quad: e[kTab2 q + j] holds entry j of angles 4q .. 4q+3
+// (the pair 2q in x, y and the pair 2q + 1 in z, w), so one 128-bit load
+// gives an entry for both pairs of a quad; angles past M are zeros
+// (weightless, motionless).  Then the inflow intensities [6][2P] per face
+// (zero for angles past M).  P, the pairs it holds, is even.
 template <int P>
 struct QTable {
-  float2 e[P * kTab2];
+  float4 e[P / 2 * kTab2];
   float inflow[6][2 * P];
 };
 
@@ -69,11 +71,11 @@ struct QTable {
 // inflow: [6][M] floats or NULL.
 template <int P>
 inline void fill_qtable(QTable<P> *t, const float *ang, int M, float C, const float dtdx[3], const float *inflow) {
-  for (int i = 0; i < P * kTab2; ++i) t->e[i] = make_float2(0.0f, 0.0f);
+  for (int i = 0; i < P / 2 * kTab2; ++i) t->e[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   for (int f = 0; f < 6; ++f)
     for (int m = 0; m < 2 * P; ++m) t->inflow[f][m] = (inflow && m < M) ? inflow[f * M + m] : 0.0f;
   for (int m = 0; m < M && m < 2 * P; ++m) {
-    const int k = m / 2, h = m % 2;
+    const int q = m / 4, c = m % 4;
     const float W = ang[4 * m + 3];
     for (int j = 0; j < kTab2; ++j) {
       float val;
@@ -90,8 +92,8 @@ inline void fill_qtable(QTable<P> *t, const float *ang, int M, float C, const fl
               : kind == 2 ? mu * dtdx[d]
                           : W * mu;
       }
-      float2 &e = t->e[kTab2 * k + j];
-      (h == 0 ? e.x : e.y) = val;
+      float4 &e = t->e[kTab2 * q + j];
+      (c == 0 ? e.x : c == 1 ? e.y : c == 2 ? e.z : e.w) = val;
     }
   }
 }
@@ -178,6 +180,11 @@ __device__ __forceinline__ double mom_4pi_double(float R, float sh, float sl, fl
   return ksum_4pi_double(k);
 }
 
+template <bool B>
+struct BoolTag {
+  static constexpr bool value = B;
+};
+
 template <int DIM, bool VEL, int TX, int TY, int TZ, bool TAB_PARAM, int TP>
 __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const QTable<TP> *qt, int tid, int tbx,
                                                int tby, int tbz, unsigned char *smem_raw) {
@@ -187,24 +194,27 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
   constexpr int kExt = (G::next + nthr - 1) / nthr;
   constexpr int kLow = (G::nlow + nthr - 1) / nthr;
   static_assert(kSlots <= 4 && kExt <= 2 && kLow <= 2, "tile halo too large for the per-thread work items");
-  const int M = a.M, NQ = (M + 3) / 4, K2 = 2 * NQ;
+  // slot s holds a staged cell for every thread of the tile
+  auto slot_full = [](int s) { return (s + 1) * nthr <= G::ncross; };
+  const int M = a.M, NQ = (M + 3) / 4;
   const long long N = a.N;
   const int org[3] = {tbx * TX, tby * TY, tbz * TZ};
   const int bstride[3] = {1, G::B0, G::B0 * G::B1};
 
   __syncthreads();   // the previous tile of a persistent CTA is done with shared memory
-  f2 *s_tab = reinterpret_cast<f2 *>(smem_raw);          // [K2][kTab2] (shared table only)
+  float4 *s_tab = reinterpret_cast<float4 *>(smem_raw);  // [NQ][kTab2] as QTable::e (shared table only)
   // staging arrays, one float4 (the four angles of a quad) per entry
-  float4 *s_It4 = reinterpret_cast<float4 *>(s_tab + (TAB_PARAM ? 0 : kTab2 * K2));   // I~ [nbox]
+  float4 *s_It4 = s_tab + (TAB_PARAM ? 0 : kTab2 * NQ);  // I~ [nbox]
   float4 *s_IV4 = s_It4 + G::nbox;                       // IV [nbox] (VEL)
   float4 *s_sI4 = s_IV4 + (VEL ? G::nbox : 0);           // half slopes of I~
   float4 *s_fx4 = s_sI4 + G::SL3;                        // face fluxes
   const float4 *I4 = reinterpret_cast<const float4 *>(a.I_in);
-  auto tab = [&](int k, int j) -> f2 {
+  // entry j of the four angles of quad q
+  auto tab4 = [&](int q, int j) -> float4 {
     if constexpr (TAB_PARAM)
-      return qt->e[kTab2 * k + j];
+      return qt->e[kTab2 * q + j];
     else
-      return s_tab[kTab2 * k + j];
+      return s_tab[kTab2 * q + j];
   };
   auto inflow = [&](int face, int m) -> float {
     if constexpr (TAB_PARAM)
@@ -217,12 +227,12 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
 
   // ---- shared pair table (as fill_qtable) --------------------------------------
   if constexpr (!TAB_PARAM) {
-    for (int i = tid; i < kTab2 * K2; i += nthr) {
-      const int k = i / kTab2, j = i % kTab2;
-      float v[2];
+    for (int i = tid; i < kTab2 * NQ; i += nthr) {
+      const int q = i / kTab2, j = i % kTab2;
+      float v[4];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int m = 2 * k + h;
+      for (int h = 0; h < 4; ++h) {
+        const int m = 4 * q + h;
         float val = 0.0f;
         if (m < M) {
           const float W = a.ang[4 * m + 3];
@@ -242,7 +252,7 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
         }
         v[h] = val;
       }
-      s_tab[i] = make_float2(v[0], v[1]);
+      s_tab[i] = make_float4(v[0], v[1], v[2], v[3]);
     }
   }
 
@@ -393,150 +403,177 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
   // halves of every float4) per three barriers.  The own cell's values that a
   // later phase needs are read back from shared memory rather than held
   // across the barriers.
+  //
+  // A slot, extension item or low face whose index range the tile fills for
+  // every thread is taken without a test (compile-time).  A tile with no
+  // staged cell beyond a vacuum or inflow face and, with velocity, no face
+  // of exactly zero velocity takes the loop without those two cases; the
+  // choice is one per tile (a CTA-wide vote), so every warp runs the same
+  // branch-free copy of the loop.
   float4 *O4 = reinterpret_cast<float4 *>(a.I_out);
   float4 pf[kSlots];   // quad j of each staged cell
 #pragma unroll
-  for (int s = 0; s < kSlots; ++s) pf[s] = sl_box[s] >= 0 ? I4[RT_IDX(sl_g[s], N)] : make_float4(0.f, 0.f, 0.f, 0.f);
-  __syncthreads();   // the shared table is complete
-
-  const float4 *qin = I4;
-  float4 *qout = O4 + c;
-  for (int j = 0; j < NQ; ++j) {
-    const int ka = 2 * j, kb = 2 * j + 1;   // kb past the last pair reads zero table entries
-    const int m = 4 * j;
-    // ---- phase 1: stage I~ and IV of the cross cells -----------------------
-    {
-      const f2 nxa = tab(ka, 0), nya = tab(ka, 1), nza = tab(ka, 2);
-      const f2 nxb = tab(kb, 0), nyb = tab(kb, 1), nzb = tab(kb, 2);
+  for (int s = 0; s < kSlots; ++s)
+    pf[s] = slot_full(s) || sl_box[s] >= 0 ? I4[RT_IDX(sl_g[s], N)] : make_float4(0.f, 0.f, 0.f, 0.f);
+  bool special = false;
 #pragma unroll
-      for (int s = 0; s < kSlots; ++s) {
-        if (sl_box[s] < 0) continue;
-        f2 Ia = lo2(pf[s]), Ib = hi2(pf[s]);
-        if (sl_code[s]) {
-          const int axis = (sl_code[s] >> 2) & 3, side = (sl_code[s] >> 4) & 1, face = axis * 2 + side;
-          const f2 mua = tab(ka, axis), mub = tab(kb, axis);
-          const bool infl = (sl_code[s] & 2) != 0;
-          if (side ? (mua.x < 0.0f) : (mua.x > 0.0f)) Ia.x = infl ? inflow(face, m) : 0.0f;
-          if (side ? (mua.y < 0.0f) : (mua.y > 0.0f)) Ia.y = infl ? inflow(face, m + 1) : 0.0f;
-          if (side ? (mub.x < 0.0f) : (mub.x > 0.0f)) Ib.x = infl ? inflow(face, m + 2) : 0.0f;
-          if (side ? (mub.y < 0.0f) : (mub.y > 0.0f)) Ib.y = infl ? inflow(face, m + 3) : 0.0f;
-        }
-        if (VEL) {
-          const f2 w0 = dup(sl_w[s][0]), w1 = dup(sl_w[s][1]), w2 = dup(sl_w[s][2]);
-          const f2 IVa = p_fma(nxa, w0, p_fma(nya, w1, p_mul(nza, w2)));
-          const f2 IVb = p_fma(nxb, w0, p_fma(nyb, w1, p_mul(nzb, w2)));
-          s_IV4[RT_IDX(sl_box[s], G::nbox)] = mk4(IVa, IVb);
-          s_It4[RT_IDX(sl_box[s], G::nbox)] = mk4(p_fma(IVa, dup(-invC), Ia), p_fma(IVb, dup(-invC), Ib));
-        } else {
-          s_It4[RT_IDX(sl_box[s], G::nbox)] = mk4(Ia, Ib);
-        }
-      }
-    }
-    if (j + 1 < NQ) {
-      qin += N;
+  for (int s = 0; s < kSlots; ++s) special |= sl_code[s] != 0;
+  if (VEL) {
 #pragma unroll
-      for (int s = 0; s < kSlots; ++s)
-        if (sl_box[s] >= 0) pf[s] = qin[RT_IDX(sl_g[s], N)];
-    }
-    __syncthreads();
-
-    // ---- phase 2: half slopes of I~ (own cell, extension cells) --------------
-    {
-      const float4 q0 = s_It4[RT_IDX(bo, G::nbox)];
+    for (int d = 0; d < DIM; ++d) special |= iv_mean[d];
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) {
-        const int st = bstride[d];
-        const float4 qm = s_It4[RT_IDX(bo - st, G::nbox)], qp = s_It4[RT_IDX(bo + st, G::nbox)];
-        s_sI4[RT_IDX(own_sl[d], G::SL3)] = mk4(vl_half2(lo2(qm), lo2(q0), lo2(qp)), vl_half2(hi2(qm), hi2(q0), hi2(qp)));
-      }
-#pragma unroll
-      for (int e = 0; e < kExt; ++e) {
-        if (ext_si[e] < 0) continue;
-        const int bb = ext_bb[e], st = ext_st[e];
-        const float4 qm = s_It4[RT_IDX(bb - st, G::nbox)], qc = s_It4[RT_IDX(bb, G::nbox)],
-                     qp = s_It4[RT_IDX(bb + st, G::nbox)];
-        s_sI4[RT_IDX(ext_si[e], G::SL3)] = mk4(vl_half2(lo2(qm), lo2(qc), lo2(qp)), vl_half2(hi2(qm), hi2(qc), hi2(qp)));
-      }
-    }
-    __syncthreads();
-
-    // ---- phase 3: face fluxes (pre-multiplied by dt/dx) ----------------------
-    float4 fhi[3];
-    {
-      const float4 q0 = s_It4[bo];
-#pragma unroll
-      for (int d = 0; d < DIM; ++d) {
-        const int st = bstride[d];
-        const int sl = own_sl[d], sn = own_sl[d] + G::sl_step(d);
-        const float4 s0 = s_sI4[RT_IDX(sl, G::SL3)], q1 = s_It4[RT_IDX(bo + st, G::nbox)], s1 = s_sI4[RT_IDX(sn, G::SL3)];
-        f2 fa = face_flux2<false>(lo2(q0), lo2(s0), lo2(q1), lo2(s1), lo2(q0), lo2(q0), lo2(q0), lo2(q0),
-                                  dup(fu_al[d]), dup(1.0f), dup(0.5f), tab(ka, 4 + d), tab(ka, 7 + d), tab(ka, 10 + d));
-        f2 fb = face_flux2<false>(hi2(q0), hi2(s0), hi2(q1), hi2(s1), hi2(q0), hi2(q0), hi2(q0), hi2(q0),
-                                  dup(fu_al[d]), dup(1.0f), dup(0.5f), tab(kb, 4 + d), tab(kb, 7 + d), tab(kb, 10 + d));
-        if (VEL) {
-          float4 iv;
-          if (iv_mean[d]) {
-            (void)RT_IDX(bo - st, G::nbox);
-            (void)RT_IDX(bo + 2 * st, G::nbox);
-            const float4 l = iv_state4(s_IV4, bo, st, fu_hv[d]), r = iv_state4(s_IV4, bo + st, st, -fu_hv[d]);
-            iv = mk4(p_mul(dup(0.5f), p_add(lo2(l), lo2(r))), p_mul(dup(0.5f), p_add(hi2(l), hi2(r))));
-          } else {
-            (void)RT_IDX(bo + iv_off[d] - st, G::nbox);
-            (void)RT_IDX(bo + iv_off[d] + st, G::nbox);
-            iv = iv_state4(s_IV4, bo + iv_off[d], st, iv_sg[d]);
-          }
-          fa = p_fma(tab(ka, 10 + d), lo2(iv), fa);
-          fb = p_fma(tab(kb, 10 + d), hi2(iv), fb);
-        }
-        fhi[d] = mk4(fa, fb);
-        s_fx4[RT_IDX(own_fx[d] + G::fx_step(d), G::FX3)] = fhi[d];
-      }
-#pragma unroll
-      for (int e = 0; e < kLow; ++e) {
-        if (lf_fx[e] < 0) continue;
-        const int d = lf_d[e], bb = lf_bb[e], st = d == 0 ? 1 : bstride[d == 1 ? 1 : 2];
-        const int si = lf_si[e], si1 = lf_si[e] + lf_sstep[e];
-        const float4 qL = s_It4[RT_IDX(bb, G::nbox)], sL = s_sI4[RT_IDX(si, G::SL3)], qR = s_It4[RT_IDX(bb + st, G::nbox)],
-                     sR = s_sI4[RT_IDX(si1, G::SL3)];
-        f2 fa = face_flux2<false>(lo2(qL), lo2(sL), lo2(qR), lo2(sR), lo2(qL), lo2(qL), lo2(qL), lo2(qL),
-                                  dup(lf_al[e]), dup(1.0f), dup(0.5f), tab(ka, 4 + d), tab(ka, 7 + d), tab(ka, 10 + d));
-        f2 fb = face_flux2<false>(hi2(qL), hi2(sL), hi2(qR), hi2(sR), hi2(qL), hi2(qL), hi2(qL), hi2(qL),
-                                  dup(lf_al[e]), dup(1.0f), dup(0.5f), tab(kb, 4 + d), tab(kb, 7 + d), tab(kb, 10 + d));
-        if (VEL) {
-          // the low face lies between slots bb (below) and bb + st (above)
-          const float wl = lf_wl[e], hv = lf_hv[e];
-          float4 iv;
-          if (wl == 0.5f) {
-            (void)RT_IDX(bb - st, G::nbox);
-            (void)RT_IDX(bb + 2 * st, G::nbox);
-            const float4 l = iv_state4(s_IV4, bb, st, hv), r = iv_state4(s_IV4, bb + st, st, -hv);
-            iv = mk4(p_mul(dup(0.5f), p_add(lo2(l), lo2(r))), p_mul(dup(0.5f), p_add(hi2(l), hi2(r))));
-          } else {
-            (void)RT_IDX((wl > 0.5f ? bb : bb + st) - st, G::nbox);
-            (void)RT_IDX((wl > 0.5f ? bb : bb + st) + st, G::nbox);
-            iv = iv_state4(s_IV4, wl > 0.5f ? bb : bb + st, st, wl > 0.5f ? hv : -hv);
-          }
-          fa = p_fma(tab(ka, 10 + d), lo2(iv), fa);
-          fb = p_fma(tab(kb, 10 + d), hi2(iv), fb);
-        }
-        s_fx4[RT_IDX(lf_fx[e], G::FX3)] = mk4(fa, fb);
-      }
-    }
-    __syncthreads();
-
-    // ---- phase 4: Delta F of the quad ---------------------------------------
-    {
-      f2 da = dup(0.0f), db = dup(0.0f);
-#pragma unroll
-      for (int d = 0; d < DIM; ++d) {
-        const float4 fl = s_fx4[RT_IDX(own_fx[d], G::FX3)];
-        da = p_add(da, p_sub(lo2(fl), lo2(fhi[d])));
-        db = p_add(db, p_sub(hi2(fl), hi2(fhi[d])));
-      }
-      if (valid) *qout = mk4(da, db);
-    }
-    qout += N;
+    for (int e = 0; e < kLow; ++e) special |= lf_fx[e] >= 0 && lf_wl[e] == 0.5f;
   }
+  const bool general = __any_sync(0xffffffffu, __syncthreads_or(special) != 0);   // also: the shared table is complete
+
+  auto transport = [&](auto tag) {
+    constexpr bool GEN = decltype(tag)::value;
+    const float4 *qin = I4;
+    float4 *qout = O4 + c;
+    for (int j = 0; j < NQ; ++j) {
+      const int m = 4 * j;   // angles past M read zero table entries
+      // ---- phase 1: stage I~ and IV of the cross cells -----------------------
+      {
+        const float4 nx4 = tab4(j, 0), ny4 = tab4(j, 1), nz4 = tab4(j, 2);
+        const f2 nxa = lo2(nx4), nya = lo2(ny4), nza = lo2(nz4);
+        const f2 nxb = hi2(nx4), nyb = hi2(ny4), nzb = hi2(nz4);
+#pragma unroll
+        for (int s = 0; s < kSlots; ++s) {
+          if (!slot_full(s) && sl_box[s] < 0) continue;
+          f2 Ia = lo2(pf[s]), Ib = hi2(pf[s]);
+          if (GEN && sl_code[s]) {
+            const int axis = (sl_code[s] >> 2) & 3, side = (sl_code[s] >> 4) & 1, face = axis * 2 + side;
+            const float4 mu4 = tab4(j, axis);
+            const f2 mua = lo2(mu4), mub = hi2(mu4);
+            const bool infl = (sl_code[s] & 2) != 0;
+            if (side ? (mua.x < 0.0f) : (mua.x > 0.0f)) Ia.x = infl ? inflow(face, m) : 0.0f;
+            if (side ? (mua.y < 0.0f) : (mua.y > 0.0f)) Ia.y = infl ? inflow(face, m + 1) : 0.0f;
+            if (side ? (mub.x < 0.0f) : (mub.x > 0.0f)) Ib.x = infl ? inflow(face, m + 2) : 0.0f;
+            if (side ? (mub.y < 0.0f) : (mub.y > 0.0f)) Ib.y = infl ? inflow(face, m + 3) : 0.0f;
+          }
+          if (VEL) {
+            const f2 w0 = dup(sl_w[s][0]), w1 = dup(sl_w[s][1]), w2 = dup(sl_w[s][2]);
+            const f2 IVa = p_fma(nxa, w0, p_fma(nya, w1, p_mul(nza, w2)));
+            const f2 IVb = p_fma(nxb, w0, p_fma(nyb, w1, p_mul(nzb, w2)));
+            s_IV4[RT_IDX(sl_box[s], G::nbox)] = mk4(IVa, IVb);
+            s_It4[RT_IDX(sl_box[s], G::nbox)] = mk4(p_fma(IVa, dup(-invC), Ia), p_fma(IVb, dup(-invC), Ib));
+          } else {
+            s_It4[RT_IDX(sl_box[s], G::nbox)] = mk4(Ia, Ib);
+          }
+        }
+      }
+      if (j + 1 < NQ) {
+        qin += N;
+#pragma unroll
+        for (int s = 0; s < kSlots; ++s)
+          if (slot_full(s) || sl_box[s] >= 0) pf[s] = qin[RT_IDX(sl_g[s], N)];
+      }
+      __syncthreads();
+
+      // ---- phase 2: half slopes of I~ (own cell, extension cells) --------------
+      {
+        const float4 q0 = s_It4[RT_IDX(bo, G::nbox)];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+          const int st = bstride[d];
+          const float4 qm = s_It4[RT_IDX(bo - st, G::nbox)], qp = s_It4[RT_IDX(bo + st, G::nbox)];
+          s_sI4[RT_IDX(own_sl[d], G::SL3)] = mk4(vl_half2(lo2(qm), lo2(q0), lo2(qp)), vl_half2(hi2(qm), hi2(q0), hi2(qp)));
+        }
+#pragma unroll
+        for (int e = 0; e < kExt; ++e) {
+          if ((e + 1) * nthr > G::next && ext_si[e] < 0) continue;
+          const int bb = ext_bb[e], st = ext_st[e];
+          const float4 qm = s_It4[RT_IDX(bb - st, G::nbox)], qc = s_It4[RT_IDX(bb, G::nbox)],
+                       qp = s_It4[RT_IDX(bb + st, G::nbox)];
+          s_sI4[RT_IDX(ext_si[e], G::SL3)] = mk4(vl_half2(lo2(qm), lo2(qc), lo2(qp)), vl_half2(hi2(qm), hi2(qc), hi2(qp)));
+        }
+      }
+      __syncthreads();
+
+      // ---- phase 3: face fluxes (pre-multiplied by dt/dx) ----------------------
+      float4 fhi[3];
+      {
+        const float4 q0 = s_It4[bo];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+          const int st = bstride[d];
+          const int sl = own_sl[d], sn = own_sl[d] + G::sl_step(d);
+          const float4 s0 = s_sI4[RT_IDX(sl, G::SL3)], q1 = s_It4[RT_IDX(bo + st, G::nbox)], s1 = s_sI4[RT_IDX(sn, G::SL3)];
+          const float4 hc4 = tab4(j, 4 + d), hca4 = tab4(j, 7 + d), mud4 = tab4(j, 10 + d);
+          f2 fa = face_flux2<false>(lo2(q0), lo2(s0), lo2(q1), lo2(s1), lo2(q0), lo2(q0), lo2(q0), lo2(q0),
+                                    dup(fu_al[d]), dup(1.0f), dup(0.5f), lo2(hc4), lo2(hca4), lo2(mud4));
+          f2 fb = face_flux2<false>(hi2(q0), hi2(s0), hi2(q1), hi2(s1), hi2(q0), hi2(q0), hi2(q0), hi2(q0),
+                                    dup(fu_al[d]), dup(1.0f), dup(0.5f), hi2(hc4), hi2(hca4), hi2(mud4));
+          if (VEL) {
+            float4 iv;
+            if (GEN && iv_mean[d]) {
+              (void)RT_IDX(bo - st, G::nbox);
+              (void)RT_IDX(bo + 2 * st, G::nbox);
+              const float4 l = iv_state4(s_IV4, bo, st, fu_hv[d]), r = iv_state4(s_IV4, bo + st, st, -fu_hv[d]);
+              iv = mk4(p_mul(dup(0.5f), p_add(lo2(l), lo2(r))), p_mul(dup(0.5f), p_add(hi2(l), hi2(r))));
+            } else {
+              (void)RT_IDX(bo + iv_off[d] - st, G::nbox);
+              (void)RT_IDX(bo + iv_off[d] + st, G::nbox);
+              iv = iv_state4(s_IV4, bo + iv_off[d], st, iv_sg[d]);
+            }
+            fa = p_fma(lo2(mud4), lo2(iv), fa);
+            fb = p_fma(hi2(mud4), hi2(iv), fb);
+          }
+          fhi[d] = mk4(fa, fb);
+          s_fx4[RT_IDX(own_fx[d] + G::fx_step(d), G::FX3)] = fhi[d];
+        }
+#pragma unroll
+        for (int e = 0; e < kLow; ++e) {
+          if ((e + 1) * nthr > G::nlow && lf_fx[e] < 0) continue;
+          const int d = lf_d[e], bb = lf_bb[e], st = d == 0 ? 1 : bstride[d == 1 ? 1 : 2];
+          const int si = lf_si[e], si1 = lf_si[e] + lf_sstep[e];
+          const float4 qL = s_It4[RT_IDX(bb, G::nbox)], sL = s_sI4[RT_IDX(si, G::SL3)], qR = s_It4[RT_IDX(bb + st, G::nbox)],
+                       sR = s_sI4[RT_IDX(si1, G::SL3)];
+          const float4 hc4 = tab4(j, 4 + d), hca4 = tab4(j, 7 + d), mud4 = tab4(j, 10 + d);
+          f2 fa = face_flux2<false>(lo2(qL), lo2(sL), lo2(qR), lo2(sR), lo2(qL), lo2(qL), lo2(qL), lo2(qL),
+                                    dup(lf_al[e]), dup(1.0f), dup(0.5f), lo2(hc4), lo2(hca4), lo2(mud4));
+          f2 fb = face_flux2<false>(hi2(qL), hi2(sL), hi2(qR), hi2(sR), hi2(qL), hi2(qL), hi2(qL), hi2(qL),
+                                    dup(lf_al[e]), dup(1.0f), dup(0.5f), hi2(hc4), hi2(hca4), hi2(mud4));
+          if (VEL) {
+            // the low face lies between slots bb (below) and bb + st (above)
+            const float wl = lf_wl[e], hv = lf_hv[e];
+            float4 iv;
+            if (GEN && wl == 0.5f) {
+              (void)RT_IDX(bb - st, G::nbox);
+              (void)RT_IDX(bb + 2 * st, G::nbox);
+              const float4 l = iv_state4(s_IV4, bb, st, hv), r = iv_state4(s_IV4, bb + st, st, -hv);
+              iv = mk4(p_mul(dup(0.5f), p_add(lo2(l), lo2(r))), p_mul(dup(0.5f), p_add(hi2(l), hi2(r))));
+            } else {
+              (void)RT_IDX((wl > 0.5f ? bb : bb + st) - st, G::nbox);
+              (void)RT_IDX((wl > 0.5f ? bb : bb + st) + st, G::nbox);
+              iv = iv_state4(s_IV4, wl > 0.5f ? bb : bb + st, st, wl > 0.5f ? hv : -hv);
+            }
+            fa = p_fma(lo2(mud4), lo2(iv), fa);
+            fb = p_fma(hi2(mud4), hi2(iv), fb);
+          }
+          s_fx4[RT_IDX(lf_fx[e], G::FX3)] = mk4(fa, fb);
+        }
+      }
+      __syncthreads();
+
+      // ---- phase 4: Delta F of the quad ---------------------------------------
+      {
+        f2 da = dup(0.0f), db = dup(0.0f);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+          const float4 fl = s_fx4[RT_IDX(own_fx[d], G::FX3)];
+          da = p_add(da, p_sub(lo2(fl), lo2(fhi[d])));
+          db = p_add(db, p_sub(hi2(fl), hi2(fhi[d])));
+        }
+        if (valid) *qout = mk4(da, db);
+      }
+      qout += N;
+    }
+  };
+  if (general)
+    transport(BoolTag<true>{});
+  else
+    transport(BoolTag<false>{});
 
   if (!valid) return;
 
@@ -618,10 +655,12 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
         d4n = pq[N];
       }
       f2 Qv[2];
+      const float4 nx4 = tab4(j, 0), ny4 = tab4(j, 1), nz4 = tab4(j, 2), W4 = tab4(j, 3);
+      const float4 wx4 = tab4(j, 13), wy4 = tab4(j, 14), wz4 = tab4(j, 15);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int k = 2 * j + h;
-        const f2 nx = tab(k, 0), ny = tab(k, 1), nz = tab(k, 2), Wm = tab(k, 3);
+        const f2 nx = h == 0 ? lo2(nx4) : hi2(nx4), ny = h == 0 ? lo2(ny4) : hi2(ny4);
+        const f2 nz = h == 0 ? lo2(nz4) : hi2(nz4), Wm = h == 0 ? lo2(W4) : hi2(W4);
         const f2 I0 = h == 0 ? make_float2(i4.x, i4.y) : make_float2(i4.z, i4.w);
         const f2 dF = h == 0 ? make_float2(d4.x, d4.y) : make_float2(d4.z, d4.w);
         f2 vn = dup(0.0f), rd = dup(rd0), ra = dup(ra0);
@@ -669,9 +708,9 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
           Bdvk = p_fma(bwar, vn, Bdvk);
           BQk = p_fma(bwa, Q, BQk);
         }
-        pre0 = p_fma(tab(k, 13), gd, pre0);
-        pre1 = p_fma(tab(k, 14), gd, pre1);
-        pre2 = p_fma(tab(k, 15), gd, pre2);
+        pre0 = p_fma(h == 0 ? lo2(wx4) : hi2(wx4), gd, pre0);
+        pre1 = p_fma(h == 0 ? lo2(wy4) : hi2(wy4), gd, pre1);
+        pre2 = p_fma(h == 0 ? lo2(wz4) : hi2(wz4), gd, pre2);
       }
       *pq = make_float4(Qv[0].x, Qv[0].y, Qv[1].x, Qv[1].y);
       pi += N;
@@ -773,10 +812,12 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
       const float4 cur = q4;
       if (j + 1 < NQ) q4 = pq[N];   // the next quad, loaded before this one is overwritten
       f2 Iv[2];
+      const float4 nx4 = tab4(j, 0), ny4 = tab4(j, 1), nz4 = tab4(j, 2), W4 = tab4(j, 3);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int k = 2 * j + h;
-        const f2 nx = tab(k, 0), ny = tab(k, 1), nz = tab(k, 2), Wm = tab(k, 3);
+        const f2 nx = h == 0 ? lo2(nx4) : hi2(nx4), ny = h == 0 ? lo2(ny4) : hi2(ny4);
+        const f2 nz = h == 0 ? lo2(nz4) : hi2(nz4), Wm = h == 0 ? lo2(W4) : hi2(W4);
         const f2 Q = h == 0 ? make_float2(cur.x, cur.y) : make_float2(cur.z, cur.w);
         f2 vn = dup(0.0f), rd = dup(rd0), ra = dup(ra0);
         if (VEL) {

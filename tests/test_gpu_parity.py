@@ -72,6 +72,32 @@ def test_box3d_ragged_many_tiles_mixed():
     _check_mixed(g, o)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_velocity_zero_in_half_the_box(precision):
+    # v = 0 for x < 18: every face there has zero velocity (the IV state at
+    # the face is the mean of its two cells' states) while the box's random
+    # flow moves the rest, so tiles with and without such faces, and ragged
+    # tiles, run in the same step
+    wl = wlmod.box3d(n=37, angles="s4", steps=0)
+    v = wl["v"].reshape(3, 37, 37, 37).copy()
+    v[:, :, :, :18] = 0.0
+    wl["v"] = v.reshape(3, -1)
+    g, o = run_both(wl, 3, precision, threads=8)
+    if precision == "fp64":
+        _check_fp64(g, o)
+    else:
+        _check_mixed(g, o)
+
+
+def test_flow_along_one_axis_2d():
+    # 2-D flow along x only: every y face has zero velocity
+    wl = wlmod.shadow2d(nx=40, ny=24, angles="s4", steps=0)
+    wl["v"] = np.zeros_like(wl["v"])
+    wl["v"][0] = 0.04 * wl["C"]
+    g, o = run_both(wl, 10, "fp32")
+    _check_mixed(g, o)
+
+
 def test_single_cell_and_single_angle():
     # degenerate sizes: one cell (periodic onto itself) and one angle (W = 1)
     wl = wlmod.slab1d(n=1, M=2, steps=0)

@@ -66,7 +66,7 @@ CASES = [
     ("box3d", dict(n=12, angles="s4", steps=0)),
     ("shadow2d", dict(nx=40, ny=20, angles="s4", steps=0)),
     ("slab1d", dict(n=700, steps=0)),
-    ("box3d", dict(n=64, angles="s4", steps=0)),   # 512 tiles of 16x8x4: every CTA walks several
+    ("box3d", dict(n=64, angles="s4", steps=0)),   # 1024 tiles of 8x8x4: every CTA walks several
 ]
 
 
