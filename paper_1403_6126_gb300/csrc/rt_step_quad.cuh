@@ -634,14 +634,16 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
   // Per angle: d = A0 - A1 vn, a' = a0 - a1 vn (rd = 1/d, ra = 1/a'), rr = r_m
   // - R (Step 4's right-hand side: I^n, plus Delta F when it goes to Step 4),
   // stored Q_m = rd rr (+ Delta F when it goes to Step 5).  Sums: T_k = sum W
-  // vn^k rd, U_k = sum W vn^k rd rr, Vw = sum W vn, Gq = sum W vn^2; with wa =
-  // W ra: As1 = sum wa, Va = sum wa vn, Ad / Adv = sum wa rd (vn), AQ = sum wa
-  // Q; the beta-weighted Bs, Bv, Bd, Bdv, BQ, and Bw = sum beta W; pre = sum
-  // W n (I^n + Delta F - R).
-  f2 U0 = dup(0.0f), U1 = dup(0.0f), U2 = dup(0.0f), Vw = dup(0.0f), Gq = dup(0.0f);
+  // vn^k rd, U_k = sum W vn^k rd rr; with wa = W ra: As1 = sum wa, Va = sum wa
+  // vn, Ad / Adv = sum wa rd (vn), AQ = sum wa Q; the beta-weighted Bs, Bv,
+  // Bd, Bdv, BQ; pre = sum W n (I^n + Delta F - R).  The sums that depend on
+  // the angle only through vn = n.v and its square (Vw = sum W vn, Gq = sum W
+  // vn^2, Bw = sum beta W) are the table's own quadrature sums of W n and W n
+  // n contracted with v, after the loop.
+  f2 U0 = dup(0.0f), U1 = dup(0.0f), U2 = dup(0.0f);
   f2 T0p = dup(0.0f), T1p = dup(0.0f), T2p = dup(0.0f), T3p = dup(0.0f);
   f2 As1k = dup(0.0f), Vak = dup(0.0f), Adk = dup(0.0f), Advk = dup(0.0f), AQk = dup(0.0f);
-  f2 Bsk = dup(0.0f), Bwk = dup(0.0f), Bvk = dup(0.0f), Bdk = dup(0.0f), Bdvk = dup(0.0f), BQk = dup(0.0f);
+  f2 Bsk = dup(0.0f), Bvk = dup(0.0f), Bdk = dup(0.0f), Bdvk = dup(0.0f), BQk = dup(0.0f);
   f2 pre0 = dup(0.0f), pre1 = dup(0.0f), pre2 = dup(0.0f);
   {
     const float4 *pi = I4 + c;
@@ -689,8 +691,6 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
           T3p = p_fma(x2, vn, T3p);
           U1 = p_add(U1, y1);
           U2 = p_fma(y1, vn, U2);
-          Vw = p_fma(Wm, vn, Vw);
-          Gq = p_fma(p_mul(Wm, vn), vn, Gq);
         }
         As1k = p_fma(Wm, ra, As1k);
         Adk = p_fma(wa, rd, Adk);
@@ -702,7 +702,6 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
           const f2 bt = p_fma(vn, p_fma(dup(bt2), vn, dup(bt1)), dup(bt0));
           const f2 bwa = p_mul(bt, wa), bwar = p_mul(bwa, rd);
           Bsk = p_fma(bt, wa, Bsk);
-          Bwk = p_fma(bt, Wm, Bwk);
           Bvk = p_fma(bwa, vn, Bvk);
           Bdk = p_fma(bwa, rd, Bdk);
           Bdvk = p_fma(bwar, vn, Bdvk);
@@ -727,9 +726,15 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
     return fmaf(-t, wn, t);
   };
   const float T0s = hsum(T0p), T1s = hsum(T1p), T2s = hsum(T2p), T3s = hsum(T3p);
-  const float U0s = hsum(U0), U1s = hsum(U1), U2s = hsum(U2), Vws = hsum(Vw), Gqs = hsum(Gq);
+  const float U0s = hsum(U0), U1s = hsum(U1), U2s = hsum(U2);
+  // sum W n_i and sum W n_i n_j (normalised, from the table in double)
+  auto ms = [&](int i) { return a.msum[i][0] + a.msum[i][1]; };
+  const float Vws = vt[0] * ms(1) + vt[1] * ms(2) + vt[2] * ms(3);
+  const float Gqs = vt[0] * vt[0] * ms(4) + vt[1] * vt[1] * ms(5) + vt[2] * vt[2] * ms(6) +
+                    2.0f * (vt[0] * vt[1] * ms(7) + vt[0] * vt[2] * ms(8) + vt[1] * vt[2] * ms(9));
   const float As1 = hsum(As1k), Va = hsum(Vak), Ad = hsum(Adk), Adv = hsum(Advk), AQ = hsum(AQk);
-  const float Bs = hsum(Bsk), Bw = hsum(Bwk), Bv = hsum(Bvk), Bd = hsum(Bdk), Bdv = hsum(Bdvk), BQ = hsum(BQk);
+  const float Bs = hsum(Bsk), Bv = hsum(Bvk), Bd = hsum(Bdk), Bdv = hsum(Bdvk), BQ = hsum(BQk);
+  const float Bw = bt0 + bt1 * Vws + bt2 * Gqs;
 
   // ---- Step 4 solve (sec. 4.3) in dth = theta - R ------------------------------
   // Each row reads I'_m - theta = rd (rr - dth - kappa S + 4 A1 theta vn), so
