@@ -336,6 +336,16 @@ rt_status rt_server_create(size_t hbm_budget_bytes, const rt_options *opts, rt_s
 rt_status rt_submit(rt_server *s, const rt_grid *grid, const rt_angles *angles, double Crat, double Prat,
                     const double *rho, const double *T, const double *v, const double *sigma_a,
                     const double *sigma_s, int nsteps, rt_ticket *out);
+/* rt_submit with incoming intensities for the grid's RT_BC_INFLOW faces
+ * (the sec. 5.8 beams): inflow is host memory [3][2][M] (axis, side, angle;
+ * the layout of rt_noalloc_fields.inflow), read for each face whose bc is
+ * RT_BC_INFLOW as rt_set_inflow would read it, or NULL (those faces then
+ * let no radiation in).  RT_E_NONFINITE for a negative or non-finite
+ * value.  The result is bitwise the one the problem gets alone through
+ * rt_step after rt_set_inflow with the same values. */
+rt_status rt_submit_inflow(rt_server *s, const rt_grid *grid, const rt_angles *angles, double Crat, double Prat,
+                           const double *rho, const double *T, const double *v, const double *sigma_a,
+                           const double *sigma_s, const double *inflow, int nsteps, rt_ticket *out);
 /* Non-blocking.  RT_PENDING while the request is queued or running.  Once
  * it is done: RT_OK and E (N), F (3N), P (6N) copied out (NULL skips a
  * field) with the submit-to-result latency in seconds, or the request's

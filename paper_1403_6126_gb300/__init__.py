@@ -108,6 +108,8 @@ def lib():
             "rt_server_create": (I, [ctypes.c_size_t, ctypes.POINTER(rt_options), ctypes.POINTER(V)]),
             "rt_submit": (I, [V, ctypes.POINTER(rt_grid), ctypes.POINTER(rt_angles), D, D, V, V, V, V, V, I,
                               ctypes.POINTER(ctypes.c_longlong)]),
+            "rt_submit_inflow": (I, [V, ctypes.POINTER(rt_grid), ctypes.POINTER(rt_angles), D, D, V, V, V, V, V, V,
+                                     I, ctypes.POINTER(ctypes.c_longlong)]),
             "rt_poll": (I, [V, ctypes.c_longlong, V, V, V, ctypes.POINTER(D)]),
             "rt_server_wait": (I, [V, ctypes.c_longlong, D]),
             "rt_server_stats": (I, [V, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(I), ctypes.POINTER(I),
@@ -306,6 +308,15 @@ def rt_submit(server, grid, angles, Crat, Prat, rho, T, v, sigma_a, sigma_s, nst
     t = ctypes.c_longlong(0)
     _check(lib().rt_submit(server, ctypes.byref(grid), ctypes.byref(angles), Crat, Prat, _ptr(rho), _ptr(T), _ptr(v),
                            _ptr(sigma_a), _ptr(sigma_s), nsteps, ctypes.byref(t)), "rt_submit")
+    return t.value
+
+
+def rt_submit_inflow(server, grid, angles, Crat, Prat, rho, T, v, sigma_a, sigma_s, inflow, nsteps):
+    """inflow: [3][2][M] float64 host array of incoming intensities per face, or None."""
+    t = ctypes.c_longlong(0)
+    _check(lib().rt_submit_inflow(server, ctypes.byref(grid), ctypes.byref(angles), Crat, Prat, _ptr(rho), _ptr(T),
+                                  _ptr(v), _ptr(sigma_a), _ptr(sigma_s), _ptr(inflow),
+                                  nsteps, ctypes.byref(t)), "rt_submit_inflow")
     return t.value
 
 

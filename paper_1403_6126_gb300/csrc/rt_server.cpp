@@ -13,6 +13,7 @@
 // result is in host memory.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstdlib>
 #include <condition_variable>
 #include <cstring>
@@ -38,6 +39,7 @@ struct Request {
   rt_ticket id = 0;
   rt_grid grid{};
   std::vector<double> n, w, rho, T, v, sa, ss;
+  std::vector<double> inflow;   // [3][2][M] for RT_BC_INFLOW faces, or empty
   double C = 1, P = 1;
   int nsteps = 0, done_steps = 0;
   size_t bytes = 0;
@@ -107,6 +109,13 @@ rt_status start(rt_server *s, Request *r) {
   o.precision = RT_FP32;
   rt_status st = rt_create(&r->grid, &a, r->C, r->P, &o, &r->ctx);
   if (st != RT_OK) return st;
+  const int M = (int)r->w.size();
+  for (int d = 0; d < r->grid.dim && !r->inflow.empty(); ++d)
+    for (int side = 0; side < 2; ++side)
+      if (r->grid.bc[d][side] == RT_BC_INFLOW) {
+        st = rt_set_inflow(r->ctx, d, side, r->inflow.data() + (size_t)(d * 2 + side) * M);
+        if (st != RT_OK) return st;
+      }
   st = rt_set_material(r->ctx, r->rho.data(), r->T.data(), r->v.data(), r->sa.data(), r->ss.data());
   if (st != RT_OK) return st;
   // host copies are no longer needed once the state is on the device
@@ -230,6 +239,12 @@ rt_status rt_server_create(size_t hbm_budget_bytes, const rt_options *opts, rt_s
 rt_status rt_submit(rt_server *s, const rt_grid *g, const rt_angles *a, double Crat, double Prat, const double *rho,
                     const double *T, const double *v, const double *sa, const double *ss, int nsteps,
                     rt_ticket *out) {
+  return rt_submit_inflow(s, g, a, Crat, Prat, rho, T, v, sa, ss, nullptr, nsteps, out);
+}
+
+rt_status rt_submit_inflow(rt_server *s, const rt_grid *g, const rt_angles *a, double Crat, double Prat,
+                           const double *rho, const double *T, const double *v, const double *sa, const double *ss,
+                           const double *inflow, int nsteps, rt_ticket *out) {
   rtg::Range nvtx_range("rt_submit");
   if (!s || !g || !a || !a->n || !a->w || !rho || !T || !v || !sa || !ss || !out)
     return fail(RT_E_INVALID, "rt_submit: NULL argument");
@@ -246,6 +261,9 @@ rt_status rt_submit(rt_server *s, const rt_grid *g, const rt_angles *a, double C
   for (long long i = 0; i < 3 * N && !vel; ++i) vel = v[i] != 0.0;
   if (!rtg::batch_fits(g->dim, a->m, vel))
     return fail(RT_E_INVALID, "rt_submit: too many angles for the batch tile's shared memory");
+  if (inflow)
+    for (long long i = 0; i < 6LL * a->m; ++i)
+      if (!std::isfinite(inflow[i]) || inflow[i] < 0) return fail(RT_E_NONFINITE, "rt_submit: need finite inflow I >= 0");
   Request *r = new (std::nothrow) Request;
   if (!r) return fail(RT_E_NOMEM, "rt_submit: host allocation");
   r->grid = *g;
@@ -259,6 +277,7 @@ rt_status rt_submit(rt_server *s, const rt_grid *g, const rt_angles *a, double C
   r->v.assign(v, v + 3 * N);
   r->sa.assign(sa, sa + N);
   r->ss.assign(ss, ss + N);
+  if (inflow) r->inflow.assign(inflow, inflow + 6 * a->m);
   r->nsteps = nsteps;
   r->bytes = rtg::context_bytes(N, a->m, false);
   if (r->bytes > s->budget) {

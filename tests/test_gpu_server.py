@@ -197,3 +197,65 @@ def test_served_result_matches_the_oracle(req):
     eE = np.abs(E[cells] - Eo).max() / scal["E_max"]
     eF = np.abs(Fg - Fa).max() / max(scal["F_max"], 1e-3 * scal["E_max"])
     assert eE <= 1e-5 and eF <= 1e-5, (eE, eF)
+
+
+def test_served_beam_with_inflow():
+    # The shadow problem (sec. 5.8: a beam entering through the lower x face,
+    # 256x128 cells x 80 angles, 4000 steps) submitted with its inflow table
+    # through rt_submit_inflow beside a periodic request: bitwise the problem
+    # stepped alone with rt_set_inflow, and within the float path's 1e-5 of
+    # the FP64 oracle's stored values (tests/golden/stated_shadow2d.txt).
+    import make_stated_steps as golden
+    name = "shadow2d"
+    dt, steps, scal, cells, Eo, Fo = golden.read(name)
+    wl, n, w, I0, _, _ = golden.inputs(name)
+    g, a, angs, fields = _request(wl)
+    M, N = len(w), int(np.prod(wl["shape"]))
+    inflow = np.zeros((3, 2, M))
+    for (axis, side), rule in wl["inflow"].items():
+        inflow[axis, side] = wlmod.inflow_values(rule, n)
+    assert inflow.any()
+    o = rt.rt_options_default()
+    o.hold_T, o.estimate_v = int(wl["hold_T"]), int(wl["estimate_v"])
+    o.gamma, o.r_ideal, o.cfl = wl["gamma"], wl["R"], wl["cfl"]
+    other = wlmod.shadow2d(nx=40, ny=24, angles="s4", steps=0)
+    other["bc"] = ((0, 0), (0, 0), (0, 0))
+    other["inflow"] = {}
+    og, oa, oangs, ofields = _request(other)
+    with pytest.raises(rt.RTError) as e:           # the table is checked at submission
+        bad = inflow.copy()
+        bad[0, 0, 0] = -1.0
+        server = rt.rt_server_create(1 << 30, o)
+        try:
+            rt.rt_submit_inflow(server, g, a, wl["C"], wl["P"], *fields, bad, 1)
+        finally:
+            rt.rt_server_destroy(server)
+    assert e.value.status == rt.RT_E_NONFINITE
+    server = rt.rt_server_create(8 << 30, o)
+    try:
+        t_other = rt.rt_submit(server, og, oa, other["C"], other["P"], *ofields, 50)
+        t = rt.rt_submit_inflow(server, g, a, wl["C"], wl["P"], *fields, inflow, steps)
+        rt.rt_server_wait(server, t, 600.0)
+        E, F, P = np.zeros(N), np.zeros((3, N)), np.zeros((6, N))
+        rt.rt_poll(server, t, E, F, P)
+        rt.rt_server_wait(server, t_other, 600.0)
+        rt.rt_poll(server, t_other)
+    finally:
+        rt.rt_server_destroy(server)
+    # alone: the same problem through rt_step, its inflow set face by face
+    ctx = gpu_context(wl, n, w, "fp32")
+    ctx.set_material(wl["rho"], wl["T"], wl["v"], wl["sa"], wl["ss"])
+    for _ in range(steps):
+        ctx.step(0.0)
+    ctx.sync()
+    Ea, Fa, Pa = ctx.moments()
+    ctx.close()
+    np.testing.assert_array_equal(E, Ea)
+    np.testing.assert_array_equal(F, Fa)
+    np.testing.assert_array_equal(P, Pa)
+    dim = wl["dim"]
+    Fg = golden.active_flux(F[:, cells], dim)
+    Fs = golden.active_flux(Fo, dim)
+    eE = np.abs(E[cells] - Eo).max() / scal["E_max"]
+    eF = np.abs(Fg - Fs).max() / max(scal["F_max"], 1e-3 * scal["E_max"])
+    assert eE <= 1e-5 and eF <= 1e-5, (eE, eF)
