@@ -243,8 +243,9 @@ rt_status rt_sources(rt_ctx *ctx, double *dE_gas, double *dMom, double *T_new);
  * outputs and state).  With host arrays the grid is cut into slabs of
  * whole tiles along its outermost active axis (z in 3-D, y in 2-D, x in
  * 1-D): the fields of a slab (and its two-plane halo) cross to the device
- * while the previous slab steps, and the sources of a slab cross back while
- * the next one steps.  Other contexts (device_ptrs, bf16 storage, grids of
+ * while the previous slab steps, the sources of a slab cross back while
+ * the next ones step, and consecutive slabs' kernels run on two streams so
+ * that one's first tiles overlap the other's last.  Other contexts (device_ptrs, bf16 storage, grids of
  * one tile layer, the first call) run the three calls in turn.
  * T_new may be T (the next step's temperature); no other output may
  * overlap an input.  Waits for the transfers.  On RT_E_NONFINITE /

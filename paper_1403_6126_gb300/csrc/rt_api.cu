@@ -71,7 +71,7 @@ namespace {
 
 void free_all(rt_ctx *c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
-  for (cudaStream_t s : {c->xs_in, c->xs_cv, c->xs_out}) {
+  for (cudaStream_t s : {c->xs_in, c->xs_cv, c->xs_out, c->xs_k}) {
     if (!s) continue;
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
@@ -155,13 +155,21 @@ size_t rtg::context_bytes(long long N, int M, bool fp64) {
   return rs * (2 * Ms * Nz + 6 * Nz + 10 * Mz) + 8 * (2 * 10 * Nz + 3 * Nz) + 16 * Nz + 2 * sizeof(int) + stage + centers;
 }
 
+cudaError_t rtg::launch_ctx_step_on(rt_ctx *c, const StepArgs<double> &a, bool vel, TileShape t, cudaStream_t s) {
+  return launch_step<double>(a, c->dim, vel, t, s);
+}
+
+cudaError_t rtg::launch_ctx_step_on(rt_ctx *c, const StepArgs<float> &a, bool vel, TileShape t, cudaStream_t s) {
+  if (c->bf16) return launch_step<float>(a, c->dim, vel, t, s);
+  return launch_step_quad(a, c->host_angf.data(), c->host_inflowf.data(), c->dim, vel, t, s);
+}
+
 cudaError_t rtg::launch_ctx_step(rt_ctx *c, const StepArgs<double> &a, bool vel, TileShape t) {
-  return launch_step<double>(a, c->dim, vel, t, c->stream);
+  return launch_ctx_step_on(c, a, vel, t, c->stream);
 }
 
 cudaError_t rtg::launch_ctx_step(rt_ctx *c, const StepArgs<float> &a, bool vel, TileShape t) {
-  if (c->bf16) return launch_step<float>(a, c->dim, vel, t, c->stream);
-  return launch_step_quad(a, c->host_angf.data(), c->host_inflowf.data(), c->dim, vel, t, c->stream);
+  return launch_ctx_step_on(c, a, vel, t, c->stream);
 }
 
 template rtg::StepArgs<float> rtg::make_args<float>(rt_ctx *, double);
@@ -258,10 +266,18 @@ namespace {
 // Copy streams and events of rt_step_coupled, made on first use (kept in the
 // context as they are made, so free_all releases a partial set too).
 rt_status coupled_init(rt_ctx *c) {
-  if (c->xs_in && c->xs_out && c->xs_cv && c->ev_done[rt_ctx::kSlabs - 1]) return RT_OK;
+  if (c->xs_in && c->xs_out && c->xs_cv && c->xs_k && c->ev_done[rt_ctx::kSlabs - 1]) return RT_OK;
+  if (!c->xs_k) RT_CUDA(cudaStreamCreateWithFlags(&c->xs_k, cudaStreamNonBlocking));
   if (!c->xs_in) RT_CUDA(cudaStreamCreateWithFlags(&c->xs_in, cudaStreamNonBlocking));
   if (!c->xs_out) RT_CUDA(cudaStreamCreateWithFlags(&c->xs_out, cudaStreamNonBlocking));
-  if (!c->xs_cv) RT_CUDA(cudaStreamCreateWithFlags(&c->xs_cv, cudaStreamNonBlocking));
+  if (!c->xs_cv) {
+    // the field conversions run at the highest priority: the step's CTAs
+    // fill every SM, and a conversion that waited for a whole slab to drain
+    // would hold up the next slab
+    int lo = 0, hi = 0;
+    RT_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    RT_CUDA(cudaStreamCreateWithPriority(&c->xs_cv, cudaStreamNonBlocking, hi));
+  }
   if (!c->ev_start) RT_CUDA(cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming));
   for (int k = 0; k < rt_ctx::kSlabs; ++k) {
     if (!c->ev_copied[k]) RT_CUDA(cudaEventCreateWithFlags(&c->ev_copied[k], cudaEventDisableTiming));
@@ -284,12 +300,12 @@ rt_status coupled_in(rt_ctx *c, const double *const f[5], long long c0, long lon
 
 // Sources of the cells [c0, c1) back to the caller (all three double on the
 // device), copied on the outgoing stream once ev (recorded after the slab's
-// kernel) has fired.
-rt_status coupled_out(rt_ctx *c, long long c0, long long c1, cudaEvent_t ev, double *dE_gas, double *dMom,
-                      double *T_new) {
+// kernel on stream ks) has fired.
+rt_status coupled_out(rt_ctx *c, long long c0, long long c1, cudaEvent_t ev, cudaStream_t ks, double *dE_gas,
+                      double *dMom, double *T_new) {
   const long long N = c->N, n = c1 - c0;
   const double *s_mom = c->dMom;
-  RT_CUDA(cudaEventRecord(ev, c->stream));
+  RT_CUDA(cudaEventRecord(ev, ks));
   RT_CUDA(cudaStreamWaitEvent(c->xs_out, ev, 0));
   const size_t b = n * sizeof(double);
   if (dE_gas) RT_CUDA(cudaMemcpyAsync(dE_gas + c0, c->dEgas + c0, b, cudaMemcpyDeviceToHost, c->xs_out));
@@ -300,19 +316,20 @@ rt_status coupled_out(rt_ctx *c, long long c0, long long c1, cudaEvent_t ev, dou
   return RT_OK;
 }
 
-// The step's kernel over tile layers [l0, l1) along z (all layers: l1 = 0).
-rt_status coupled_launch(rt_ctx *c, double dt, bool vel, int l0, int l1) {
+// The step's kernel over tile layers [l0, l1) along z (all layers: l1 = 0),
+// on stream s.
+rt_status coupled_launch(rt_ctx *c, double dt, bool vel, int l0, int l1, cudaStream_t s) {
   cudaError_t e;
   if (c->fp64) {
     rtg::StepArgs<double> a = rtg::make_args<double>(c, dt);
     a.outer_begin = l0;
     a.outer_count = l1 - l0;
-    e = rtg::launch_ctx_step(c, a, vel, c->tile);
+    e = rtg::launch_ctx_step_on(c, a, vel, c->tile, s);
   } else {
     rtg::StepArgs<float> a = rtg::make_args<float>(c, dt);
     a.outer_begin = l0;
     a.outer_count = l1 - l0;
-    e = rtg::launch_ctx_step(c, a, vel, c->tile);
+    e = rtg::launch_ctx_step_on(c, a, vel, c->tile, s);
   }
   return e == cudaSuccess ? RT_OK : cuda_fail(e, "step kernel launch");
 }
@@ -929,17 +946,22 @@ rt_status rt_step_coupled(rt_ctx *c, double dt, const double *rho, const double 
   for (int d = 0; d < d_out; ++d) Nxy *= c->n[d];
   const int S = std::min(rt_ctx::kSlabs, layers);
   int L[rt_ctx::kSlabs + 1], e[rt_ctx::kSlabs];   // slab s: tile layers [L[s], L[s+1]), planes up to e[s]
-  // Thin first and last slabs: nothing overlaps the first slab's fields
-  // going over or the last slab's sources coming back.
-  const int thin = S >= 3 ? std::max(1, layers / 16) : 0;
-  L[0] = 0;
-  L[S] = layers;
-  if (thin) {
-    L[1] = thin;
-    L[S - 1] = layers - thin;
-    for (int s = 2; s < S - 1; ++s) L[s] = thin + (int)((long long)(layers - 2 * thin) * (s - 1) / (S - 2));
-  } else {
-    for (int s = 1; s < S; ++s) L[s] = (int)((long long)layers * s / S);
+  // Slab sizes double from each end towards the middle (weights 1, 2, 4,
+  // ..., 4, 2, 1): nothing overlaps the first slab's fields going over or
+  // the last slab's sources coming back, so both are one layer; every other
+  // slab's fields arrive while the slab before it runs (the link moves a
+  // layer's fields ~3x faster than the kernel steps it), and its sources go
+  // back while the slabs after it run.
+  {
+    double w[rt_ctx::kSlabs], wsum = 0, acc = 0;
+    for (int s = 0; s < S; ++s) wsum += (w[s] = std::ldexp(1.0, std::min(s, S - 1 - s)));
+    L[0] = 0;
+    for (int s = 0; s < S; ++s) {
+      acc += w[s];
+      L[s + 1] = std::max(L[s] + 1, (int)std::llround(layers * acc / wsum));
+    }
+    L[S] = layers;
+    for (int s = S - 1; s >= 1; --s) L[s] = std::min(L[s], L[s + 1] - 1);
   }
   for (int s = 0; s < S; ++s) e[s] = std::min(L[s + 1] * TZ, nz);
   // A slab reads the fields of two planes beyond its own on each side.  The
@@ -959,6 +981,7 @@ rt_status rt_step_coupled(rt_ctx *c, double dt, const double *rho, const double 
   RT_CUDA(cudaStreamWaitEvent(c->xs_in, c->ev_start, 0));
   RT_CUDA(cudaStreamWaitEvent(c->xs_cv, c->ev_start, 0));
   RT_CUDA(cudaStreamWaitEvent(c->xs_out, c->ev_start, 0));
+  RT_CUDA(cudaStreamWaitEvent(c->xs_k, c->ev_start, 0));
   const bool vel = rtg::velocity_on(c);   // kernel of the previous fields; checked below
   int sent = 0;
   for (int s = 0; s < S; ++s) {
@@ -972,11 +995,20 @@ rt_status rt_step_coupled(rt_ctx *c, double dt, const double *rho, const double 
     if (s == 0 && top < nz && (st = fields_in(c, top * Nxy, nz * Nxy, true, c->xs_cv)) != RT_OK) return st;
     if (upto > sent && (st = fields_in(c, sent * Nxy, upto * Nxy, true, c->xs_cv)) != RT_OK) return st;
     RT_CUDA(cudaEventRecord(c->ev_in[s], c->xs_cv));
-    RT_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in[s], 0));
+    // slabs alternate between two streams, so that a slab's first CTAs take
+    // the SMs that the previous slab's last wave leaves idle (the slabs
+    // write disjoint cells and read only step-n state and converted fields)
+    cudaStream_t ks = (s & 1) ? c->xs_k : c->stream;
+    RT_CUDA(cudaStreamWaitEvent(ks, c->ev_in[s], 0));
     sent = std::max(sent, upto);
-    if ((st = coupled_launch(c, dt, vel, L[s], L[s + 1])) != RT_OK) return st;
+    if ((st = coupled_launch(c, dt, vel, L[s], L[s + 1], ks)) != RT_OK) return st;
     const long long c0 = (long long)L[s] * TZ * Nxy, c1 = (long long)e[s] * Nxy;
-    if ((st = coupled_out(c, c0, c1, c->ev_done[s], dE_gas, dMom, T_new)) != RT_OK) return st;
+    if ((st = coupled_out(c, c0, c1, c->ev_done[s], ks, dE_gas, dMom, T_new)) != RT_OK) return st;
+  }
+  if (S > 1) {
+    // the context's stream goes on after the last slab of the second stream
+    const int last_k = ((S - 1) & 1) ? S - 1 : S - 2;
+    RT_CUDA(cudaStreamWaitEvent(c->stream, c->ev_done[last_k], 0));
   }
   int flag = 0;
   RT_CUDA(cudaMemcpyAsync(&flag, c->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -993,7 +1025,7 @@ rt_status rt_step_coupled(rt_ctx *c, double dt, const double *rho, const double 
     // the fields switched the velocity terms on or off: step again from the
     // staged T with the other kernel
     RT_CUDA(cudaMemcpyAsync(c->T, c->stage + c->N, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    if ((st = coupled_launch(c, dt, !vel, 0, 0)) != RT_OK) return st;
+    if ((st = coupled_launch(c, dt, !vel, 0, 0, c->stream)) != RT_OK) return st;
     c->cur = 1 - c->cur;
     return rt_sources(c, dE_gas, dMom, T_new);
   }

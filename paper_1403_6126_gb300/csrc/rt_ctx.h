@@ -49,10 +49,10 @@ struct rt_ctx {
   bool graph_vel = false;
   void *batch = nullptr;  // the rt_batch this context belongs to, if any
   // rt_step_coupled: copy streams (fields in, sources out), a stream for the
-  // field conversions, and the events that order them against the slab
-  // launches, made on first use
-  static constexpr int kSlabs = 4;
-  cudaStream_t xs_in = nullptr, xs_out = nullptr, xs_cv = nullptr;
+  // field conversions, a second stream for every other slab's kernel, and
+  // the events that order them against the slab launches, made on first use
+  static constexpr int kSlabs = 8;
+  cudaStream_t xs_in = nullptr, xs_out = nullptr, xs_cv = nullptr, xs_k = nullptr;
   cudaEvent_t ev_start = nullptr, ev_copied[kSlabs] = {}, ev_in[kSlabs] = {}, ev_done[kSlabs] = {};
 };
 
@@ -85,6 +85,9 @@ size_t context_bytes(long long N, int M, bool fp64);
 // kernel's launch-parameter table).
 cudaError_t launch_ctx_step(rt_ctx *c, const StepArgs<float> &a, bool vel, TileShape t);
 cudaError_t launch_ctx_step(rt_ctx *c, const StepArgs<double> &a, bool vel, TileShape t);
+// The same on stream s instead of the context's stream.
+cudaError_t launch_ctx_step_on(rt_ctx *c, const StepArgs<float> &a, bool vel, TileShape t, cudaStream_t s);
+cudaError_t launch_ctx_step_on(rt_ctx *c, const StepArgs<double> &a, bool vel, TileShape t, cudaStream_t s);
 // Whether a problem of this dimension and angle count fits the batch tile.
 bool batch_fits(int dim, int M, bool vel);
 }  // namespace rtg

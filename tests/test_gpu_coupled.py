@@ -78,7 +78,8 @@ def _assert_same(hist, out):
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_coupled_equals_three_calls_periodic(precision):
-    # 40 planes: 10 tile layers of 4 in four uneven slabs; the periodic wrap
+    # 40 planes: 10 tile layers of 4 in eight slabs (1, 1, 1, 2, 2, 1, 1, 1
+    # layers) on two alternating streams; the periodic wrap
     # makes slab 0 read the top planes
     _assert_same(*_run_pair(_box((40, 24, 32), 31), precision, 4))
 
