@@ -4,8 +4,8 @@
 // Storage.  The intensity of a float context is kept as Q = ceil(M/4) planes
 // of float4: I[q][c] holds angles 4q .. 4q+3 of cell c (angles past M are
 // zero padding).  A thread reads or writes the four angles of its cell with
-// one 128-bit access, and the 16 x-consecutive cells of a tile row cover two
-// whole 128-byte lines.
+// one 128-bit access, and the 8 x-consecutive cells of a tile row cover one
+// whole 128-byte line.
 //
 // Same method, tile geometry and reading of the paper as process_tile2
 // (rt_step_pair.cuh): one thread per cell, every per-angle quantity carried
