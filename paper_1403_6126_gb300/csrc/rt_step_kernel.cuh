@@ -136,7 +136,9 @@ struct Geo {
   int ncell = 1, nbox = 1, ncross = 1, next = 0, nlow = 0;
   int RX = 1, RXF = 1;          // row lengths of the x slope / flux arrays
   int sl_off[4] = {0, 0, 0, 0}, fx_off[4] = {0, 0, 0, 0};  // slope / flux array offsets per axis
-  __host__ __device__ constexpr void init(int dim, int tx, int ty, int tz) {
+  bool quad = false;            // the layout of the quad kernel (16-byte entries)
+  __host__ __device__ constexpr void init(int dim, int tx, int ty, int tz, bool q = false) {
+    quad = q;
     T[0] = tx; T[1] = ty; T[2] = tz;
     ncell = tx * ty * tz;
     nbox = 1;
@@ -148,10 +150,21 @@ struct Geo {
     // congruent to tx mod 32, which puts those rows on disjoint banks.
     RX = tx >= 32 ? tx + 2 : tx + 32;
     RXF = tx >= 32 ? tx + 1 : tx + 32;
+    // The quad kernel's 16-byte entries take eight lanes per shared-memory
+    // wavefront.  Its x-halo, x-extension and lowest-x-face work items run
+    // along y, so there the box row and the rows of the x arrays (y
+    // innermost) have odd lengths: eight items consecutive in y then fall on
+    // eight different bank groups.  Tile rows along x are conflict free
+    // with any row length.
+    if (quad) {
+      RX = (tx + 2) | 1;
+      RXF = (tx + 1) | 1;
+    }
     sl_off[0] = fx_off[0] = 0;
     for (int d = 0; d < 3; ++d) {
       bool act = d < dim;
       B[d] = act ? T[d] + 2 * kHalo : 1;
+      if (quad && d == 0 && dim >= 2) B[0] |= 1;
       nbox *= B[d];
       P[d] = ncell / T[d];
       ncross += act ? 2 * kHalo * P[d] : 0;
@@ -163,7 +176,7 @@ struct Geo {
   }
   // Slope of the cell at local (lx, ly, lz) along axis d, l_d in [-1, T_d].
   __host__ __device__ constexpr int sl_idx(int d, int lx, int ly, int lz) const {
-    return d == 0 ? (lx + 1) + RX * (lz + T[2] * ly)
+    return d == 0 ? (lx + 1) + RX * (quad ? ly + T[1] * lz : lz + T[2] * ly)
            : d == 1 ? lx + T[0] * (lz + T[2] * (ly + 1))
                     : lx + T[0] * ((lz + 1) + (T[2] + 2) * ly);
   }
@@ -173,7 +186,9 @@ struct Geo {
   __host__ __device__ constexpr int sl_step(int d) const { return d == 0 ? 1 : d == 1 ? T[0] * T[2] : T[0]; }
   // Flux of face f along d (between local f-1 and f) in the row of (lx, ly, lz).
   __host__ __device__ constexpr int fx_idx(int d, int f, int lx, int ly, int lz) const {
-    return d == 0 ? f + RXF * (lz + T[2] * ly) : d == 1 ? lx + T[0] * (lz + T[2] * f) : lx + T[0] * (f + (T[2] + 1) * ly);
+    return d == 0   ? f + RXF * (quad ? ly + T[1] * lz : lz + T[2] * ly)
+           : d == 1 ? lx + T[0] * (lz + T[2] * f)
+                    : lx + T[0] * (f + (T[2] + 1) * ly);
   }
   __host__ __device__ constexpr int fx_size(int d) const {
     return d == 0 ? RXF * T[2] * T[1] : d == 1 ? T[0] * T[2] * (T[1] + 1) : T[0] * (T[2] + 1) * T[1];
@@ -183,11 +198,11 @@ struct Geo {
 
 // The same geometry for a compile-time shape, as constants, for device
 // code (runtime-indexed member arrays would put the struct in memory).
-template <int DIM, int TX, int TY, int TZ>
+template <int DIM, int TX, int TY, int TZ, bool Q = false>
 struct GeoT {
   __host__ __device__ static constexpr Geo g() {
     Geo x;
-    x.init(DIM, TX, TY, TZ);
+    x.init(DIM, TX, TY, TZ, Q);
     return x;
   }
   static constexpr int ncell = g().ncell, nbox = g().nbox, ncross = g().ncross, next = g().next, nlow = g().nlow;
@@ -202,13 +217,15 @@ struct GeoT {
   __host__ __device__ static constexpr int sl_off(int d) { return d == 0 ? SL0 : d == 1 ? SL1 : SL2; }
   __host__ __device__ static constexpr int fx_off(int d) { return d == 0 ? FX0 : d == 1 ? FX1 : FX2; }
   __host__ __device__ static constexpr int sl_idx(int d, int lx, int ly, int lz) {
-    return d == 0 ? (lx + 1) + RX * (lz + TZ * ly)
+    return d == 0 ? (lx + 1) + RX * (Q ? ly + TY * lz : lz + TZ * ly)
            : d == 1 ? lx + TX * (lz + TZ * (ly + 1))
                     : lx + TX * ((lz + 1) + (TZ + 2) * ly);
   }
   __host__ __device__ static constexpr int sl_step(int d) { return d == 0 ? 1 : d == 1 ? TX * TZ : TX; }
   __host__ __device__ static constexpr int fx_idx(int d, int f, int lx, int ly, int lz) {
-    return d == 0 ? f + RXF * (lz + TZ * ly) : d == 1 ? lx + TX * (lz + TZ * f) : lx + TX * (f + (TZ + 1) * ly);
+    return d == 0   ? f + RXF * (Q ? ly + TY * lz : lz + TZ * ly)
+           : d == 1 ? lx + TX * (lz + TZ * f)
+                    : lx + TX * (f + (TZ + 1) * ly);
   }
   __host__ __device__ static constexpr int fx_step(int d) { return d == 0 ? 1 : d == 1 ? TX * TZ : TX; }
 };

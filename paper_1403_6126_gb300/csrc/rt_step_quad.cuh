@@ -103,7 +103,7 @@ inline void fill_qtable(QTable<P> *t, const float *ang, int M, float C, const fl
 // is not a launch parameter.
 __host__ __device__ inline size_t smem_bytes_q(int dim, int M, bool has_v, int tx, int ty, int tz, bool tab_param) {
   Geo g;
-  g.init(dim, tx, ty, tz);
+  g.init(dim, tx, ty, tz, true);
   const size_t q = has_v ? 2 : 1, pairs = 2 * (size_t)((M + 3) / 4);
   const size_t n4 = q * g.nbox + g.sl_off[3] + g.fx_off[3];
   return (tab_param ? 0 : kTab2 * pairs * sizeof(f2)) + n4 * sizeof(float4) + 16;
@@ -188,7 +188,7 @@ struct BoolTag {
 template <int DIM, bool VEL, int TX, int TY, int TZ, bool TAB_PARAM, int TP>
 __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const QTable<TP> *qt, int tid, int tbx,
                                                int tby, int tbz, unsigned char *smem_raw) {
-  using G = GeoT<DIM, TX, TY, TZ>;
+  using G = GeoT<DIM, TX, TY, TZ, true>;
   constexpr int nthr = G::ncell;
   constexpr int kSlots = slots_for(DIM, TX, TY, TZ);
   constexpr int kExt = (G::next + nthr - 1) / nthr;
