@@ -288,7 +288,10 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
       int kk = k - G::ncell;
       int d = 0;
       while (kk >= 2 * kHalo * G::P(d)) { kk -= 2 * kHalo * G::P(d); ++d; }
-      const int layer = kk / G::P(d), o = kk % G::P(d);
+      // the x halo hands out its four layers fastest: the two cells of a
+      // side share a 32-byte sector of the intensity array, so the loads of
+      // eight consecutive items fill four sectors instead of eight
+      const int layer = d == 0 ? kk % (2 * kHalo) : kk / G::P(d), o = d == 0 ? kk / (2 * kHalo) : kk % G::P(d);
       const int side = layer / kHalo, h = layer % kHalo;
       const int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;
       const int bd = side == 0 ? h : G::T(d) + kHalo + h;
