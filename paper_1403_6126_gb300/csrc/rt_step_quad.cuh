@@ -427,7 +427,12 @@ __device__ __forceinline__ void process_tile_q(const StepArgs<float> &a, const Q
 #pragma unroll
     for (int e = 0; e < kLow; ++e) special |= lf_fx[e] >= 0 && lf_wl[e] == 0.5f;
   }
-  const bool general = __any_sync(0xffffffffu, __syncthreads_or(special) != 0);   // also: the shared table is complete
+  // The CTA-wide vote is also the barrier after which the shared table is
+  // complete.  The warp vote on top of it changes no value (every lane
+  // holds the same one; every tile shape is whole warps) but lets the
+  // compiler see a warp-uniform choice, so the table loads of both copies
+  // stay warp-uniform constant-bank loads.
+  const bool general = __any_sync(0xffffffffu, __syncthreads_or(special) != 0);
 
   auto transport = [&](auto tag) {
     constexpr bool GEN = decltype(tag)::value;
