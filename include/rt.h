@@ -266,7 +266,7 @@ rt_status rt_get_intensity(rt_ctx *ctx, double *I);
  * made by rt_create with the same grid, angles and options, loaded with
  * rt_load_state, continues bitwise as the saved one would have.  buf is
  * host memory owned by the caller.  The paper has no counterpart (its
- * restart files are Athena++'s). */
+ * restart files are Athena's). */
 size_t rt_state_bytes(const rt_ctx *ctx);
 /* Waits for the context's stream, then copies the state into buf (bytes >=
  * rt_state_bytes).  RT_E_STATE before rt_set_material. */
