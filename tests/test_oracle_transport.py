@@ -71,6 +71,34 @@ def test_boundary_kinds_at_unit_courant(kind):
     assert out["I"][1, -1] == 0.0
 
 
+def test_light_crossing_time_step_keeps_transport_bounded():
+    # Step 1 (sec. 4.1): dt from the cell size and the speed of light with a
+    # CFL number of 0.4.  Pinned by what it is for: at that dt the explicit,
+    # unsplit van Leer transport of every ray of the 3-D S8 set (sigma = 0,
+    # periodic, uneven cells) keeps each angle's values inside the range they
+    # started in, step after step; at CFL 1 (a ray along the cube diagonal
+    # then crosses sqrt(3) cells per step) the first step already leaves it.
+    # Inactive axes do not limit dt.
+    n, w = angles.level_symmetric(8)
+    rng = np.random.default_rng(5)
+    p = oracle.Problem((6, 7, 8), (0.1, 0.07, 0.13), n, w, C=3.0, P=1.0)
+    N = p.N
+    flat = lambda I: oracle.step(p, dt, I, np.ones(N), np.ones(N), np.zeros((3, N)), _zeros(N), _zeros(N))["I"]
+    dt = oracle.cfl_dt(p, 0.4)
+    assert dt * p.C / 0.07 == pytest.approx(0.4, rel=1e-15)
+    I0 = rng.uniform(0.0, 1.0, (p.M, N))
+    I = I0
+    for _ in range(100):
+        I = flat(I)
+        assert (I.min(axis=1) >= I0.min(axis=1) - 1e-13).all() and (I.max(axis=1) <= I0.max(axis=1) + 1e-13).all()
+    assert np.ptp(I, axis=1).max() < 0.5 * np.ptp(I0, axis=1).min()     # and it did move them
+    dt = oracle.cfl_dt(p, 1.0)
+    I = flat(I0)
+    assert (I.min(axis=1) < I0.min(axis=1) - 0.1).any() or (I.max(axis=1) > I0.max(axis=1) + 0.1).any()
+    p1 = oracle.Problem((1, 1, 8), (0.1, 1e-9, 1e-9), n, w, C=3.0, P=1.0, dim=1)
+    assert oracle.cfl_dt(p1, 0.4) * 3.0 / 0.1 == pytest.approx(0.4, rel=1e-15)
+
+
 def test_uniform_field_has_no_transport():
     # a constant intensity with uniform J and v gives zero flux divergence
     n, w = angles.level_symmetric(6)
