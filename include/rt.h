@@ -352,8 +352,11 @@ rt_status rt_submit_inflow(rt_server *s, const rt_grid *grid, const rt_angles *a
  * field) with the submit-to-result latency in seconds, or the request's
  * error status; either way the ticket is then released. */
 rt_status rt_poll(rt_server *s, rt_ticket t, double *E, double *F, double *P, double *latency_s);
-/* Blocks until the request is done (timeout_s < 0: no limit); RT_E_TIMEOUT
- * when the limit passes first.  Does not release the ticket. */
+/* Blocks until the request is done (timeout_s < 0 or above 3e8 s: no
+ * limit; RT_E_INVALID for NaN); RT_E_TIMEOUT when the limit passes first.
+ * Does not release the ticket.  If another thread collects the ticket with
+ * rt_poll during the wait, the wait returns RT_OK (the request is done).
+ * No thread may wait on a server that is being destroyed. */
 rt_status rt_server_wait(rt_server *s, rt_ticket t, double timeout_s);
 /* Steps launched so far, requests queued / running, device bytes in use. */
 rt_status rt_server_stats(rt_server *s, long long *steps, int *queued, int *running, size_t *bytes_in_use);

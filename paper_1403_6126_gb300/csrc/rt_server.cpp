@@ -322,17 +322,24 @@ rt_status rt_poll(rt_server *s, rt_ticket t, double *E, double *F, double *P, do
 
 rt_status rt_server_wait(rt_server *s, rt_ticket t, double timeout_s) {
   if (!s) return fail(RT_E_INVALID, "rt_server_wait: NULL server");
+  if (std::isnan(timeout_s)) return fail(RT_E_INVALID, "rt_server_wait: timeout is NaN");
   std::unique_lock<std::mutex> lock(s->mu);
-  auto it = s->all.find(t);
-  if (it == s->all.end()) return fail(RT_E_INVALID, "rt_server_wait: unknown or already collected ticket");
-  Request *r = it->second;
-  auto pred = [&] { return r->state == Request::DONE; };
-  if (timeout_s < 0) {
+  if (s->all.find(t) == s->all.end())
+    return fail(RT_E_INVALID, "rt_server_wait: unknown or already collected ticket");
+  // The request is looked up again at every wake-up: another thread may
+  // collect it with rt_poll meanwhile, which frees it (rt_poll collects only
+  // finished requests, so a ticket gone from the table is done).
+  auto pred = [&] {
+    auto it = s->all.find(t);
+    return it == s->all.end() || it->second->state == Request::DONE;
+  };
+  // beyond about ten years the limit is no limit (and the conversion to the
+  // clock's integer ticks cannot overflow)
+  if (timeout_s < 0 || timeout_s > 3e8) {
     s->done_cv.wait(lock, pred);
-    return RT_OK;
-  }
-  if (!s->done_cv.wait_for(lock, std::chrono::duration<double>(timeout_s), pred))
+  } else if (!s->done_cv.wait_for(lock, std::chrono::duration<double>(timeout_s), pred)) {
     return fail(RT_E_TIMEOUT, "rt_server_wait: timed out");
+  }
   return RT_OK;
 }
 
