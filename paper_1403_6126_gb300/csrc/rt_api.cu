@@ -407,8 +407,9 @@ rt_status rt_create(const rt_grid *g, const rt_angles *ang, double Crat, double 
   if (opts) o = *opts;
   if (o.precision != RT_FP64 && o.precision != RT_FP32 && o.precision != RT_BF16)
     return fail(RT_E_INVALID, "rt_create: precision must be RT_FP64, RT_FP32 or RT_BF16");
-  if (!(o.cfl > 0) || !(o.gamma > 1.0) || !(o.r_ideal > 0))
-    return fail(RT_E_INVALID, "rt_create: need cfl > 0, gamma > 1, r_ideal > 0");
+  if (!(o.cfl > 0) || !(o.gamma > 1.0) || !(o.r_ideal > 0) || !std::isfinite(o.cfl) || !std::isfinite(o.gamma) ||
+      !std::isfinite(o.r_ideal))
+    return fail(RT_E_INVALID, "rt_create: need finite cfl > 0, gamma > 1, r_ideal > 0");
   if (rt_status st = rtg::check_newton_options(o, "rt_create"); st != RT_OK) return st;
 
   rt_ctx *c = new (std::nothrow) rt_ctx;

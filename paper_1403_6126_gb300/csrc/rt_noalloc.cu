@@ -154,8 +154,9 @@ extern "C" rt_status rt_step_noalloc(const rt_grid *g, const rt_angles *ang, dou
     N *= a.n[d];
   }
   if (N >= (1LL << 28)) return set_error(RT_E_INVALID, "rt_step_noalloc: more than 2^28 cells");
-  if (!(dt > 0) || !std::isfinite(dt) || !(Crat > 0) || !(Prat > 0) || !(opts->gamma > 1) || !(opts->r_ideal > 0))
-    return set_error(RT_E_INVALID, "rt_step_noalloc: need dt, Crat, Prat, r_ideal > 0 and gamma > 1");
+  if (!(dt > 0) || !std::isfinite(dt) || !(Crat > 0) || !(Prat > 0) || !(opts->gamma > 1) || !(opts->r_ideal > 0) ||
+      !std::isfinite(Crat) || !std::isfinite(Prat) || !std::isfinite(opts->gamma) || !std::isfinite(opts->r_ideal))
+    return set_error(RT_E_INVALID, "rt_step_noalloc: need finite dt, Crat, Prat, r_ideal > 0 and gamma > 1");
   if (opts->precision != RT_FP32) return set_error(RT_E_INVALID, "rt_step_noalloc: float intensities only (RT_FP32)");
   if (rt_status st = rtg::check_newton_options(*opts, "rt_step_noalloc"); st != RT_OK) return st;
   const size_t sm_need = g->dim == 1   ? rtg::stepk::smem_bytes_q(1, M, true, 512, 1, 1, true)

@@ -106,6 +106,12 @@ def test_create_validates_before_touching_the_device():
     g = _grid()
     g.bc[0][0], g.bc[0][1] = rt.RT_BC_PERIODIC, rt.RT_BC_VACUUM
     _expect(rt.RT_E_INVALID, rt.rt_create, g, _angles(n, w), 10.0, 1.0, o)
+    for field, value in (("cfl", 0.0), ("cfl", float("inf")), ("gamma", 1.0), ("gamma", float("nan")),
+                         ("r_ideal", float("inf"))):
+        bad_o = rt.rt_options_default()
+        setattr(bad_o, field, value)
+        _expect(rt.RT_E_INVALID, rt.rt_create, _grid(), _angles(n, w), 10.0, 1.0, bad_o)
+        assert "finite cfl" in rt.rt_last_error()
     o.precision = 7
     _expect(rt.RT_E_INVALID, rt.rt_create, _grid(), _angles(n, w), 10.0, 1.0, o)
     assert "precision" in rt.rt_last_error()
@@ -167,3 +173,21 @@ def test_noalloc_refuses_in_place_buffers_on_the_host():
             f.mom_out = f.mom_in
         _expect(rt.RT_E_INVALID, rt.rt_step_noalloc, _grid(), _angles(n, w), 10.0, 1.0, o, 1e-3, f)
         assert "different buffers" in rt.rt_last_error()
+
+
+def test_noalloc_refuses_non_finite_scalars_on_the_host():
+    # every scalar is checked before the device is touched (the field
+    # pointers here are distinct dummies that are never dereferenced)
+    n, w = oracle.angles.by_name("gl8")
+    n, w = np.ascontiguousarray(n), np.ascontiguousarray(w)
+    f = rt.rt_noalloc_fields()
+    for i, (k, _) in enumerate(f._fields_):
+        setattr(f, k, 4096 * (i + 1))
+    for C, P, dt, field, value in ((float("inf"), 1.0, 1e-3, None, None), (10.0, float("inf"), 1e-3, None, None),
+                                   (10.0, 1.0, float("nan"), None, None), (10.0, 1.0, 1e-3, "gamma", float("inf")),
+                                   (10.0, 1.0, 1e-3, "r_ideal", float("nan"))):
+        o = rt.rt_options_default()
+        if field:
+            setattr(o, field, value)
+        _expect(rt.RT_E_INVALID, rt.rt_step_noalloc, _grid(), _angles(n, w), C, P, o, dt, f)
+        assert "need finite" in rt.rt_last_error()
