@@ -831,6 +831,7 @@ rt_status rt_run(rt_ctx *c, double dt, int nsteps) {
   if (nsteps < 0) return fail(RT_E_INVALID, "rt_run: nsteps < 0");
   if (nsteps == 0) return RT_OK;
   if (!(dt > 0)) dt = rt_cfl_dt(c);
+  if (!std::isfinite(dt)) return fail(RT_E_INVALID, "rt_run: dt not finite");
   if (c->stream == nullptr) {
     // the legacy default stream cannot be captured: plain launches
     for (int k = 0; k < nsteps; ++k) {
