@@ -60,6 +60,38 @@ def test_thermal_equilibrium_static_medium(E0, T4, sa):
     np.testing.assert_allclose(out["E"], Teq ** 4, rtol=1e-8)
 
 
+@pytest.mark.parametrize("dense", [False, True])
+def test_isotropic_equilibrium_is_a_fixed_point(dense):
+    # secs. 4.2-4.4: a static medium (v = 0) at one temperature with
+    # I = T^4 / (4 pi) on every angle is in radiative equilibrium whatever the
+    # opacities and densities are cell by cell: transport moves nothing, the
+    # emission balances the absorption and scattering keeps an isotropic
+    # field.  Every step leaves I and T as they were and hands the gas no
+    # energy or momentum (T live, periodic 3-D box, uneven random fields).
+    # To round-off: the dense Gaussian elimination of systems whose diagonal
+    # reaches 1 + dt C sigma ~ 700 keeps about 12 digits (measured 1.0e-12
+    # after five steps), the reduced form about 15.
+    rtol = 1e-11 if dense else 1e-13
+    rng = np.random.default_rng(17)
+    p = _uniform((4, 5, 6), "s6", C=30.0, P=3.0, hold_T=False, dense=dense)
+    N, M = p.N, p.M
+    T0 = 1.3
+    I = np.full((M, N), T0 ** 4 / FOURPI)
+    T = np.full(N, T0)
+    rho = rng.uniform(0.2, 5.0, N)
+    sa, ss = 10 ** rng.uniform(-2, 4, N), 10 ** rng.uniform(-2, 4, N)
+    dt = oracle.cfl_dt(p, 0.4)
+    for _ in range(5):
+        out = oracle.step(p, dt, I, T, rho, np.zeros((3, N)), sa, ss)
+        assert out["failures"] == 0
+        I, T = out["I"], out["T"]
+    np.testing.assert_allclose(I, T0 ** 4 / FOURPI, rtol=rtol)
+    np.testing.assert_allclose(T, T0, rtol=rtol)
+    np.testing.assert_allclose(out["dEgas"], 0.0, atol=10 * rtol * T0 ** 4)
+    np.testing.assert_allclose(out["dMom"], 0.0, atol=10 * rtol * T0 ** 4)
+    np.testing.assert_allclose(out["E"], T0 ** 4, rtol=rtol)
+
+
 def test_large_opacity_reaches_equilibrium_in_about_one_step():
     # sec. 5.1: with s_a = 100 the step is much longer than the thermalisation
     # time and the equilibrium is reached within about one step.
