@@ -158,13 +158,15 @@ rt_status rt_create(const rt_grid *grid, const rt_angles *angles, double Crat, d
  * N values; v: 3N (component-major).  Requires rho > 0, T > 0,
  * sigma >= 0, all finite (RT_E_NONFINITE / RT_E_INVALID otherwise).  The
  * first call also sets I to the isotropic equilibrium T^4/(4 pi) unless
- * rt_set_intensity was called before. */
+ * rt_set_intensity was called before.  Host arrays have been read when the
+ * call returns (it waits for the stream to check the values). */
 rt_status rt_set_material(rt_ctx *ctx, const double *rho, const double *T, const double *v,
                           const double *sigma_a, const double *sigma_s);
 
 /* Sets I (M*N values, angle-major).  NULL sets the isotropic equilibrium
  * I = T^4/(4 pi) from the current temperature (needs rt_set_material).
- * Recomputes E_r, F_r, P_r of the new field. */
+ * Recomputes E_r, F_r, P_r of the new field.  A host array has been read
+ * when the call returns (it waits for the stream). */
 rt_status rt_set_intensity(rt_ctx *ctx, const double *I);
 
 /* Incoming intensities (M values) for a face with bc == RT_BC_INFLOW:

@@ -570,6 +570,9 @@ rt_status rt_set_intensity(rt_ctx *c, const double *I) {
   if (st != RT_OK) return st;
   if (c->bf16)
     RT_CUDA(rtg::launch_encode_b16(c->qscr, c->mom[c->cur], (unsigned short *)c->I[c->cur], c->M, N, c->stream));
+  // a host array may be page-locked, and then the copies above read it
+  // asynchronously: the call returns once they are done
+  if (I && !c->opt.device_ptrs) RT_CUDA(cudaStreamSynchronize(c->stream));
   c->intensity_set = true;
   return RT_OK;
 }
@@ -775,6 +778,9 @@ rt_status rt_load_state(rt_ctx *c, const void *buf, size_t bytes) {
   c->cur = 0;
   const char *in = static_cast<const char *>(buf) + sizeof h;
   std::memcpy(c->host_inflow.data(), in, sizeof(double) * 6 * (size_t)c->M);
+  // the float step takes its inflow from the host's float table (launch
+  // parameters), the batch kernel from the device table restored below
+  for (size_t i = 0; i < 6 * (size_t)c->M; ++i) c->host_inflowf[i] = (float)c->host_inflow[i];
   in += sizeof(double) * 6 * (size_t)c->M;
   void *p[16];
   size_t b[16];

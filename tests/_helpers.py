@@ -16,13 +16,15 @@ def oracle_problem(wl, n, w, dense=False):
                           estimate_v=wl["estimate_v"], dense=dense)
 
 
-def gpu_context(wl, n, w, precision, **kw):
+def gpu_context(wl, n, w, precision, inflow=True, **kw):
+    """A context for the workload; with inflow=False its inflow faces are
+    left without incoming intensities (zero until set)."""
     import paper_1403_6126_gb300 as rt
     prec = {"fp64": rt.RT_FP64, "fp32": rt.RT_FP32, "bf16": rt.RT_BF16}[precision]
     ctx = rt.Context(wl["shape"], n, w, wl["C"], wl["P"], dim=wl["dim"], lo=wl["lo"], hi=wl["hi"], bc=wl["bc"],
                      precision=prec, cfl=wl["cfl"], gamma=wl["gamma"], r_ideal=wl["R"], hold_T=wl["hold_T"],
                      estimate_v=wl["estimate_v"], **kw)
-    for (axis, side), rule in wl["inflow"].items():
+    for (axis, side), rule in (wl["inflow"].items() if inflow else ()):
         ctx.set_inflow(axis, side, wlmod.inflow_values(rule, n))
     return ctx
 

@@ -14,9 +14,9 @@ from _helpers import gpu_context, initial_state
 pytestmark = pytest.mark.gpu
 
 
-def _make(wl, precision, set_material=True):
+def _make(wl, precision, set_material=True, inflow=True):
     n, w = oracle.angles.by_name(wl["angles"])
-    ctx = gpu_context(wl, n, w, precision)
+    ctx = gpu_context(wl, n, w, precision, inflow=inflow)
     if set_material:
         ctx.set_intensity(initial_state(wl, len(w), precision))
         ctx.set_material(wl["rho"], wl["T"], wl["v"], wl["sa"], wl["ss"])
@@ -48,9 +48,9 @@ def test_resume_is_bitwise(name, kw, precision):
         first.step(0.0)
     buf = first.save_state()
     first.close()
-    # a fresh context: same grid, angles and options (inflow tables come
-    # from the state), no material set before the load
-    second = _make(wl, precision, set_material=False)
+    # a fresh context: same grid, angles and options, no inflow and no
+    # material set before the load (both come from the state)
+    second = _make(wl, precision, set_material=False, inflow=False)
     second.load_state(buf)
     for _ in range(3):
         second.step(0.0)
