@@ -588,6 +588,12 @@ rt_status rt_set_inflow(rt_ctx *c, int axis, int side, const double *I_ghost) {
   rt_status st = convert_in(c, c->stage, c->inflow, 6 * c->M);
   if (st != RT_OK) return st;
   RT_CUDA(cudaStreamSynchronize(c->stream));
+  // the float step carries the table in its launch parameters: a graph
+  // captured by rt_run holds the old one
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
   return RT_OK;
 }
 

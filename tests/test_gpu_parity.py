@@ -9,7 +9,7 @@ import pytest
 import oracle
 from paper_1403_6126_gb300 import workloads as wlmod
 
-from _helpers import field_err, flux_magnitude, rel_err, run_both
+from _helpers import field_err, flux_magnitude, gpu_context, initial_state, rel_err, run_both
 
 pytestmark = pytest.mark.gpu
 
@@ -178,3 +178,34 @@ def test_crossing_beams(precision):
     else:
         assert np.abs(E - o["E"]).max() <= MIXED_TOL * Emax
         assert np.abs(flux_magnitude(F) - flux_magnitude(o["F"])).max() <= MIXED_TOL * Emax
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_inflow_change_between_graph_runs(precision):
+    # rt_run replays a captured CUDA graph of its steps; an inflow table set
+    # between two runs must reach the second one (the float step carries the
+    # table in its launch parameters, which a kept graph would replay):
+    # the same steps as plain launches give bitwise the same result
+    import torch
+    wl = wlmod.shadow2d(nx=40, ny=24, angles="s4", steps=0)
+    n, w = oracle.angles.by_name(wl["angles"])
+    stream = torch.cuda.Stream()
+    out = []
+    for graph in (True, False):
+        ctx = gpu_context(wl, n, w, precision, stream=stream.cuda_stream)
+        ctx.set_intensity(initial_state(wl, len(w), precision))
+        ctx.set_material(wl["rho"], wl["T"], wl["v"], wl["sa"], wl["ss"])
+        for k, scale in enumerate((1.0, 3.0)):
+            if k:
+                for (axis, side), rule in wl["inflow"].items():
+                    ctx.set_inflow(axis, side, scale * wlmod.inflow_values(rule, n))
+            if graph:
+                ctx.run(0.0, 4)
+            else:
+                for _ in range(4):
+                    ctx.step(0.0)
+        ctx.sync()
+        out.append(ctx.moments())
+        ctx.close()
+    for a, b in zip(*out):
+        np.testing.assert_array_equal(a, b)
