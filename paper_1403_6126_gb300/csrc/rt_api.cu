@@ -520,7 +520,10 @@ rt_status rt_set_material(rt_ctx *c, const double *rho, const double *T, const d
   RT_CUDA(cudaStreamSynchronize(c->stream));
   if (flag & 1) return fail(RT_E_NONFINITE, "rt_set_material: need finite rho > 0, T > 0, sigma >= 0, v");
   if ((st = fields_in(c, 0, N, true, c->stream)) != RT_OK) return st;
+  const bool vel_before = rtg::velocity_on(c);
   c->has_v = (flag & 2) != 0;
+  // a batch compiles its launch for the velocity terms or without them
+  if (c->batch && rtg::velocity_on(c) != vel_before) rtg::batch_touch(c->batch);
   c->material_set = true;
   if (!c->intensity_set) return rt_set_intensity(c, nullptr);
   return RT_OK;

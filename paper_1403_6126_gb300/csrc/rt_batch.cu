@@ -54,6 +54,10 @@ struct rt_batch {
   int graph_steps = 0, graph_phase = -1;
 };
 
+void rtg::batch_touch(void *batch) {
+  if (batch) static_cast<rt_batch *>(batch)->dirty = true;
+}
+
 namespace {
 
 rt_status cuda_err(cudaError_t e, const char *what) {

@@ -90,4 +90,7 @@ cudaError_t launch_ctx_step_on(rt_ctx *c, const StepArgs<float> &a, bool vel, Ti
 cudaError_t launch_ctx_step_on(rt_ctx *c, const StepArgs<double> &a, bool vel, TileShape t, cudaStream_t s);
 // Whether a problem of this dimension and angle count fits the batch tile.
 bool batch_fits(int dim, int M, bool vel);
+// Marks a batch for a rebuild before its next step (a member changed what
+// the batch's launch depends on).
+void batch_touch(void *batch);
 }  // namespace rtg
