@@ -290,7 +290,9 @@ void rt_destroy(rt_ctx *ctx);
  * RT_FP32, the batch's stream, and have their material set; while in a
  * batch they are stepped only by rt_batch_step (rt_step returns
  * RT_E_STATE), and are read with the usual rt_moments / rt_sources /
- * rt_get_intensity / rt_sync calls.  The caller keeps ownership of them. */
+ * rt_get_intensity / rt_sync calls; between steps they may take new
+ * material, intensity or inflow through the usual calls.  The caller keeps
+ * ownership of them. */
 typedef struct rt_batch rt_batch;
 
 /* stream: the cudaStream_t of the member contexts (NULL: legacy default
