@@ -420,6 +420,9 @@ class Context:
         rt_set_intensity(self.ctx, None if I is None else self._host(I, self.M * self.N))
 
     def set_inflow(self, axis, side, I_ghost):
+        I_ghost = np.ascontiguousarray(I_ghost, dtype=np.float64).reshape(-1)
+        if I_ghost.size != self.M:
+            raise ValueError("expected %d incoming intensities, got %d" % (self.M, I_ghost.size))
         rt_set_inflow(self.ctx, axis, side, I_ghost)
 
     def cfl_dt(self):
