@@ -55,3 +55,34 @@ def test_cpu_baseline_reports_the_threads_it_used():
     assert "6x6x6 cells x 8 angles" in one["sample"] and "1 thread" in one["sample"]
     two = bench.cpu_baseline("box3d", 2, 1, wl=wl, threads=2)
     assert two["cores"] == 2 and "2 timed steps (+1 warm-up)" in two["sample"]
+
+
+def test_roofline_bytes_and_profile_traffic():
+    # 848 bytes per cell at 80 float angles with T live and velocity on:
+    # I in and out 640, rho sigma_a sigma_s v 24, T in and out 16, E F P_dd
+    # of step n 56, moments and sources out 112
+    assert bench.algorithmic_bytes_per_cell(80, 4, True, True) == 848
+    assert bench.algorithmic_bytes_per_cell(80, 4, True, True) * 128 ** 3 == 1778384896
+    assert bench.algorithmic_bytes_per_cell(8, 8, False, False) == 2 * 8 * 8 + 48 + 8 + 112
+    # the ncu figure is reported only while the summary's kernel hash matches
+    text = open(bench.PROFILE).read()
+    assert "algorithmic_bytes_per_launch: `1778384896`" in text
+    traffic = bench._profile_traffic()
+    if ("kernel_source_sha256_16: `%s`" % bench.kernel_sha()) in text:
+        assert traffic is not None and traffic > 1778384896
+    else:
+        assert traffic is None
+
+
+def test_clock_summary_reads_nvidia_smi_rows():
+    s = bench.ClockSampler(0)
+    s.rows = [["0", "2070", "2070", "900.1", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+              ["0", "2055", "2070", "1100.5", "0x4", "Not Active", "Not Active", "Not Active", "Active"],
+              ["0", "1980", "2070", "1390.0", "0x4", "Not Active", "Not Active", "Not Active", "Active"]]
+    out = s.summary()
+    assert out["sm_mhz"] == 2055.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 3
+    assert out["reasons"] == ["sw_power_cap"]
+    s.rows = [["0", "[N/A]", "[N/A]", "[N/A]", "[N/A]", "Active", "Not Active", "Not Active", "Not Active"]]
+    out = s.summary()
+    assert out["sm_mhz"] is None and out["reasons"] == ["hw_slowdown"]
+    assert bench.ClockSampler(0).summary()["reasons"] == ["unsampled"]
