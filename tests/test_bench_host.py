@@ -86,3 +86,20 @@ def test_clock_summary_reads_nvidia_smi_rows():
     out = s.summary()
     assert out["sm_mhz"] is None and out["reasons"] == ["hw_slowdown"]
     assert bench.ClockSampler(0).summary()["reasons"] == ["unsampled"]
+
+
+def test_reference_arm_line(capsys):
+    # the reference arm's JSON line (the FP64 oracle on the host cores) on a
+    # small box: the contract's keys, its own cpu_baseline and an e2e entry
+    # with no host-device bytes
+    import json
+    args = types.SimpleNamespace(workload="box3d", n=8, steps=2, warmup=3, ref_steps=5)
+    assert bench.run_reference(args) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["dtype"] == "f64" and line["steps"] == 2 and line["warmup"] == 1
+    assert line["config"]["cells"] == 8 ** 3 and line["config"]["angles"] == 80
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
