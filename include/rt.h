@@ -215,9 +215,9 @@ rt_status rt_step(rt_ctx *ctx, double dt);
  * CUDA graph (no host work between steps) on a context with a stream; on
  * the legacy default stream (rt_options.stream NULL), which cannot be
  * captured, as plain launches.  The graph is kept for the next call with
- * the same dt, nsteps and buffer parity, and captured again after rt_set_tile,
- * rt_autotune, rt_set_inflow, rt_load_state or a change of the velocity
- * terms.  RT_E_INVALID for nsteps < 0 or a non-finite dt. */
+ * the same dt, nsteps and buffer parity, and captured again after
+ * rt_set_tile, a tile change by rt_autotune, rt_set_inflow, rt_load_state
+ * or a change of the velocity terms.  RT_E_INVALID for nsteps < 0 or a non-finite dt. */
 rt_status rt_run(rt_ctx *ctx, double dt, int nsteps);
 
 /* Waits for the context's stream and reports the status of the steps run
