@@ -92,6 +92,33 @@ def test_isotropic_equilibrium_is_a_fixed_point(dense):
     np.testing.assert_allclose(out["E"], T0 ** 4, rtol=rtol)
 
 
+@pytest.mark.parametrize("dense", [False, True])
+@pytest.mark.parametrize("sa", [1.0, 100.0])
+def test_energy_exchange_is_backward_euler_in_both_unknowns(sa, dense):
+    # secs. 4.3 and 5.1: Step 4 is backward Euler in I and T together.  For a
+    # static uniform medium (no transport, v = 0) with an anisotropic field,
+    # every angle obeys its own discrete transfer equation with the NEW
+    # temperature's emission, I1 - I0 = dt C s_a (T1^4 / (4 pi) - I1), and the
+    # gas takes what the radiation loses, rho R/(gamma-1) (T1 - T0) =
+    # -P (E1 - E0).  An emission at T^n (a semi-implicit step) keeps the
+    # second relation and the equilibrium but fails the first.
+    rng = np.random.default_rng(23)
+    p = _uniform((1, 2, 2), "s4", C=10.0, P=1.0, hold_T=False, dense=dense)
+    N, M = p.N, p.M
+    I0 = np.repeat(rng.uniform(1.0, 15.0, (M, 1)), N, axis=1)
+    T0 = np.full(N, 1.0)
+    kv = 1.0 / (5.0 / 3.0 - 1.0)
+    dt = oracle.cfl_dt(p, 0.4)
+    out = oracle.step(p, dt, I0, T0, np.ones(N), np.zeros((3, N)), np.full(N, sa), np.zeros(N))
+    assert out["failures"] == 0
+    I1, T1 = out["I"], out["T"]
+    a = dt * p.C * sa
+    np.testing.assert_allclose(I1, (I0 + a * T1 ** 4 / FOURPI) / (1.0 + a), rtol=1e-12)
+    E0 = FOURPI * np.einsum("m,mc->c", p.w, I0)
+    np.testing.assert_allclose(kv * (T1 - T0), -p.P * (out["E"] - E0), rtol=1e-11, atol=1e-12 * E0.max())
+    assert (T1 > 1.0).all()                 # the field (E ~ 100) heats the gas
+
+
 def test_large_opacity_reaches_equilibrium_in_about_one_step():
     # sec. 5.1: with s_a = 100 the step is much longer than the thermalisation
     # time and the equilibrium is reached within about one step.
