@@ -329,3 +329,35 @@ def test_quadrature_of_isotropic_field():
         np.testing.assert_allclose(F, 0.0, atol=1e-15)
         np.testing.assert_allclose(P[:3], FOURPI * 0.7 / 3, rtol=1e-14)
         np.testing.assert_allclose(P[3:], 0.0, atol=1e-15)
+
+
+@pytest.mark.parametrize("estimate_v", [False, True])
+def test_transparent_cells_exchange_nothing_with_the_gas(estimate_v):
+    # secs. 2 and 4.3-4.4: the radiation acts on the gas only through the
+    # opacities.  In a cell with sigma_a = sigma_s = 0 the beams pass through
+    # (the transport changes I there) but the gas gets no momentum, no
+    # energy and keeps its temperature; the momentum source counts only the
+    # change made by the implicit steps (eq. momentumchange), not the
+    # transport flux.  A random anisotropic field on a periodic 3-D box,
+    # moving gas, every other cell transparent.
+    rng = np.random.default_rng(31)
+    p = _uniform((4, 4, 6), "s4", C=20.0, P=5.0, hold_T=False, estimate_v=estimate_v)
+    N, M = p.N, p.M
+    I = rng.uniform(0.05, 2.0, (M, N))
+    T = rng.uniform(0.5, 1.5, N)
+    rho = rng.uniform(0.5, 2.0, N)
+    v = rng.uniform(-0.1, 0.1, (3, N)) * p.C
+    clear = (np.arange(N) % 2) == 0
+    sa = np.where(clear, 0.0, 10 ** rng.uniform(-1, 2, N))
+    ss = np.where(clear, 0.0, 10 ** rng.uniform(-1, 2, N))
+    dt = oracle.cfl_dt(p, 0.4)
+    out = oracle.step(p, dt, I, T, rho, v, sa, ss, return_dF=True)
+    assert out["failures"] == 0
+    assert np.abs(out["dF"][:, clear]).max() > 1e-2          # the beams do move through them
+    # zero to the rounding of the (identity) implicit solves
+    mscale, escale = np.abs(out["dMom"]).max(), np.abs(out["dEgas"]).max()
+    np.testing.assert_allclose(out["dMom"][:, clear], 0.0, atol=1e-13 * mscale)
+    np.testing.assert_allclose(out["dEgas"][clear], 0.0, atol=1e-13 * escale)
+    np.testing.assert_array_equal(out["T"][clear], T[clear])
+    np.testing.assert_allclose(out["I"][:, clear], (I + out["dF"])[:, clear], rtol=1e-14, atol=0)
+    assert np.abs(out["dMom"][:, ~clear]).min() > 0 and np.abs(out["dEgas"][~clear]).min() > 0
