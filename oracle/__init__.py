@@ -21,8 +21,11 @@ import numpy as np
 from . import angles  # noqa: F401  (re-exported)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "rt_oracle.c")
-_LIB = os.path.join(_HERE, "_liborc.so")
+# RT_ORACLE_SRC / RT_ORACLE_LIB point the module at another copy of the C
+# source and its library (tests/oracle_mutations.py builds altered copies
+# there to check that the pins catch them); unset, the files beside this one
+_SRC = os.environ.get("RT_ORACLE_SRC") or os.path.join(_HERE, "rt_oracle.c")
+_LIB = os.environ.get("RT_ORACLE_LIB") or os.path.join(_HERE, "_liborc.so")
 
 PERIODIC, VACUUM, COPY, INFLOW = 0, 1, 2, 3
 
