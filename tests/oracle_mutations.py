@@ -44,7 +44,21 @@ MUTATIONS = {
     "IV without its factor 3": [("double iv = 3.0 * (nm[0]", "double iv = 1.0 * (nm[0]")],
     "IV faces not time-centred": [("double lv = IV[qa] + 0.5 * (1.0 - nv) * va;", "double lv = IV[qa] + 0.5 * va;"),
                                   ("double rv = IV[qb] - 0.5 * (1.0 - nv) * vb;", "double rv = IV[qb] - 0.5 * vb;")],
+    "one axis's cell size for all": [("double rdx = dt / p->dx[d];", "double rdx = dt / p->dx[0];")],
+    "IV face velocity of one cell": [("double vf = 0.5 * (vd[qa] + vd[qb]);", "double vf = vd[qa];")],
+    "IV Courant number times C": [("double nv = fabs(vf) * rdx;", "double nv = fabs(vf) * rdx * p->C;")],
+    "opacity without scattering": [("    J[c] = E[c] / (4 * ORC_PI);\n    st[c] = sa[c] + ss[c];",
+                                    "    J[c] = E[c] / (4 * ORC_PI);\n    st[c] = sa[c];")],
+    # quadrature (sec. 3) and the step-n moments the step uses
+    "P_xy and P_xz swapped": [("q[3] += n[0] * n[1] * wi; q[4] += n[0] * n[2] * wi;",
+                               "q[3] += n[0] * n[2] * wi; q[4] += n[0] * n[1] * wi;")],
+    "v~ with off-diagonal P": [("double Pd[3] = {Pm[6 * c], Pm[6 * c + 1], Pm[6 * c + 2]};",
+                                "double Pd[3] = {Pm[6 * c], Pm[6 * c + 3], Pm[6 * c + 4]};")],
+    "J = E instead of E / 4 pi": [("    J[c] = E[c] / (4 * ORC_PI);\n    st[c] = sa[c] + ss[c];",
+                                   "    J[c] = E[c];\n    st[c] = sa[c] + ss[c];")],
     # boundary values
+    "vacuum zeroes the outgoing rays too": [("  if (!incoming) return val;\n  if (p->bc[d][side] == ORC_VACUUM) return 0.0;",
+                                             "  if (p->bc[d][side] == ORC_VACUUM) return 0.0;\n  if (!incoming) return val;")],
     "inflow on the outgoing rays": [("int incoming = side ? (mud < 0) : (mud > 0);",
                                      "int incoming = side ? (mud > 0) : (mud < 0);")],
     "copy from the far end": [("cc[d] = side ? n - 1 : 0;", "cc[d] = side ? 0 : n - 1;")],
@@ -80,6 +94,9 @@ MUTATIONS = {
                                            "pre[i] += p->w[m] * p->mu[3 * m + i] * I0[m];")],
     "gas energy rho R / gamma": [("double kv = rho[c] * p->R / (p->gamma - 1.0);", "double kv = rho[c] * p->R / p->gamma;")],
     "kinetic energy change with the wrong sign": [("dEgas[c] = kv * (T1 - T[c]) + dEK;", "dEgas[c] = kv * (T1 - T[c]) - dEK;")],
+    "kinetic energy without the 1/2": [("dEK += ((m0 + dm) * (m0 + dm) - m0 * m0) / (2.0 * rho[c]);",
+                                        "dEK += ((m0 + dm) * (m0 + dm) - m0 * m0) / rho[c];")],
+    "Newton stopped at 1e-6": [("#define ORC_NEWTON_RTOL 1e-13", "#define ORC_NEWTON_RTOL 1e-6")],
 }
 
 

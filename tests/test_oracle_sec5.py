@@ -325,3 +325,96 @@ def test_gas_energy_source_closes_the_energy_budget(opacity):
         worst = max(worst, np.abs(gas + P * out["E"] - total0).max() / np.abs(total0).max())
     assert worst < 3 * paper_values()["moving_energy_error"]
     assert v[0].max() < 0.3 * C                       # the drag did work on the gas
+
+
+@pytest.mark.parametrize("estimate_v", [False, True])
+def test_whole_step_is_covariant_under_swapping_x_and_y(estimate_v):
+    # The method has no preferred axis: swapping x and y in the input (the
+    # grid, the fields, the velocity components and the angles: the S4 set
+    # maps onto itself) swaps them in every output.  A whole step on a
+    # random periodic 3-D box with moving gas, T live.  Catches any axis
+    # index taken from the wrong component (a slope, a face velocity, the
+    # P_dd of the velocity estimate, the order of the stored tensor).
+    n, w = angles.level_symmetric(4)
+    M = len(w)
+    rng = np.random.default_rng(53)
+    nz, ny, nx = 3, 4, 5
+    N = nz * ny * nx
+    dx = (0.1, 0.13, 0.11)
+    I = rng.uniform(0.1, 2.0, (M, nz, ny, nx))
+    T = rng.uniform(0.7, 1.3, (nz, ny, nx))
+    rho = rng.uniform(0.5, 2.0, (nz, ny, nx))
+    v = rng.uniform(-1.5, 1.5, (3, nz, ny, nx))
+    sa = 10 ** rng.uniform(-1, 2, (nz, ny, nx))
+    ss = 10 ** rng.uniform(-1, 2, (nz, ny, nx))
+    # angle m' of the swapped set has n' = (n_y, n_x, n_z) of angle m
+    key = {tuple(np.round(a, 12)): i for i, a in enumerate(n)}
+    perm = np.array([key[tuple(np.round([a[1], a[0], a[2]], 12))] for a in n])
+    sw = lambda a: np.ascontiguousarray(np.swapaxes(a, -1, -2))
+
+    def run(shape, d, I_, T_, rho_, v_, sa_, ss_):
+        p = oracle.Problem(shape, d, n, w, C=15.0, P=3.0, hold_T=False, estimate_v=estimate_v)
+        k = int(np.prod(shape))
+        return oracle.step(p, 0.4 * min(d) / 15.0, I_.reshape(M, k), T_.reshape(k), rho_.reshape(k),
+                           v_.reshape(3, k), sa_.reshape(k), ss_.reshape(k))
+
+    a = run((nz, ny, nx), dx, I, T, rho, v, sa, ss)
+    I2 = np.empty_like(sw(I))
+    I2[perm] = sw(I)
+    b = run((nz, nx, ny), (dx[1], dx[0], dx[2]), I2, sw(T), sw(rho), sw(v[[1, 0, 2]]), sw(sa), sw(ss))
+    back = lambda x, lead: sw(x.reshape(lead + (nz, nx, ny))).reshape(lead + (N,))
+    assert a["failures"] == 0 and b["failures"] == 0
+    np.testing.assert_allclose(back(b["I"], (M,))[perm], a["I"], rtol=1e-12)
+    for k in ("T", "E", "dEgas"):
+        np.testing.assert_allclose(back(b[k], ()), a[k], rtol=1e-12, atol=1e-13, err_msg=k)
+    for k in ("F", "dMom"):
+        np.testing.assert_allclose(back(b[k], (3,))[[1, 0, 2]], a[k], rtol=1e-11, atol=1e-12, err_msg=k)
+    # P: xx yy zz xy xz yz of the swapped problem are yy xx zz xy yz xz of the original
+    np.testing.assert_allclose(back(b["P"], (6,))[[1, 0, 2, 3, 5, 4]], a["P"], rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("estimate_v", [False, True])
+def test_whole_step_is_covariant_under_reflecting_x(estimate_v):
+    # The method has no preferred direction along an axis either: mirroring
+    # x (the cell order, v_x, and n_x of the angles: the S4 set maps onto
+    # itself) mirrors every output (F_x, P_xy, P_xz and the x momentum change
+    # sign).  A whole step on a random periodic 3-D box with moving gas, T
+    # live.  Catches a face quantity taken from one side (say the face
+    # velocity of the IV term from the lower cell alone) where it should be
+    # symmetric.
+    n, w = angles.level_symmetric(4)
+    M = len(w)
+    rng = np.random.default_rng(59)
+    nz, ny, nx = 3, 4, 6
+    N = nz * ny * nx
+    dx = (0.1, 0.13, 0.11)
+    I = rng.uniform(0.1, 2.0, (M, nz, ny, nx))
+    T = rng.uniform(0.7, 1.3, (nz, ny, nx))
+    rho = rng.uniform(0.5, 2.0, (nz, ny, nx))
+    v = rng.uniform(-1.5, 1.5, (3, nz, ny, nx))
+    sa = 10 ** rng.uniform(-1, 2, (nz, ny, nx))
+    ss = 10 ** rng.uniform(-1, 2, (nz, ny, nx))
+    key = {tuple(np.round(a, 12)): i for i, a in enumerate(n)}
+    perm = np.array([key[tuple(np.round([-a[0], a[1], a[2]], 12))] for a in n])
+    fl = lambda a: np.ascontiguousarray(a[..., ::-1])
+
+    def run(I_, T_, rho_, v_, sa_, ss_):
+        p = oracle.Problem((nz, ny, nx), dx, n, w, C=15.0, P=3.0, hold_T=False, estimate_v=estimate_v)
+        return oracle.step(p, 0.4 * min(dx) / 15.0, I_.reshape(M, N), T_.reshape(N), rho_.reshape(N),
+                           v_.reshape(3, N), sa_.reshape(N), ss_.reshape(N))
+
+    a = run(I, T, rho, v, sa, ss)
+    I2 = np.empty_like(I)
+    I2[perm] = fl(I)
+    v2 = fl(v) * np.array([-1.0, 1.0, 1.0])[:, None, None, None]
+    b = run(I2, fl(T), fl(rho), v2, fl(sa), fl(ss))
+    back = lambda x, lead: fl(x.reshape(lead + (nz, ny, nx))).reshape(lead + (N,))
+    assert a["failures"] == 0 and b["failures"] == 0
+    np.testing.assert_allclose(back(b["I"], (M,))[perm], a["I"], rtol=1e-12)
+    for k in ("T", "E", "dEgas"):
+        np.testing.assert_allclose(back(b[k], ()), a[k], rtol=1e-12, atol=1e-13, err_msg=k)
+    sign3 = np.array([-1.0, 1.0, 1.0])[:, None]
+    for k in ("F", "dMom"):
+        np.testing.assert_allclose(sign3 * back(b[k], (3,)), a[k], rtol=1e-11, atol=1e-12, err_msg=k)
+    sign6 = np.array([1.0, 1.0, 1.0, -1.0, -1.0, 1.0])[:, None]
+    np.testing.assert_allclose(sign6 * back(b["P"], (6,)), a["P"], rtol=1e-12, atol=1e-13)

@@ -207,3 +207,47 @@ def test_crossing_beams_pass_through_each_other():
         wy0, wy1 = I0.sum(axis=1), I1.sum(axis=1)
         y_expect = (wy0 * y).sum() / wy0.sum() + p.C * n[m, 1] * t
         assert abs((wy1 * y).sum() / wy1.sum() - y_expect) < 0.05 * 4.0 / ny, m
+
+
+def test_outgoing_rays_see_the_same_ghost_at_every_open_face():
+    # Boundary values (setups of secs. 5.3, 5.8): vacuum, copy and inflow
+    # faces all copy the OUTGOING rays from the last active cell; they differ
+    # only on the incoming ones.  Each angle's transport depends only on its
+    # own intensities (v = 0), so an outgoing ray's Delta F is the same for
+    # the three kinds, also where the cells are optically thick (alpha < 1:
+    # the downwind ghost enters the face value).
+    n, w = angles.level_symmetric(4)
+    rng = np.random.default_rng(41)
+    shape = (1, 6, 7)
+    N, M = 42, len(w)
+    I = rng.uniform(0.1, 2.0, (M, N))
+    st = 10 ** rng.uniform(0, 3, N)                      # 10 dl sigma_t up to 1e3: alpha well below 1
+    dFs = {}
+    for kind in (oracle.VACUUM, oracle.COPY, oracle.INFLOW):
+        p = oracle.Problem(shape, (0.1, 0.12, 1.0), n, w, C=10.0, P=1.0, dim=2,
+                           bc=((kind, kind), (oracle.PERIODIC, oracle.PERIODIC), (0, 0)),
+                           inflow={(0, 0): rng.uniform(0, 3, M), (0, 1): rng.uniform(0, 3, M)})
+        dFs[kind] = oracle.transport(p, 0.4 * 0.1 / 10.0, I, np.zeros((3, N)), st, np.zeros(N))
+    out_lo = n[:, 0] < 0          # leaving through x_lo
+    out_hi = n[:, 0] > 0          # leaving through x_hi
+    first = (np.arange(N) % 7) == 0
+    last = (np.arange(N) % 7) == 6
+    for kind in (oracle.COPY, oracle.INFLOW):
+        np.testing.assert_allclose(dFs[kind][np.ix_(out_lo, first)], dFs[oracle.VACUUM][np.ix_(out_lo, first)],
+                                   rtol=1e-14, atol=1e-14)
+        np.testing.assert_allclose(dFs[kind][np.ix_(out_hi, last)], dFs[oracle.VACUUM][np.ix_(out_hi, last)],
+                                   rtol=1e-14, atol=1e-14)
+    # the incoming rays do see the face kind
+    assert np.abs(dFs[oracle.COPY][np.ix_(out_hi, first)] - dFs[oracle.VACUUM][np.ix_(out_hi, first)]).max() > 1e-3
+
+
+def test_pressure_tensor_component_order():
+    # sec. 3: P_r = 4 pi sum W n n I, stored xx, yy, zz, xy, xz, yz.  One
+    # ray along (1, 2, 3)/sqrt(14) carrying all the radiation.
+    nvec = np.array([[1.0, 2.0, 3.0]]) / np.sqrt(14.0)
+    p = oracle.Problem((1, 1, 2), 1.0, nvec, np.array([1.0]), C=1.0, P=1.0, dim=1)
+    E, F, P = oracle.moments(p, np.full((1, 2), 0.5))
+    s = 4 * np.pi * 0.5 / 14.0
+    np.testing.assert_allclose(E, 4 * np.pi * 0.5, rtol=1e-15)
+    np.testing.assert_allclose(F[:, 0] * np.sqrt(14.0) / (4 * np.pi * 0.5), [1, 2, 3], rtol=1e-15)
+    np.testing.assert_allclose(P[:, 0] / s, [1, 4, 9, 2, 3, 6], rtol=1e-14)
