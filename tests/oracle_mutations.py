@@ -8,7 +8,7 @@ at the copy) and runs the oracle's pin tests against it.  Every alteration
 must make at least one pin fail; the script prints the first failing pin of
 each and exits 1 if any alteration survives.
 
-usage: python tests/oracle_mutations.py [name ...]     (about ten minutes for all)
+usage: python tests/oracle_mutations.py [name ...]     (about six minutes for all on eight cores)
 """
 import os
 import subprocess
