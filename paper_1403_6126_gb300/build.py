@@ -20,10 +20,11 @@ LIB = os.path.join(HERE, "librt_gb300.so")
 LIB_CHECK = os.path.join(HERE, "librt_gb300_check.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
-# Units that instantiate the float step kernel (rt_step_pair.cuh).  Its
-# per-angle arithmetic spells out every fused multiply-add it wants; these
-# units are compiled without implicit contraction so that the per-cell code
-# rounds the same way wherever it is inlined: the single-problem, batch and
+# Units that instantiate the float step kernels (rt_step_quad.cuh, and the
+# pair kernel of rt_step_pair.cuh for bf16 storage).  Their per-angle
+# arithmetic spells out every fused multiply-add it wants; these units are
+# compiled without implicit contraction so that the per-cell code rounds the
+# same way wherever it is inlined: the single-problem, batch and
 # allocation-free kernels then give bitwise equal results.
 NO_CONTRACT = {"rt_step_f3.cu", "rt_step_f12.cu", "rt_step_b16.cu", "rt_batch_k512.cu", "rt_batch_k256.cu", "rt_batch_k128.cu",
                "rt_noalloc.cu"}
