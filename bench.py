@@ -30,7 +30,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PROFILE = os.path.join(ROOT, "profiles", "step_kernel_box3d.md")
-# sources of the float step kernel (the pair kernel and the tile geometry it shares)
+# sources of the float step kernel (the quad kernel, the packed-FP32 helpers of
+# the pair kernel it includes, and the tile geometry)
 KERNEL_SRCS = [os.path.join(ROOT, "paper_1403_6126_gb300", "csrc", f)
                for f in ("rt_step_quad.cuh", "rt_step_pair.cuh", "rt_step_kernel.cuh")]
 NOMINAL_HBM_GBS = 8000.0
